@@ -1,0 +1,313 @@
+"""Benchmark of the MRT lattice Boltzmann hot path on one GB300 (or N replicas).
+
+Workload: the synthetic four-directional braided cell 128x128x256 (interior
+braiding angle 30 deg, yarn fraction 0.45, seed 42, yarn tensor
+k_axial = 6.0 / k_trans = 0.8 rotated per family, matrix 0.2), temperature
+difference along z, periodic laterals, FP32 distributions.
+
+One bench step = one pass of the hot path over the cell: ITERS fused
+collide-stream iterations in check intervals of K = 100 (each interval ends
+with an FP64 plane-flux / residual check and the k_eff finalize), launched as
+one CUDA graph with a device-side while condition.  Metric: GLUPS (giga
+lattice updates per second).  The f buffers (2 x 117 MB) exceed the 129 MB
+L2, so no flush is needed between steps.
+
+`value`: device time (CUDA events on the solver's stream) with the state
+resident.  `e2e`: the same metric through the public C ABI with host
+buffers: upload the phase map and tensors, solve ITERS iterations from the
+linear start, download the temperature field, every step.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, NY, NZ = 128, 128, 256
+G_DEG, PHI, SEED, NMAX = 30.0, 0.45, 42, 128
+K = 100
+ITERS = 1000
+BYTES_PER_LUP = 57          # 7 x 4 B read + 7 x 4 B written + 1 B phase id
+WORKLOAD = (f"braid {NX}x{NY}x{NZ} g=30deg phi=0.45 seed=42, dT along z, periodic laterals, "
+            f"FP32 D3Q7 MRT")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (getattr(self, "out", "") or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_cell(lbm, I, device):
+    S = lbm.Solver(NX, NY, NZ, device=device)
+    anchors = I.braid_anchors(NX, NY, SEED, n_max=NMAX)
+    used, frac = S.set_geometry_braid(math.radians(G_DEG), anchors, PHI)
+    lam = I.braid_tensors(G_DEG)
+    S.set_tensors(lam)
+    return S, lam, used, frac
+
+
+def cpu_oracle_sample(seconds_target=15.0):
+    """Times the FP64 oracle on the host cores on the same cell: a fixed
+    number of iterations of the full 128x128x256 lattice."""
+    from oracle import oracle as O
+    from paper_1503_08718_gb300 import inputs as I
+
+    anchors = I.braid_anchors(NX, NY, SEED, n_max=NMAX)
+    phase, _, _ = O.braid_phase(NX, NY, NZ, math.radians(G_DEG), anchors, PHI)
+    lam = I.braid_tensors(G_DEG)
+    L = O.Lattice(phase, lam, O.lattice_scale(lam), 2, 0)
+    L.init_linear()
+    t0 = time.perf_counter()
+    L.step(2)
+    dt = time.perf_counter() - t0
+    n = max(2, min(200, int(seconds_target / max(dt / 2, 1e-6))))
+    t0 = time.perf_counter()
+    L.step(n)
+    dt = time.perf_counter() - t0
+    glups = NX * NY * NZ * n / dt / 1e9
+    return glups, O.max_threads(), n, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O  # noqa: F401  (builds on first use)
+    per_step = []
+    glups_all = []
+    cores = None
+    sample = None
+    for i in range(args.warmup + args.steps):
+        glups, cores, n, dt = cpu_oracle_sample(seconds_target=args.ref_seconds)
+        if i >= args.warmup:
+            per_step.append(dt)
+            glups_all.append(glups)
+            sample = f"{n} FP64 oracle iterations of the full {NX}x{NY}x{NZ} cell per step"
+    value = statistics.mean(glups_all)
+    line = {
+        "impl": "reference", "metric": "GLUPS", "value": value, "unit": "GLUPS",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * statistics.mean(per_step), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "iters_per_step": "bounded sample"},
+        "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1503_08718_gb300 import build as B
+    from paper_1503_08718_gb300 import inputs as I
+    from paper_1503_08718_gb300 import lbm
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    B.build()
+    lbm.load()
+
+    S, lam, used, frac = make_cell(lbm, I, dev)
+    stream = torch.cuda.Stream(device=dev)
+    iters = args.iters
+    opts = S.opts(tol=0.0, max_iters=iters, check_every=K)
+    opts.stream = int(stream.cuda_stream)
+
+    def one_step():
+        S.start(2, 0, opts)
+        info = S.run()
+        assert info.iters == iters, info.as_dict()
+        return info
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        ev0.record(stream)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            info = one_step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        torch.distributed.barrier()
+        t = torch.tensor([ms], device=f"cuda:{dev}", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    n_vox = NX * NY * NZ
+    lups = n_vox * iters * args.steps * ws
+    glups = lups / (ms / 1000.0) / 1e9
+    launches_per_step = iters + iters // K + 2      # fused steps, finalizes, permute + init
+    # roofline of the dominant kernel (the fused step): algorithmic bytes per
+    # launch over the average launch time of the timed region
+    per_launch_s = (ms / 1000.0) / (args.steps * iters)
+    achieved = BYTES_PER_LUP * n_vox / per_launch_s / 1e9
+    peak, peak_kind = peaks()
+
+    # end to end through the public API with host buffers
+    anchors = I.braid_anchors(NX, NY, SEED, n_max=NMAX)
+    phase_h = S.geometry()
+    T_h = np.empty((NZ, NY, NX), np.float32)
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.set_geometry(phase_h, 5)
+        S.set_tensors(lam)
+        S.start(2, 0, opts)
+        S.run()
+        S.temperature(out=T_h)
+        S.k_eff()
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            e2e_ms.append((t1 - t0) * 1000)
+    e2e_glups = n_vox * iters * len(e2e_ms) * ws / (sum(e2e_ms) / 1000.0) / 1e9
+    del anchors
+
+    if rank == 0:
+        cpu = None
+        if not args.skip_cpu:
+            g, cores, n, dt = cpu_oracle_sample(seconds_target=args.ref_seconds)
+            cpu = {"value": g, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+                   "sample": f"{n} FP64 oracle iterations of the full {NX}x{NY}x{NZ} cell "
+                             f"({dt:.1f} s)"}
+        line = {
+            "metric": "GLUPS", "value": glups, "unit": "GLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "iters_per_step": iters, "check_every": K,
+                       "yarns": used, "yarn_fraction": round(frac, 6),
+                       "l2": "inputs larger than L2 (f buffers 2 x 117 MB)",
+                       "parallelism": f"replicas{ws}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": args.traffic,
+                         "peak_source": peak_kind, "bytes_per_lup": BYTES_PER_LUP},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_glups, "unit": "GLUPS",
+                    "h2d_bytes_per_step": n_vox + lam.nbytes,
+                    "d2h_bytes_per_step": 4 * n_vox + 8},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk.summary(),
+            "k_eff_after_step": info.k_eff,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    S.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--iters", type=int, default=ITERS, help="iterations per step (multiple of 100)")
+    ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline leg")
+    ap.add_argument("--ref-seconds", type=float, default=15.0)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per fused-step launch from an ncu capture")
+    args = ap.parse_args()
+    if args.iters % K:
+        ap.error("--iters must be a multiple of 100")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) solver for the effective thermal
+ * conductivity of heterogeneous anisotropic media with the D3Q7
+ * multiple-relaxation-time lattice Boltzmann model and an off-diagonal
+ * relaxation block (Fang et al., arXiv 1503.08718).
+ *
+ * Problem statement (Section 2.1, Eq. 1-4; Section 2.3): a voxel phase map,
+ * one symmetric conductivity tensor per phase, a temperature difference
+ * applied across two opposite faces (Dirichlet, Eq. 23) and either periodic
+ * (Eq. 25) or adiabatic (Eq. 24 with zero flux) conditions on the four other
+ * faces.  The solver iterates the lattice Boltzmann map (Eq. 5-13, 21) to its
+ * steady state and returns the effective conductivity of Eq. 22.
+ *
+ * Conventions shared by every call:
+ *   - Lattice units dx = dt = 1; gamma = 1/8 and eps = 2 gamma (Section 2.2);
+ *     relaxation times tau_0 = tau_4 = tau_5 = tau_6 = 1.
+ *   - The diffusivity is D = s * lambda (unit heat capacity, Eq. 20) with a
+ *     lattice scale s; tau = I/2 + D/eps (Eq. 13).  s is chosen so the largest
+ *     diagonal tau equals opts.tau_max, unless opts.lattice_scale > 0 sets it.
+ *   - Arrays of voxels are x fastest: index = (z * ny + y) * nx + x.
+ *   - Tensors are 6 doubles per phase in the order xx, yy, zz, yz, xz, xy.
+ *   - The hot wall (t_hot) is the face at the axis minimum, walls sit half a
+ *     spacing outside the first and last node, L = N_axis and A = N_b N_c.
+ *   - Pointers documented as "host" are read (or written) during the call
+ *     only and never retained; every buffer the library needs on the device
+ *     is allocated and owned by the context.
+ *   - A call that fails returns a non-zero lbm_status and records a message
+ *     retrievable with lbm_last_error().  After LBM_ERR_CUDA the context is
+ *     poisoned: only lbm_last_error() and lbm_destroy() remain valid.
+ *   - One context per host thread; contexts are independent.
+ *   - Computation is FP32 with distributions stored as deviations from
+ *     w_i * T_ref, T_ref = (t_hot + t_cold) / 2; plane-flux and residual
+ *     reductions are FP64.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID_ARG = 1,   /* bad size, pointer, id or tensor */
+    LBM_ERR_STATE = 2,         /* call out of order (e.g. solve before set_tensors) */
+    LBM_ERR_CUDA = 3,          /* CUDA runtime error; context poisoned */
+    LBM_ERR_OUT_OF_MEMORY = 4, /* device allocation failed */
+    LBM_ERR_NOT_CONVERGED = 5, /* max_iters reached; results still readable */
+    LBM_ERR_DIVERGED = 6,      /* non-finite residual or flux */
+    LBM_ERR_STALLED = 7,       /* residual did not improve for stall_checks checks */
+    LBM_ERR_TIMEOUT = 8,       /* reserved for bounded device-side waits */
+    LBM_ERR_INTERNAL = 9
+} lbm_status;
+
+typedef enum { LBM_AXIS_X = 0, LBM_AXIS_Y = 1, LBM_AXIS_Z = 2 } lbm_axis;
+typedef enum { LBM_LATERAL_PERIODIC = 0, LBM_LATERAL_ADIABATIC = 1 } lbm_lateral;
+typedef enum { LBM_STORE_F32 = 0 } lbm_storage;
+
+typedef struct {
+    double t_hot, t_cold;   /* wall temperatures (defaults 1, 0); t_hot != t_cold */
+    double tau_max;         /* largest diagonal relaxation time (default 1.5), > 0.5 */
+    double lattice_scale;   /* > 0 overrides tau_max: D = lattice_scale * lambda */
+    double tol;             /* stop when R_T <= tol at a check (default 1e-8) */
+    int64_t max_iters;      /* iteration cap (default 50 000 000) */
+    int32_t check_every;    /* K: steps per check interval, even, >= 2 (default 100) */
+    int32_t stall_checks;   /* stop with LBM_ERR_STALLED after this many checks
+                               without a new smallest R_T; 0 disables (default 0) */
+    int32_t storage;        /* lbm_storage; LBM_STORE_F32 */
+    int32_t reserved;
+    const float* t_init;    /* host, nx*ny*nz initial T field in the original axis
+                               order, or NULL for the linear profile between walls */
+    void* stream;           /* cudaStream_t for all work, or NULL for the context's */
+} lbm_solve_opts;
+
+typedef struct {
+    int64_t iters;          /* iterations performed since lbm_start */
+    double k_eff;           /* Eq. 22 at the last check */
+    double residual_T;      /* R_T = sum|T^n - T^(n-1)| / sum|T^n| at the last check */
+    double residual_Q;      /* R_Q = (max_k Q - min_k Q) / |mean Q| at the last check */
+    double elapsed_ms;      /* device time of the call's iterations (CUDA events) */
+    double lattice_scale;   /* s used */
+    int32_t status;         /* lbm_status of the solve */
+    int32_t checks;         /* number of checks performed since lbm_start */
+} lbm_solve_info;
+
+/* Fills o with the defaults listed in lbm_solve_opts. */
+void lbm_default_opts(lbm_solve_opts* o);
+
+/* Creates a context for an nx*ny*nz cell on CUDA device cuda_device.
+ * Sizes must be >= 2 and nx*ny*nz < 2^31.  *out receives the context. */
+lbm_status lbm_create(int nx, int ny, int nz, int cuda_device, lbm_ctx** out);
+
+/* Voxel phase map (step-wise material description, Sections 3.2 and 5).
+ * phase: host, nx*ny*nz uint8 phase ids, each < n_phases; 1 <= n_phases <= 255.
+ * Copied to the device.  Invalidates any solve state. */
+lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* phase, int n_phases);
+
+/* Per-phase conductivity tensors (Eq. 26 rotated into xyz; Eq. 31).
+ * lambda: host, n_phases*6 doubles (xx, yy, zz, yz, xz, xy); each tensor must
+ * be symmetric positive definite (checked by Cholesky in FP64).
+ * n_phases must equal the geometry's. */
+lbm_status lbm_set_tensors(lbm_ctx* c, const double* lambda, int n_phases);
+
+/* Prepares a solve with the temperature difference along `axis` and the
+ * given lateral faces: computes s, tau and the relaxation block S_b = tau^-1
+ * per phase (Eq. 12-13) in FP64, lays the cell out with `axis` slowest, and
+ * writes the initial distributions f^eq(T0) (Eq. 6).  Iterations restart at 0.
+ * o may be NULL for defaults. */
+lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_solve_opts* o);
+
+/* Advances n_steps fused collide-stream iterations (Eq. 5, 21, 23-25) with
+ * no convergence check, asynchronously on the solve's stream. */
+lbm_status lbm_advance(lbm_ctx* c, int64_t n_steps);
+
+/* Runs one iteration as a check step: the fused step plus FP64 plane sums of
+ * the axial heat flux (Eq. 15-16) and the residual R_T, then Eq. 22.
+ * Synchronises the stream; info (nullable) receives the results. */
+lbm_status lbm_check(lbm_ctx* c, lbm_solve_info* info);
+
+/* Iterates from the current state in whole check intervals (CUDA graph with
+ * a device-side while condition, no host round trip per check) until R_T <=
+ * tol, max_iters, a stall or a non-finite value.  Synchronous. */
+lbm_status lbm_run(lbm_ctx* c, lbm_solve_info* info);
+
+/* lbm_start followed by lbm_run. */
+lbm_status lbm_solve(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral,
+                     const lbm_solve_opts* o, lbm_solve_info* info);
+
+/* Effective conductivity (Eq. 22) of the last check. */
+lbm_status lbm_k_eff(const lbm_ctx* c, double* out);
+
+/* Current temperature T = sum f (Eq. 14) into host_out (nx*ny*nz floats,
+ * original axis order). Synchronous. */
+lbm_status lbm_get_temperature(lbm_ctx* c, float* host_out);
+
+/* Plane sums Q[k] of the axial flux at the last check (n == N_axis doubles). */
+lbm_status lbm_get_plane_flux(const lbm_ctx* c, double* host_out, int n);
+
+/* Synthetic four-directional braided cell (yarns along
+ * (sx sin g / sqrt 2, sy sin g / sqrt 2, cos g), Section 4.1) voxelised on
+ * the device by a voxel-centre test in FP64 without contraction (the
+ * step-wise approximation of Section 3.2).  anchors: host, n_max (x0, y0)
+ * pairs; yarn i belongs to family i mod 4 with signs (+,+), (-,+), (-,-),
+ * (+,-) and elliptic section with semi-axes A (horizontal) and B.  Yarns are
+ * added in order until the yarn fraction reaches phi; a voxel takes the
+ * family (1..4) of the first yarn containing it, else 0.  Sets the geometry
+ * with n_phases = 5.  n_used and fraction (host, nullable) receive the yarn
+ * count and the achieved fraction. Returns LBM_ERR_INVALID_ARG if phi is not
+ * reached with n_max yarns or g is not in (0, pi/2). */
+lbm_status lbm_set_geometry_braid(lbm_ctx* c, double g_rad, double A, double B,
+                                  const double* anchors, int n_max, double phi,
+                                  int* n_used, double* fraction);
+
+/* Copies the phase map (nx*ny*nz uint8, original order) to host_out. */
+lbm_status lbm_get_geometry(lbm_ctx* c, uint8_t* host_out);
+
+/* Message of the last failed call on this context (context-owned string,
+ * valid until the next call).  NULL-safe. */
+const char* lbm_last_error(const lbm_ctx* c);
+
+/* Frees the context and all device memory it owns. NULL-safe. */
+void lbm_destroy(lbm_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,688 @@
+// C ABI of the GB300 lattice Boltzmann solver (declared in include/lbm.h).
+//
+// Host responsibilities: validation, the FP64 material-to-lattice step
+// (Eq. 12-13: tau = I/2 + s lambda / eps, S_b = tau^-1 per phase), laying the
+// cell out with the Dirichlet axis slowest, device memory, and the CUDA graph
+// that runs whole check intervals under a device-side while condition.  All
+// per-voxel work runs in the kernels of lbm_kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_kernels.cuh"
+
+using lbm::Ctl;
+using lbm::Layout;
+
+struct lbm_ctx {
+    int n[3] = {0, 0, 0};
+    int device = 0;
+    cudaStream_t own_stream = nullptr;     // context stream (non-blocking)
+    cudaStream_t cap_stream = nullptr;     // private stream used only for graph capture
+    bool poisoned = false;
+    std::string err;
+
+    // geometry and material (original order)
+    uint8_t* d_phase = nullptr;            // nx*ny*nz
+    int n_phases = 0;
+    bool have_geometry = false;
+    std::vector<double> lambda;            // n_phases*6
+    bool have_tensors = false;
+
+    // solve state
+    bool started = false;
+    int axis = 2, lateral = 0;
+    lbm_solve_opts opts{};
+    cudaStream_t stream = nullptr;         // stream used by the current solve
+    Layout L{};
+    float* d_f[2] = {nullptr, nullptr};
+    size_t cap_f[2] = {0, 0};              // capacity of the f buffers (floats)
+    int cur = 0;                           // buffer holding the current state
+    uint8_t* d_phase_c = nullptr;          // canonical padded phase map
+    size_t cap_phase_c = 0;
+    float4* d_sb = nullptr;                // 2 float4 per phase
+    int cap_sb = 0;
+    double* d_part = nullptr;
+    size_t cap_part = 0;
+    double* d_Q = nullptr;
+    int cap_Q = 0;
+    float* d_T = nullptr;                  // nx*ny*nz staging (T output / t_init input)
+    Ctl* d_ctl = nullptr;
+    Ctl* h_ctl = nullptr;                  // pinned mirror
+    double s = 0.0;
+    double t_ref = 0.0;
+    int blocks_per_plane = 0;
+    long long pstride = 0;
+    std::vector<double> Q_host;
+    double k_eff = NAN;
+    bool have_k = false;
+
+    // graph of one check interval inside a while node, one per buffer parity
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    std::vector<char> gsig[2];             // kernel arguments baked into each graph
+    int g_interval = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx* c, lbm_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return st;
+}
+
+#define CUDA_TRY(c, call)                                                                   \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            (c)->poisoned = true;                                                           \
+            return fail((c), e_ == cudaErrorMemoryAllocation ? LBM_ERR_OUT_OF_MEMORY        \
+                                                             : LBM_ERR_CUDA,                \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,   \
+                        __LINE__);                                                          \
+        }                                                                                   \
+    } while (0)
+
+#define CHECK_CTX(c)                                                                        \
+    do {                                                                                    \
+        if (!(c)) return LBM_ERR_INVALID_ARG;                                               \
+        if ((c)->poisoned) return fail((c), LBM_ERR_CUDA, "context poisoned by an earlier CUDA error"); \
+        (c)->err.clear();                                                                   \
+    } while (0)
+
+void free_graphs(lbm_ctx* c) {
+    for (int p = 0; p < 2; ++p) {
+        if (c->gexec[p]) cudaGraphExecDestroy(c->gexec[p]);
+        c->gexec[p] = nullptr;
+        c->gsig[p].clear();
+    }
+    c->g_interval = 0;
+}
+
+// Cholesky test of a symmetric 3x3 tensor (xx, yy, zz, yz, xz, xy).
+bool spd6(const double* t) {
+    const double a00 = t[0], a11 = t[1], a22 = t[2], a12 = t[3], a02 = t[4], a01 = t[5];
+    if (!(a00 > 0.0)) return false;
+    const double l00 = std::sqrt(a00);
+    const double l10 = a01 / l00, l20 = a02 / l00;
+    const double d1 = a11 - l10 * l10;
+    if (!(d1 > 0.0)) return false;
+    const double l11 = std::sqrt(d1);
+    const double l21 = (a12 - l20 * l10) / l11;
+    const double d2 = a22 - l20 * l20 - l21 * l21;
+    return d2 > 0.0 && std::isfinite(d2);
+}
+
+// Inverse of a symmetric 3x3 matrix (row-major) by cofactors, in FP64.
+void inv3(const double* m, double* r) {
+    const double c00 = m[4] * m[8] - m[5] * m[7];
+    const double c01 = m[5] * m[6] - m[3] * m[8];
+    const double c02 = m[3] * m[7] - m[4] * m[6];
+    const double det = m[0] * c00 + m[1] * c01 + m[2] * c02;
+    r[0] = c00 / det;
+    r[1] = (m[2] * m[7] - m[1] * m[8]) / det;
+    r[2] = (m[1] * m[5] - m[2] * m[4]) / det;
+    r[3] = c01 / det;
+    r[4] = (m[0] * m[8] - m[2] * m[6]) / det;
+    r[5] = (m[2] * m[3] - m[0] * m[5]) / det;
+    r[6] = c02 / det;
+    r[7] = (m[1] * m[6] - m[0] * m[7]) / det;
+    r[8] = (m[0] * m[4] - m[1] * m[3]) / det;
+}
+
+int grid_1d(long long total) {
+    long long b = (total + 255) / 256;
+    if (b > 152LL * 32) b = 152LL * 32;
+    return (int)(b < 1 ? 1 : b);
+}
+
+lbm::StepArgs step_args(const lbm_ctx* c, int src) {
+    lbm::StepArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.src = c->d_f[src];
+    a.dst = c->d_f[src ^ 1];
+    a.phase = c->d_phase_c;
+    a.sb = c->d_sb;
+    a.part = c->d_part;
+    a.pstride = c->pstride;
+    a.nx = c->L.NX;
+    a.ny = c->L.NY;
+    a.nz = c->L.NZ;
+    a.pitch = c->L.pitch;
+    a.n_phases = c->n_phases;
+    a.quads_per_plane = (c->L.pitch / 4) * c->L.NY;
+    a.blocks_per_plane = c->blocks_per_plane;
+    const double eps = 0.25;
+    a.g_hot = (float)(eps * (c->opts.t_hot - c->t_ref));
+    a.g_cold = (float)(eps * (c->opts.t_cold - c->t_ref));
+    a.t_ref = (float)c->t_ref;
+    return a;
+}
+
+cudaError_t launch_step(const lbm_ctx* c, int src, bool check, cudaStream_t st) {
+    const lbm::StepArgs a = step_args(c, src);
+    const dim3 grid(c->blocks_per_plane, c->L.NZ);
+    const size_t smem = sizeof(float4) * 2 * c->n_phases;
+    if (c->lateral == LBM_LATERAL_PERIODIC) {
+        if (check) lbm::step_kernel<true, true><<<grid, lbm::kThreads, smem, st>>>(a);
+        else lbm::step_kernel<true, false><<<grid, lbm::kThreads, smem, st>>>(a);
+    } else {
+        if (check) lbm::step_kernel<false, true><<<grid, lbm::kThreads, smem, st>>>(a);
+        else lbm::step_kernel<false, false><<<grid, lbm::kThreads, smem, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+lbm::FinalArgs final_args(const lbm_ctx* c, int steps, int interval) {
+    lbm::FinalArgs f;
+    std::memset(&f, 0, sizeof f);
+    f.part = c->d_part;
+    f.Q = c->d_Q;
+    f.ctl = c->d_ctl;
+    f.nz = c->L.NZ;
+    f.blocks_per_plane = c->blocks_per_plane;
+    f.steps = steps;
+    f.stall_checks = c->opts.stall_checks;
+    f.max_iters = c->opts.max_iters;
+    f.interval = interval;
+    f.tol = c->opts.tol;
+    f.keff_scale = (double)c->L.NZ /
+                   (c->s * (c->opts.t_hot - c->opts.t_cold) * (double)c->L.NX * (double)c->L.NY);
+    f.t_ref = c->t_ref;
+    f.handle = 0;
+    f.use_handle = 0;
+    return f;
+}
+
+template <typename T>
+lbm_status ensure(lbm_ctx* c, T** p, size_t count, size_t* cap) {
+    if (*p && *cap >= count) return LBM_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(c, LBM_ERR_OUT_OF_MEMORY, "cudaMalloc of %zu bytes failed: %s",
+                    sizeof(T) * count, cudaGetErrorString(e));
+    }
+    *cap = count;
+    return LBM_OK;
+}
+
+void fill_info(const lbm_ctx* c, lbm_solve_info* info, double ms) {
+    if (!info) return;
+    info->iters = c->h_ctl->iter;
+    info->k_eff = c->h_ctl->k_eff;
+    info->residual_T = c->h_ctl->r_t;
+    info->residual_Q = c->h_ctl->r_q;
+    info->elapsed_ms = ms;
+    info->lattice_scale = c->s;
+    info->status = c->h_ctl->status;
+    info->checks = (int32_t)c->h_ctl->checks;
+}
+
+lbm_status read_ctl(lbm_ctx* c, cudaStream_t st) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaMemcpyAsync(c->Q_host.data(), c->d_Q, sizeof(double) * c->L.NZ,
+                                cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    c->k_eff = c->h_ctl->k_eff;
+    c->have_k = c->h_ctl->checks > 0;
+    return LBM_OK;
+}
+
+// Everything a check-interval graph bakes in: the kernel arguments of both
+// buffer parities, the finalize arguments and the lateral type.
+std::vector<char> graph_signature(const lbm_ctx* c, int parity) {
+    const lbm::StepArgs a = step_args(c, parity);
+    const lbm::FinalArgs f = final_args(c, c->opts.check_every, c->opts.check_every);
+    std::vector<char> sig(sizeof a + sizeof f + 2 * sizeof(int));
+    std::memcpy(sig.data(), &a, sizeof a);
+    std::memcpy(sig.data() + sizeof a, &f, sizeof f);
+    const int extra[2] = {c->lateral, c->opts.check_every};
+    std::memcpy(sig.data() + sizeof a + sizeof f, extra, sizeof extra);
+    return sig;
+}
+
+// Builds the executable graph: while (cond) { K-1 steps; check step; finalize }.
+lbm_status build_graph(lbm_ctx* c, int parity) {
+    const int K = c->opts.check_every;
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(c, cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        c->poisoned = true;
+        return fail(c, LBM_ERR_CUDA, "cudaGraphConditionalHandleCreate: %s", cudaGetErrorString(e));
+    }
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        c->poisoned = true;
+        return fail(c, LBM_ERR_CUDA, "cudaGraphAddNode(conditional): %s", cudaGetErrorString(e));
+    }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        int src = parity;
+        for (int k = 0; k < K && e == cudaSuccess; ++k) {
+            e = launch_step(c, src, k == K - 1, c->cap_stream);
+            src ^= 1;
+        }
+        if (e == cudaSuccess) {
+            lbm::FinalArgs f = final_args(c, K, K);
+            f.handle = h;
+            f.use_handle = 1;
+            lbm::finalize_kernel<<<1, lbm::kFinalThreads, 0, c->cap_stream>>>(f);
+            e = cudaGetLastError();
+        }
+        cudaGraph_t captured = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &captured);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->gexec[parity] = nullptr;
+        c->poisoned = true;
+        return fail(c, LBM_ERR_CUDA, "building the check-interval graph failed: %s",
+                    cudaGetErrorString(e));
+    }
+    c->g_interval = K;
+    c->gsig[parity] = graph_signature(c, parity);
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_opts(lbm_solve_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->t_hot = 1.0;
+    o->t_cold = 0.0;
+    o->tau_max = 1.5;
+    o->lattice_scale = 0.0;
+    o->tol = 1e-8;
+    o->max_iters = 50000000LL;
+    o->check_every = 100;
+    o->stall_checks = 0;
+    o->storage = LBM_STORE_F32;
+    o->t_init = nullptr;
+    o->stream = nullptr;
+}
+
+lbm_status lbm_create(int nx, int ny, int nz, int cuda_device, lbm_ctx** out) {
+    if (!out) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (nx < 2 || ny < 2 || nz < 2) return LBM_ERR_INVALID_ARG;
+    const long long N = (long long)nx * ny * nz;
+    if (N >= (1LL << 31)) return LBM_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cuda_device < 0 || cuda_device >= ndev) {
+        cudaGetLastError();
+        return LBM_ERR_INVALID_ARG;
+    }
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return LBM_ERR_OUT_OF_MEMORY;
+    c->n[0] = nx;
+    c->n[1] = ny;
+    c->n[2] = nz;
+    c->device = cuda_device;
+    lbm_default_opts(&c->opts);
+    bool ok = cudaSetDevice(cuda_device) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaMalloc((void**)&c->d_phase, (size_t)N) == cudaSuccess &&
+              cudaMalloc((void**)&c->d_T, sizeof(float) * (size_t)N) == cudaSuccess &&
+              cudaMalloc((void**)&c->d_ctl, sizeof(Ctl)) == cudaSuccess &&
+              cudaMallocHost((void**)&c->h_ctl, sizeof(Ctl)) == cudaSuccess &&
+              cudaEventCreate(&c->ev0) == cudaSuccess && cudaEventCreate(&c->ev1) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        lbm_destroy(c);
+        return LBM_ERR_OUT_OF_MEMORY;
+    }
+    std::memset(c->h_ctl, 0, sizeof(Ctl));
+    *out = c;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* phase, int n_phases) {
+    CHECK_CTX(c);
+    if (!phase) return fail(c, LBM_ERR_INVALID_ARG, "phase is NULL");
+    if (n_phases < 1 || n_phases > 255) return fail(c, LBM_ERR_INVALID_ARG, "n_phases must be in [1, 255]");
+    const size_t N = (size_t)c->n[0] * c->n[1] * c->n[2];
+    for (size_t i = 0; i < N; ++i)
+        if (phase[i] >= n_phases)
+            return fail(c, LBM_ERR_INVALID_ARG, "phase id %d at voxel %zu is >= n_phases %d",
+                        (int)phase[i], i, n_phases);
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    CUDA_TRY(c, cudaMemcpy(c->d_phase, phase, N, cudaMemcpyHostToDevice));
+    if (c->have_tensors && (int)c->lambda.size() != 6 * n_phases) c->have_tensors = false;
+    c->n_phases = n_phases;
+    c->have_geometry = true;
+    c->started = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_tensors(lbm_ctx* c, const double* lambda, int n_phases) {
+    CHECK_CTX(c);
+    if (!lambda) return fail(c, LBM_ERR_INVALID_ARG, "lambda is NULL");
+    if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "set the geometry before the tensors");
+    if (n_phases != c->n_phases)
+        return fail(c, LBM_ERR_INVALID_ARG, "n_phases %d does not match the geometry's %d", n_phases,
+                    c->n_phases);
+    for (int p = 0; p < n_phases; ++p) {
+        for (int k = 0; k < 6; ++k)
+            if (!std::isfinite(lambda[6 * p + k]))
+                return fail(c, LBM_ERR_INVALID_ARG, "tensor of phase %d is not finite", p);
+        if (!spd6(lambda + 6 * p))
+            return fail(c, LBM_ERR_INVALID_ARG, "tensor of phase %d is not positive definite", p);
+    }
+    c->lambda.assign(lambda, lambda + 6 * n_phases);
+    c->have_tensors = true;
+    c->started = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_solve_opts* o) {
+    CHECK_CTX(c);
+    if (!c->have_geometry || !c->have_tensors)
+        return fail(c, LBM_ERR_STATE, "set geometry and tensors before starting a solve");
+    if (axis < LBM_AXIS_X || axis > LBM_AXIS_Z) return fail(c, LBM_ERR_INVALID_ARG, "bad axis");
+    if (lateral != LBM_LATERAL_PERIODIC && lateral != LBM_LATERAL_ADIABATIC)
+        return fail(c, LBM_ERR_INVALID_ARG, "bad lateral type");
+    lbm_solve_opts op;
+    if (o) op = *o;
+    else lbm_default_opts(&op);
+    if (!(op.t_hot != op.t_cold) || !std::isfinite(op.t_hot) || !std::isfinite(op.t_cold))
+        return fail(c, LBM_ERR_INVALID_ARG, "t_hot and t_cold must be finite and differ");
+    if (op.check_every < 2 || (op.check_every & 1))
+        return fail(c, LBM_ERR_INVALID_ARG, "check_every must be even and >= 2");
+    if (op.max_iters < 0) return fail(c, LBM_ERR_INVALID_ARG, "max_iters must be >= 0");
+    if (op.storage != LBM_STORE_F32) return fail(c, LBM_ERR_INVALID_ARG, "unsupported storage");
+    if (!(op.lattice_scale > 0.0) && !(op.tau_max > 0.5))
+        return fail(c, LBM_ERR_INVALID_ARG, "tau_max must exceed 1/2");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+
+    // lattice scale and S_b = tau^-1 per phase (Eq. 12-13), FP64 on the host
+    const double eps = 0.25;
+    double s = op.lattice_scale;
+    if (!(s > 0.0)) {
+        double m = 0.0;
+        for (int p = 0; p < c->n_phases; ++p)
+            for (int k = 0; k < 3; ++k) m = std::fmax(m, c->lambda[6 * p + k]);
+        s = eps * (op.tau_max - 0.5) / m;
+    }
+    // canonical layout: new axis i is old axis perm[i], Dirichlet axis last
+    static const int perms[3][3] = {{1, 2, 0}, {2, 0, 1}, {0, 1, 2}};
+    Layout L;
+    for (int i = 0; i < 3; ++i) {
+        L.n[i] = c->n[i];
+        L.perm[i] = perms[axis][i];
+    }
+    L.NX = c->n[L.perm[0]];
+    L.NY = c->n[L.perm[1]];
+    L.NZ = c->n[L.perm[2]];
+    L.pitch = (L.NX + 3) & ~3;
+    std::vector<float4> sb(2 * (size_t)c->n_phases);
+    for (int p = 0; p < c->n_phases; ++p) {
+        const double* t = &c->lambda[6 * p];
+        const double full[9] = {t[0], t[5], t[4], t[5], t[1], t[3], t[4], t[3], t[2]};
+        double lam[9], tau[9], S[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) lam[3 * i + j] = full[3 * L.perm[i] + L.perm[j]];
+        for (int k = 0; k < 9; ++k) tau[k] = s * lam[k] / eps;
+        tau[0] += 0.5;
+        tau[4] += 0.5;
+        tau[8] += 0.5;
+        inv3(tau, S);
+        sb[2 * p] = make_float4((float)S[0], (float)S[4], (float)S[8], (float)S[5]);
+        sb[2 * p + 1] = make_float4((float)S[2], (float)S[1], 0.f, 0.f);
+    }
+
+    // buffers
+    const long long cells = (long long)L.pitch * L.NY * L.NZ;
+    lbm_status st;
+    if ((st = ensure(c, &c->d_f[0], (size_t)(7 * cells), &c->cap_f[0])) != LBM_OK) return st;
+    if ((st = ensure(c, &c->d_f[1], (size_t)(7 * cells), &c->cap_f[1])) != LBM_OK) return st;
+    if ((st = ensure(c, &c->d_phase_c, (size_t)cells, &c->cap_phase_c)) != LBM_OK) return st;
+    size_t cap_sb = (size_t)c->cap_sb;
+    if ((st = ensure(c, &c->d_sb, sb.size(), &cap_sb)) != LBM_OK) return st;
+    c->cap_sb = (int)cap_sb;
+    const int quads = (L.pitch / 4) * L.NY;
+    c->blocks_per_plane = (quads + lbm::kThreads - 1) / lbm::kThreads;
+    if ((st = ensure(c, &c->d_part, (size_t)3 * L.NZ * c->blocks_per_plane, &c->cap_part)) != LBM_OK)
+        return st;
+    size_t capQ = (size_t)c->cap_Q;
+    if ((st = ensure(c, &c->d_Q, (size_t)L.NZ, &capQ)) != LBM_OK) return st;
+    c->cap_Q = (int)capQ;
+    c->Q_host.assign(L.NZ, 0.0);
+
+    c->opts = op;
+    c->axis = axis;
+    c->lateral = lateral;
+    c->L = L;
+    c->s = s;
+    c->t_ref = 0.5 * (op.t_hot + op.t_cold);
+    c->pstride = cells;
+    c->stream = op.stream ? (cudaStream_t)op.stream : c->own_stream;
+    c->cur = 0;
+    c->have_k = false;
+    c->k_eff = NAN;
+
+    cudaStream_t stm = c->stream;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_sb, sb.data(), sizeof(float4) * sb.size(),
+                                cudaMemcpyHostToDevice, stm));
+    lbm::permute_phase_kernel<<<grid_1d(cells), 256, 0, stm>>>(c->d_phase, c->d_phase_c, L);
+    CUDA_TRY(c, cudaGetLastError());
+    const float* tinit = nullptr;
+    if (op.t_init) {
+        const size_t N = (size_t)c->n[0] * c->n[1] * c->n[2];
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_T, op.t_init, sizeof(float) * N, cudaMemcpyHostToDevice, stm));
+        tinit = c->d_T;
+    }
+    lbm::init_kernel<<<grid_1d(cells), 256, 0, stm>>>(c->d_f[0], cells, L, (float)op.t_hot,
+                                                      (float)op.t_cold, (float)c->t_ref, tinit);
+    CUDA_TRY(c, cudaGetLastError());
+    Ctl h{};
+    h.best_rt = INFINITY;
+    h.k_eff = NAN;
+    h.r_t = NAN;
+    h.r_q = NAN;
+    h.status = LBM_ERR_NOT_CONVERGED;
+    *c->h_ctl = h;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_ctl, c->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, stm));
+    CUDA_TRY(c, cudaStreamSynchronize(stm));
+    c->started = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_advance(lbm_ctx* c, int64_t n_steps) {
+    CHECK_CTX(c);
+    if (!c->started) return fail(c, LBM_ERR_STATE, "call lbm_start first");
+    if (n_steps < 0) return fail(c, LBM_ERR_INVALID_ARG, "n_steps must be >= 0");
+    if (n_steps == 0) return LBM_OK;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    for (int64_t k = 0; k < n_steps; ++k) {
+        CUDA_TRY(c, launch_step(c, c->cur, false, c->stream));
+        c->cur ^= 1;
+    }
+    lbm::add_iters_kernel<<<1, 1, 0, c->stream>>>(c->d_ctl, (long long)n_steps);
+    CUDA_TRY(c, cudaGetLastError());
+    return LBM_OK;
+}
+
+lbm_status lbm_check(lbm_ctx* c, lbm_solve_info* info) {
+    CHECK_CTX(c);
+    if (!c->started) return fail(c, LBM_ERR_STATE, "call lbm_start first");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    CUDA_TRY(c, cudaEventRecord(c->ev0, c->stream));
+    CUDA_TRY(c, launch_step(c, c->cur, true, c->stream));
+    c->cur ^= 1;
+    lbm::FinalArgs f = final_args(c, 1, c->opts.check_every);
+    lbm::finalize_kernel<<<1, lbm::kFinalThreads, 0, c->stream>>>(f);
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaEventRecord(c->ev1, c->stream));
+    lbm_status st = read_ctl(c, c->stream);
+    if (st != LBM_OK) return st;
+    float ms = 0.f;
+    CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    fill_info(c, info, ms);
+    return LBM_OK;
+}
+
+lbm_status lbm_run(lbm_ctx* c, lbm_solve_info* info) {
+    CHECK_CTX(c);
+    if (!c->started) return fail(c, LBM_ERR_STATE, "call lbm_start first");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const int K = c->opts.check_every;
+    // the stop rule needs the current iteration count
+    lbm_status st = read_ctl(c, c->stream);
+    if (st != LBM_OK) return st;
+    if (c->h_ctl->iter + K > c->opts.max_iters) {
+        fill_info(c, info, 0.0);
+        if (info) info->status = LBM_ERR_NOT_CONVERGED;
+        return fail(c, LBM_ERR_NOT_CONVERGED, "max_iters leaves no whole check interval to run");
+    }
+    // reuse the graph of an earlier solve when nothing it bakes in changed
+    if (!c->gexec[c->cur] || c->gsig[c->cur] != graph_signature(c, c->cur)) {
+        if (c->gexec[c->cur]) cudaGraphExecDestroy(c->gexec[c->cur]);
+        c->gexec[c->cur] = nullptr;
+        if ((st = build_graph(c, c->cur)) != LBM_OK) return st;
+    }
+    const long long iter0 = c->h_ctl->iter;
+    CUDA_TRY(c, cudaEventRecord(c->ev0, c->stream));
+    CUDA_TRY(c, cudaGraphLaunch(c->gexec[c->cur], c->stream));
+    CUDA_TRY(c, cudaEventRecord(c->ev1, c->stream));
+    if ((st = read_ctl(c, c->stream)) != LBM_OK) return st;
+    // K is even, so the state is back in the buffer it started from
+    float ms = 0.f;
+    CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    (void)iter0;
+    fill_info(c, info, ms);
+    const int s = c->h_ctl->status;
+    if (s == LBM_OK) return LBM_OK;
+    if (s == LBM_ERR_DIVERGED) return fail(c, LBM_ERR_DIVERGED, "non-finite residual or flux");
+    if (s == LBM_ERR_STALLED) return fail(c, LBM_ERR_STALLED, "residual stalled at %.3e", c->h_ctl->r_t);
+    return fail(c, LBM_ERR_NOT_CONVERGED, "max_iters reached with R_T = %.3e", c->h_ctl->r_t);
+}
+
+lbm_status lbm_solve(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_solve_opts* o,
+                     lbm_solve_info* info) {
+    lbm_status st = lbm_start(c, axis, lateral, o);
+    if (st != LBM_OK) return st;
+    return lbm_run(c, info);
+}
+
+lbm_status lbm_k_eff(const lbm_ctx* c, double* out) {
+    if (!c || !out) return LBM_ERR_INVALID_ARG;
+    if (c->poisoned) return LBM_ERR_CUDA;
+    if (!c->have_k) return LBM_ERR_STATE;
+    *out = c->k_eff;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_temperature(lbm_ctx* c, float* host_out) {
+    CHECK_CTX(c);
+    if (!host_out) return fail(c, LBM_ERR_INVALID_ARG, "host_out is NULL");
+    if (!c->started) return fail(c, LBM_ERR_STATE, "no solve state");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const long long N = (long long)c->n[0] * c->n[1] * c->n[2];
+    lbm::temperature_kernel<<<grid_1d(N), 256, 0, c->stream>>>(c->d_f[c->cur], c->pstride, c->L,
+                                                              (float)c->t_ref, c->d_T);
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaMemcpyAsync(host_out, c->d_T, sizeof(float) * N, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_plane_flux(const lbm_ctx* c, double* host_out, int n) {
+    if (!c || !host_out) return LBM_ERR_INVALID_ARG;
+    if (c->poisoned) return LBM_ERR_CUDA;
+    if (!c->have_k) return LBM_ERR_STATE;
+    if (n != c->L.NZ) return LBM_ERR_INVALID_ARG;
+    std::memcpy(host_out, c->Q_host.data(), sizeof(double) * n);
+    return LBM_OK;
+}
+
+lbm_status lbm_get_geometry(lbm_ctx* c, uint8_t* host_out) {
+    CHECK_CTX(c);
+    if (!host_out) return fail(c, LBM_ERR_INVALID_ARG, "host_out is NULL");
+    if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "no geometry set");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const size_t N = (size_t)c->n[0] * c->n[1] * c->n[2];
+    CUDA_TRY(c, cudaMemcpy(host_out, c->d_phase, N, cudaMemcpyDeviceToHost));
+    return LBM_OK;
+}
+
+const char* lbm_last_error(const lbm_ctx* c) {
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_graphs(c);
+    cudaFree(c->d_f[0]);
+    cudaFree(c->d_f[1]);
+    cudaFree(c->d_phase_c);
+    cudaFree(c->d_sb);
+    cudaFree(c->d_part);
+    cudaFree(c->d_Q);
+    cudaFree(c->d_T);
+    cudaFree(c->d_phase);
+    cudaFree(c->d_ctl);
+    if (c->h_ctl) cudaFreeHost(c->h_ctl);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    cudaGetLastError();
+    delete c;
+}
+
+// Internal hooks for the voxeliser translation unit (hidden, not part of the ABI).
+#define LBM_HIDDEN __attribute__((visibility("hidden")))
+LBM_HIDDEN uint8_t* lbm__device_phase(lbm_ctx* c) { return c ? c->d_phase : nullptr; }
+LBM_HIDDEN int lbm__dims(const lbm_ctx* c, int* n) {
+    if (!c) return -1;
+    n[0] = c->n[0]; n[1] = c->n[1]; n[2] = c->n[2];
+    return c->device;
+}
+LBM_HIDDEN void lbm__set_phase_count(lbm_ctx* c, int n_phases) {
+    if (c->have_tensors && (int)c->lambda.size() != 6 * n_phases) c->have_tensors = false;
+    c->n_phases = n_phases;
+    c->have_geometry = true;
+    c->started = false;
+}
+LBM_HIDDEN void lbm__set_error(lbm_ctx* c, const char* msg) { if (c) c->err = msg; }
+LBM_HIDDEN int lbm__poisoned(const lbm_ctx* c) { return c ? (c->poisoned ? 1 : 0) : 1; }
+LBM_HIDDEN void lbm__poison(lbm_ctx* c) { if (c) c->poisoned = true; }
+
+}  // extern "C"

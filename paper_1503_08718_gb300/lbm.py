@@ -1,0 +1,292 @@
+"""Python binding of the C ABI in include/lbm.h (ctypes, marshalling only).
+
+Every function here has the name of the C entry point it wraps and does
+nothing but convert arguments; all computation runs in libmrtlbm.so's CUDA
+kernels.  Loading fails loudly if the library has not been built: there is no
+CPU fallback.
+
+`Solver` is a thin convenience object over the same calls (it owns one
+context and raises `LBMError` on a non-zero status).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_build", "libmrtlbm.so")
+
+LBM_OK = 0
+LBM_ERR_INVALID_ARG = 1
+LBM_ERR_STATE = 2
+LBM_ERR_CUDA = 3
+LBM_ERR_OUT_OF_MEMORY = 4
+LBM_ERR_NOT_CONVERGED = 5
+LBM_ERR_DIVERGED = 6
+LBM_ERR_STALLED = 7
+LBM_ERR_TIMEOUT = 8
+LBM_ERR_INTERNAL = 9
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "STATE", 3: "CUDA", 4: "OUT_OF_MEMORY",
+                5: "NOT_CONVERGED", 6: "DIVERGED", 7: "STALLED", 8: "TIMEOUT", 9: "INTERNAL"}
+
+LBM_AXIS_X, LBM_AXIS_Y, LBM_AXIS_Z = 0, 1, 2
+LBM_LATERAL_PERIODIC, LBM_LATERAL_ADIABATIC = 0, 1
+LBM_STORE_F32 = 0
+
+
+class lbm_solve_opts(ctypes.Structure):
+    _fields_ = [("t_hot", ctypes.c_double), ("t_cold", ctypes.c_double),
+                ("tau_max", ctypes.c_double), ("lattice_scale", ctypes.c_double),
+                ("tol", ctypes.c_double), ("max_iters", ctypes.c_int64),
+                ("check_every", ctypes.c_int32), ("stall_checks", ctypes.c_int32),
+                ("storage", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("t_init", ctypes.POINTER(ctypes.c_float)), ("stream", ctypes.c_void_p)]
+
+
+class lbm_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("k_eff", ctypes.c_double),
+                ("residual_T", ctypes.c_double), ("residual_Q", ctypes.c_double),
+                ("elapsed_ms", ctypes.c_double), ("lattice_scale", ctypes.c_double),
+                ("status", ctypes.c_int32), ("checks", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_ctx_p = ctypes.c_void_p
+_PROTOS = {
+    "lbm_default_opts": (None, [ctypes.POINTER(lbm_solve_opts)]),
+    "lbm_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  ctypes.POINTER(_ctx_p)]),
+    "lbm_set_geometry": (ctypes.c_int, [_ctx_p, ctypes.POINTER(ctypes.c_uint8), ctypes.c_int]),
+    "lbm_set_tensors": (ctypes.c_int, [_ctx_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    "lbm_start": (ctypes.c_int, [_ctx_p, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(lbm_solve_opts)]),
+    "lbm_advance": (ctypes.c_int, [_ctx_p, ctypes.c_int64]),
+    "lbm_check": (ctypes.c_int, [_ctx_p, ctypes.POINTER(lbm_solve_info)]),
+    "lbm_run": (ctypes.c_int, [_ctx_p, ctypes.POINTER(lbm_solve_info)]),
+    "lbm_solve": (ctypes.c_int, [_ctx_p, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(lbm_solve_opts), ctypes.POINTER(lbm_solve_info)]),
+    "lbm_k_eff": (ctypes.c_int, [_ctx_p, ctypes.POINTER(ctypes.c_double)]),
+    "lbm_get_temperature": (ctypes.c_int, [_ctx_p, ctypes.POINTER(ctypes.c_float)]),
+    "lbm_get_plane_flux": (ctypes.c_int, [_ctx_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    "lbm_set_geometry_braid": (ctypes.c_int, [_ctx_p, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.c_int, ctypes.c_double,
+                                              ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_double)]),
+    "lbm_get_geometry": (ctypes.c_int, [_ctx_p, ctypes.POINTER(ctypes.c_uint8)]),
+    "lbm_last_error": (ctypes.c_char_p, [_ctx_p]),
+    "lbm_destroy": (None, [_ctx_p]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Loads libmrtlbm.so (raises if it is missing: build it with build.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} is missing "
+                               "(run paper_1503_08718_gb300.build.build())")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _PROTOS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _f64(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ---- one function per C entry point -------------------------------------
+
+def lbm_default_opts() -> lbm_solve_opts:
+    o = lbm_solve_opts()
+    load().lbm_default_opts(ctypes.byref(o))
+    return o
+
+
+def lbm_create(nx: int, ny: int, nz: int, cuda_device: int = 0):
+    h = _ctx_p()
+    st = load().lbm_create(nx, ny, nz, cuda_device, ctypes.byref(h))
+    return st, h
+
+
+def lbm_set_geometry(ctx, phase: np.ndarray, n_phases: int) -> int:
+    phase = np.ascontiguousarray(phase, dtype=np.uint8)
+    return load().lbm_set_geometry(ctx, phase.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                   int(n_phases))
+
+
+def lbm_set_tensors(ctx, lam: np.ndarray, n_phases: int) -> int:
+    lam = np.ascontiguousarray(lam, dtype=np.float64).reshape(-1)
+    return load().lbm_set_tensors(ctx, _f64(lam), int(n_phases))
+
+
+def lbm_start(ctx, axis: int, lateral: int, opts: lbm_solve_opts | None = None) -> int:
+    return load().lbm_start(ctx, axis, lateral, ctypes.byref(opts) if opts is not None else None)
+
+
+def lbm_advance(ctx, n_steps: int) -> int:
+    return load().lbm_advance(ctx, int(n_steps))
+
+
+def lbm_check(ctx, info: lbm_solve_info | None = None) -> int:
+    return load().lbm_check(ctx, ctypes.byref(info) if info is not None else None)
+
+
+def lbm_run(ctx, info: lbm_solve_info | None = None) -> int:
+    return load().lbm_run(ctx, ctypes.byref(info) if info is not None else None)
+
+
+def lbm_solve(ctx, axis: int, lateral: int, opts: lbm_solve_opts | None = None,
+              info: lbm_solve_info | None = None) -> int:
+    return load().lbm_solve(ctx, axis, lateral,
+                            ctypes.byref(opts) if opts is not None else None,
+                            ctypes.byref(info) if info is not None else None)
+
+
+def lbm_k_eff(ctx):
+    out = ctypes.c_double(0.0)
+    st = load().lbm_k_eff(ctx, ctypes.byref(out))
+    return st, out.value
+
+
+def lbm_get_temperature(ctx, out: np.ndarray) -> int:
+    assert out.dtype == np.float32 and out.flags.c_contiguous
+    return load().lbm_get_temperature(ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+
+
+def lbm_get_plane_flux(ctx, out: np.ndarray) -> int:
+    assert out.dtype == np.float64 and out.flags.c_contiguous
+    return load().lbm_get_plane_flux(ctx, _f64(out), out.size)
+
+
+def lbm_set_geometry_braid(ctx, g_rad: float, A: float, B: float, anchors: np.ndarray,
+                           phi: float):
+    anchors = np.ascontiguousarray(anchors, dtype=np.float64).reshape(-1, 2)
+    used = ctypes.c_int(0)
+    frac = ctypes.c_double(0.0)
+    st = load().lbm_set_geometry_braid(ctx, g_rad, A, B, _f64(anchors.reshape(-1)),
+                                       anchors.shape[0], phi, ctypes.byref(used),
+                                       ctypes.byref(frac))
+    return st, used.value, frac.value
+
+
+def lbm_get_geometry(ctx, out: np.ndarray) -> int:
+    assert out.dtype == np.uint8 and out.flags.c_contiguous
+    return load().lbm_get_geometry(ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+
+
+def lbm_last_error(ctx) -> str:
+    s = load().lbm_last_error(ctx)
+    return s.decode() if s else ""
+
+
+def lbm_destroy(ctx) -> None:
+    load().lbm_destroy(ctx)
+
+
+# ---- convenience object ---------------------------------------------------
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Solver:
+    """One solver context for an (nz, ny, nx) cell on one CUDA device."""
+
+    def __init__(self, nx: int, ny: int, nz: int, device: int = 0):
+        st, h = lbm_create(nx, ny, nz, device)
+        if st != LBM_OK:
+            raise LBMError(st, f"lbm_create({nx}, {ny}, {nz}, {device}) failed")
+        self.h = h
+        self.shape = (nz, ny, nx)
+
+    def _ok(self, st: int, allow=()) -> int:
+        if st != LBM_OK and st not in allow:
+            raise LBMError(st, lbm_last_error(self.h))
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_geometry(self, phase, n_phases):
+        self._ok(lbm_set_geometry(self.h, phase, n_phases))
+
+    def set_tensors(self, lam):
+        lam = np.asarray(lam, dtype=np.float64).reshape(-1, 6)
+        self._ok(lbm_set_tensors(self.h, lam, lam.shape[0]))
+
+    def set_geometry_braid(self, g_rad, anchors, phi, A=10.0, B=6.0):
+        st, used, frac = lbm_set_geometry_braid(self.h, g_rad, A, B, anchors, phi)
+        self._ok(st)
+        return used, frac
+
+    def geometry(self):
+        out = np.empty(self.shape, np.uint8)
+        self._ok(lbm_get_geometry(self.h, out))
+        return out
+
+    @staticmethod
+    def opts(**kw) -> lbm_solve_opts:
+        o = lbm_default_opts()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+
+    def start(self, axis=2, lateral=0, opts=None):
+        self._ok(lbm_start(self.h, axis, lateral, opts))
+
+    def advance(self, n):
+        self._ok(lbm_advance(self.h, n))
+
+    def check(self) -> lbm_solve_info:
+        info = lbm_solve_info()
+        self._ok(lbm_check(self.h, info))
+        return info
+
+    def run(self, allow=(LBM_ERR_NOT_CONVERGED,)) -> lbm_solve_info:
+        info = lbm_solve_info()
+        self._ok(lbm_run(self.h, info), allow)
+        return info
+
+    def solve(self, axis=2, lateral=0, opts=None, allow=(LBM_ERR_NOT_CONVERGED,)):
+        info = lbm_solve_info()
+        self._ok(lbm_solve(self.h, axis, lateral, opts, info), allow)
+        return info
+
+    def k_eff(self) -> float:
+        st, k = lbm_k_eff(self.h)
+        self._ok(st)
+        return k
+
+    def temperature(self, out: np.ndarray | None = None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self.shape, np.float32)
+        self._ok(lbm_get_temperature(self.h, out))
+        return out
+
+    def plane_flux(self, n_axis: int) -> np.ndarray:
+        out = np.empty(n_axis, np.float64)
+        self._ok(lbm_get_plane_flux(self.h, out))
+        return out

@@ -1,0 +1,258 @@
+"""GPU-vs-oracle parity through the C ABI (FP32 CUDA path vs FP64 oracle).
+
+Tolerances: temperature max |dT| <= 1e-5 and k_eff relative 1e-5, the bars
+the FP32 path is held to; the voxeliser must match bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1503_08718_gb300 import inputs as I
+from paper_1503_08718_gb300 import lbm
+
+pytestmark = pytest.mark.gpu
+
+T_TOL = 1e-5
+K_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1503_08718_gb300 import build
+    build.build()
+    lbm.load()
+
+
+def _oracle(phase, lam, axis, lateral, s, n, t_hot=1.0, t_cold=0.0):
+    L = O.Lattice(phase, lam, s, axis, lateral, t_hot, t_cold)
+    L.init_linear()
+    L.step(n)
+    return L
+
+
+def _gpu_at(phase, lam, axis, lateral, n, **opts):
+    nz, ny, nx = phase.shape
+    S = lbm.Solver(nx, ny, nz)
+    S.set_geometry(phase, lam.shape[0])
+    S.set_tensors(lam)
+    S.start(axis, lateral, S.opts(**opts))
+    S.advance(n - 1)
+    info = S.check()
+    return S, info
+
+
+CASES = [
+    # (nx, ny, nz) chosen for ragged rows (nx % 4 != 0), several blocks per
+    # plane and odd sizes; every axis and both lateral types
+    ((37, 60, 9), 2, 0), ((37, 60, 9), 2, 1),
+    ((13, 10, 22), 0, 0), ((13, 10, 22), 0, 1),
+    ((18, 7, 11), 1, 0), ((18, 7, 11), 1, 1),
+    ((2, 2, 2), 2, 1), ((5, 3, 4), 1, 0),
+]
+
+
+@pytest.mark.parametrize("shape,axis,lateral", CASES)
+@pytest.mark.parametrize("n", [1, 10, 300])
+def test_fixed_iteration_parity(shape, axis, lateral, n):
+    nx, ny, nz = shape
+    rng = np.random.default_rng(hash((shape, axis, lateral)) & 0xffff)
+    lam = np.stack([I.random_spd(rng) for _ in range(3)])
+    phase = I.random_phase(rng, nx, ny, nz, 3)
+    S, info = _gpu_at(phase, lam, axis, lateral, n)
+    ref = _oracle(phase, lam, axis, lateral, info.lattice_scale, n)
+    assert info.iters == n
+    T = S.temperature()
+    assert np.max(np.abs(T - ref.temperature())) <= T_TOL
+    k_ref, _ = ref.k_eff()
+    assert info.k_eff == pytest.approx(k_ref, rel=K_TOL, abs=1e-7)
+    Q = S.plane_flux(shape[axis])
+    Q_ref = ref.plane_flux()
+    assert np.max(np.abs(Q - Q_ref)) <= K_TOL * np.max(np.abs(Q_ref)) + 1e-7
+    S.close()
+
+
+def test_nondefault_walls_and_scale():
+    rng = np.random.default_rng(11)
+    lam = np.stack([I.random_spd(rng) for _ in range(2)])
+    phase = I.random_phase(rng, 9, 6, 7, 2)
+    S, info = _gpu_at(phase, lam, 2, 1, 50, t_hot=0.3, t_cold=-1.7, lattice_scale=0.02)
+    assert info.lattice_scale == 0.02
+    ref = _oracle(phase, lam, 2, 1, 0.02, 50, 0.3, -1.7)
+    assert np.max(np.abs(S.temperature() - ref.temperature())) <= T_TOL * 2
+    assert info.k_eff == pytest.approx(ref.k_eff()[0], rel=K_TOL)
+
+
+def test_config1_layered_cell_converges_to_the_closed_form():
+    """32^3 layered cell (8-voxel z-layers), matrix 0.2, yarn 6.0/0.8 at 30 deg
+    from z in xz, T = 1/0 on z, periodic x/y, stop at R_T <= 1e-8.  The
+    oracle is run on a 2x2x32 column for the same iteration count: periodic
+    laterals make the 32^3 field independent of x and y."""
+    yarn = I.transversely_isotropic(6.0, 0.8, I.axis_in_xz_from_z(30.0))
+    lam = np.stack([I.isotropic(0.2), yarn])
+    phase = I.layered_phase(32, 32, 32)
+    S = lbm.Solver(32, 32, 32)
+    S.set_geometry(phase, 2)
+    S.set_tensors(lam)
+    info = S.solve(2, 0, S.opts(tol=1e-8, max_iters=2_000_000), allow=())
+    assert info.status == lbm.LBM_OK and info.residual_T <= 1e-8
+    ref = _oracle(I.layered_phase(2, 2, 32), lam, 2, 0, info.lattice_scale, info.iters)
+    k_ref = ref.k_eff()[0]
+    assert info.k_eff == pytest.approx(k_ref, rel=K_TOL)
+    T = S.temperature()
+    assert np.max(np.abs(T - ref.temperature()[:, :1, :1])) <= T_TOL
+    # the converged value approaches the exact fixed point 94/245
+    assert info.k_eff == pytest.approx(94.0 / 245.0, rel=2e-3)
+
+
+def test_graph_run_equals_explicit_steps():
+    rng = np.random.default_rng(5)
+    lam = np.stack([I.random_spd(rng) for _ in range(4)])
+    phase = I.random_phase(rng, 20, 12, 16, 4)
+    A = lbm.Solver(20, 12, 16)
+    A.set_geometry(phase, 4)
+    A.set_tensors(lam)
+    A.start(0, 1, A.opts(check_every=10, tol=0.0, max_iters=30))
+    info = A.run()
+    assert info.iters == 30 and info.checks == 3
+    B = lbm.Solver(20, 12, 16)
+    B.set_geometry(phase, 4)
+    B.set_tensors(lam)
+    B.start(0, 1, B.opts(check_every=10))
+    for _ in range(3):
+        B.advance(9)
+        ib = B.check()
+    assert np.array_equal(A.temperature(), B.temperature())
+    assert ib.k_eff == info.k_eff and ib.residual_T == info.residual_T
+
+
+def test_warm_start_from_converged_field_stops_immediately():
+    yarn = I.transversely_isotropic(6.0, 0.8, I.axis_in_xz_from_z(30.0))
+    lam = np.stack([I.isotropic(0.2), yarn])
+    phase = I.layered_phase(8, 8, 32)
+    S = lbm.Solver(8, 8, 32)
+    S.set_geometry(phase, 2)
+    S.set_tensors(lam)
+    first = S.solve(2, 0, S.opts(tol=1e-8, max_iters=2_000_000), allow=())
+    T = np.ascontiguousarray(S.temperature())
+    o = S.opts(tol=1e-6)
+    o.t_init = T.ctypes.data_as(lbm.ctypes.POINTER(lbm.ctypes.c_float))
+    warm = S.solve(2, 0, o, allow=())
+    assert warm.iters < first.iters // 10
+    assert warm.k_eff == pytest.approx(first.k_eff, rel=1e-3)
+
+
+def test_deterministic_repeat():
+    rng = np.random.default_rng(8)
+    lam = np.stack([I.random_spd(rng) for _ in range(3)])
+    phase = I.random_phase(rng, 24, 24, 24, 3)
+    out = []
+    for _ in range(2):
+        S = lbm.Solver(24, 24, 24)
+        S.set_geometry(phase, 3)
+        S.set_tensors(lam)
+        info = S.solve(1, 0, S.opts(tol=0.0, max_iters=200))
+        out.append((S.temperature(), info.k_eff, info.residual_T))
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1:] == out[1][1:]
+
+
+def test_braid_voxeliser_bit_exact_at_full_size():
+    """The 128x128x256 braided cell (g = 30 deg, yarn fraction 0.45, seed 42)
+    voxelised on the device equals the oracle's voxelisation byte for byte."""
+    nx, ny, nz = 128, 128, 256
+    anchors = I.braid_anchors(nx, ny, 42, n_max=128)
+    g = math.radians(30.0)
+    S = lbm.Solver(nx, ny, nz)
+    used, frac = S.set_geometry_braid(g, anchors, 0.45)
+    ph_gpu = S.geometry()
+    ph_ref, used_ref, frac_ref = O.braid_phase(nx, ny, nz, g, anchors, 0.45)
+    assert used == used_ref and frac == frac_ref
+    assert np.array_equal(ph_gpu, ph_ref)
+
+
+def test_full_size_braid_parity_sampled():
+    """The bench workload itself (128x128x256 braid, z axis, periodic) in the
+    same launch configuration, compared with the FP64 oracle after 20
+    iterations on every voxel, plus plane fluxes and k_eff."""
+    nx, ny, nz = 128, 128, 256
+    anchors = I.braid_anchors(nx, ny, 42, n_max=128)
+    g = math.radians(30.0)
+    lam = I.braid_tensors(30.0)
+    S = lbm.Solver(nx, ny, nz)
+    S.set_geometry_braid(g, anchors, 0.45)
+    S.set_tensors(lam)
+    S.start(2, 0)
+    S.advance(19)
+    info = S.check()
+    ph = S.geometry()
+    ref = _oracle(ph, lam, 2, 0, info.lattice_scale, 20)
+    assert np.max(np.abs(S.temperature() - ref.temperature())) <= T_TOL
+    assert info.k_eff == pytest.approx(ref.k_eff()[0], rel=K_TOL)
+
+
+@pytest.mark.parametrize("axis,lateral", [(0, 1), (1, 0)])
+def test_braid_other_axes_sampled(axis, lateral):
+    nx, ny, nz = 64, 64, 96
+    anchors = I.braid_anchors(nx, ny, 7, n_max=64)
+    lam = I.braid_tensors(35.0)
+    S = lbm.Solver(nx, ny, nz)
+    S.set_geometry_braid(math.radians(35.0), anchors, 0.4)
+    S.set_tensors(lam)
+    S.start(axis, lateral)
+    S.advance(49)
+    info = S.check()
+    ref = _oracle(S.geometry(), lam, axis, lateral, info.lattice_scale, 50)
+    assert np.max(np.abs(S.temperature() - ref.temperature())) <= T_TOL
+    assert info.k_eff == pytest.approx(ref.k_eff()[0], rel=K_TOL)
+
+
+def test_invalid_inputs_are_rejected():
+    S = lbm.Solver(8, 8, 8)
+    with pytest.raises(lbm.LBMError) as e:
+        S.set_tensors(np.stack([I.isotropic(1.0)]))
+    assert e.value.status == lbm.LBM_ERR_STATE
+    bad = np.zeros((8, 8, 8), np.uint8)
+    bad[3, 3, 3] = 2
+    with pytest.raises(lbm.LBMError) as e:
+        S.set_geometry(bad, 2)
+    assert e.value.status == lbm.LBM_ERR_INVALID_ARG
+    S.set_geometry(np.zeros((8, 8, 8), np.uint8), 1)
+    with pytest.raises(lbm.LBMError) as e:
+        S.set_tensors(I.sym6(np.diag([1.0, -1.0, 1.0]))[None])
+    assert e.value.status == lbm.LBM_ERR_INVALID_ARG
+    with pytest.raises(lbm.LBMError):
+        S.set_tensors(np.stack([I.isotropic(1.0)] * 2))
+    with pytest.raises(lbm.LBMError) as e:
+        S.advance(3)
+    assert e.value.status == lbm.LBM_ERR_STATE
+    S.set_tensors(I.isotropic(1.0)[None])
+    with pytest.raises(lbm.LBMError):
+        S.start(2, 0, S.opts(check_every=7))
+    with pytest.raises(lbm.LBMError):
+        S.start(2, 0, S.opts(t_hot=1.0, t_cold=1.0))
+    with pytest.raises(lbm.LBMError):
+        S.set_geometry_braid(0.0, np.zeros((4, 2)), 0.1)
+    # not converged: status reported, k_eff still readable
+    info = S.solve(2, 0, S.opts(tol=0.0, max_iters=200))
+    assert info.status == lbm.LBM_ERR_NOT_CONVERGED and info.iters == 200
+    assert np.isfinite(S.k_eff())
+
+
+def test_nonfinite_tensor_rejected_and_not_run():
+    S = lbm.Solver(4, 4, 4)
+    S.set_geometry(np.zeros((4, 4, 4), np.uint8), 1)
+    with pytest.raises(lbm.LBMError):
+        S.set_tensors(np.array([[np.nan, 1, 1, 0, 0, 0]]))
+
+
+def test_max_phase_count():
+    rng = np.random.default_rng(2)
+    lam = np.stack([I.random_spd(rng) for _ in range(255)])
+    phase = I.random_phase(rng, 16, 16, 12, 255)
+    S, info = _gpu_at(phase, lam, 2, 0, 5)
+    ref = _oracle(phase, lam, 2, 0, info.lattice_scale, 5)
+    assert np.max(np.abs(S.temperature() - ref.temperature())) <= T_TOL
