@@ -67,7 +67,7 @@ typedef struct {
     double lattice_scale;   /* > 0 overrides tau_max: D = lattice_scale * lambda */
     double tol;             /* stop when R_T <= tol at a check (default 1e-8) */
     int64_t max_iters;      /* iteration cap (default 50 000 000) */
-    int32_t check_every;    /* K: steps per check interval, even, >= 2 (default 100) */
+    int32_t check_every;    /* K: steps per check interval, even, in [2, 4096] (default 100) */
     int32_t stall_checks;   /* stop with LBM_ERR_STALLED after this many checks
                                without a new smallest R_T; 0 disables (default 0) */
     int32_t storage;        /* lbm_storage; LBM_STORE_F32 */
@@ -110,6 +110,7 @@ lbm_status lbm_set_tensors(lbm_ctx* c, const double* lambda, int n_phases);
  * given lateral faces: computes s, tau and the relaxation block S_b = tau^-1
  * per phase (Eq. 12-13) in FP64, lays the cell out with `axis` slowest, and
  * writes the initial distributions f^eq(T0) (Eq. 6).  Iterations restart at 0.
+ * The axis must have at most 65535 nodes.
  * o may be NULL for defaults. */
 lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_solve_opts* o);
 

@@ -420,8 +420,8 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
     else lbm_default_opts(&op);
     if (!(op.t_hot != op.t_cold) || !std::isfinite(op.t_hot) || !std::isfinite(op.t_cold))
         return fail(c, LBM_ERR_INVALID_ARG, "t_hot and t_cold must be finite and differ");
-    if (op.check_every < 2 || (op.check_every & 1))
-        return fail(c, LBM_ERR_INVALID_ARG, "check_every must be even and >= 2");
+    if (op.check_every < 2 || (op.check_every & 1) || op.check_every > 4096)
+        return fail(c, LBM_ERR_INVALID_ARG, "check_every must be even and in [2, 4096]");
     if (op.max_iters < 0) return fail(c, LBM_ERR_INVALID_ARG, "max_iters must be >= 0");
     if (op.storage != LBM_STORE_F32) return fail(c, LBM_ERR_INVALID_ARG, "unsupported storage");
     if (!(op.lattice_scale > 0.0) && !(op.tau_max > 0.5))
@@ -448,6 +448,8 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
     L.NY = c->n[L.perm[1]];
     L.NZ = c->n[L.perm[2]];
     L.pitch = (L.NX + 3) & ~3;
+    if (L.NZ > 65535)
+        return fail(c, LBM_ERR_INVALID_ARG, "the temperature-difference axis may have at most 65535 nodes");
     std::vector<float4> sb(2 * (size_t)c->n_phases);
     for (int p = 0; p < c->n_phases; ++p) {
         const double* t = &c->lambda[6 * p];
