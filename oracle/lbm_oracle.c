@@ -439,9 +439,13 @@ int orc_k_eff(const orc_lbm *o, double *k_eff, double *r_q) {
     return 0;
 }
 
-/* Iterates until R_T = sum|T^n - T^(n-1)| / sum|T^n| <= tol at a check
- * (every check_every steps) or max_iters steps.  Returns 0 when converged,
- * 1 when max_iters was reached, -1 on a non-finite residual or an error. */
+/* Iterates in check intervals of check_every steps (the last one shortened
+ * by max_iters) until R_T <= tol at a check.  The paper states no stopping
+ * rule; the reading taken here is the mean per-step temperature change over
+ * the interval, relative to the field:
+ *     R_T = sum|T^n - T^(n-m)| / (m * sum|T^n|),  m = steps in the interval.
+ * Returns 0 when converged, 1 when max_iters was reached, -1 on a
+ * non-finite residual or an error. */
 int orc_solve(orc_lbm *o, double tol, int64_t check_every, int64_t max_iters,
               double *r_t_out) {
     const int64_t N = o->N;
@@ -450,19 +454,19 @@ int orc_solve(orc_lbm *o, double tol, int64_t check_every, int64_t max_iters,
     if (!Tp || !T) { free(Tp); free(T); return -1; }
     int rc = 1;
     double r_t = INFINITY;
+    orc_temperature(o, Tp);
     while (o->iter < max_iters) {
         int64_t left = max_iters - o->iter;
         int64_t run = check_every < left ? check_every : left;
-        orc_step(o, run - 1);
-        orc_temperature(o, Tp);
-        orc_step(o, 1);
+        orc_step(o, run);
         orc_temperature(o, T);
         double num = 0.0, den = 0.0;
         for (int64_t v = 0; v < N; ++v) {
             num += fabs(T[v] - Tp[v]);
             den += fabs(T[v]);
         }
-        r_t = num / den;
+        r_t = num / ((double)run * den);
+        double *t = Tp; Tp = T; T = t;
         if (!isfinite(r_t)) { rc = -1; break; }
         if (r_t <= tol) { rc = 0; break; }
     }
