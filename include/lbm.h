@@ -80,7 +80,8 @@ typedef struct {
 typedef struct {
     int64_t iters;          /* iterations performed since lbm_start */
     double k_eff;           /* Eq. 22 at the last check */
-    double residual_T;      /* R_T = sum|T^n - T^(n-1)| / sum|T^n| at the last check */
+    double residual_T;      /* R_T = sum|T^n - T^(n-m)| / (m sum|T^n|) at the last check,
+                               m = iterations since the previous check (or start) */
     double residual_Q;      /* R_Q = (max_k Q - min_k Q) / |mean Q| at the last check */
     double elapsed_ms;      /* device time of the call's iterations (CUDA events) */
     double lattice_scale;   /* s used */

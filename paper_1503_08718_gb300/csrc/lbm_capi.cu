@@ -46,6 +46,8 @@ struct lbm_ctx {
     int cur = 0;                           // buffer holding the current state
     uint8_t* d_phase_c = nullptr;          // canonical padded phase map
     size_t cap_phase_c = 0;
+    float* d_tsnap = nullptr;              // T - T_ref at the previous check (canonical)
+    size_t cap_tsnap = 0;
     float4* d_sb = nullptr;                // 2 float4 per phase
     int cap_sb = 0;
     double* d_part = nullptr;
@@ -155,6 +157,7 @@ lbm::StepArgs step_args(const lbm_ctx* c, int src) {
     a.phase = c->d_phase_c;
     a.sb = c->d_sb;
     a.part = c->d_part;
+    a.tsnap = c->d_tsnap;
     a.pstride = c->pstride;
     a.nx = c->L.NX;
     a.ny = c->L.NY;
@@ -472,6 +475,7 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
     if ((st = ensure(c, &c->d_f[0], (size_t)(7 * cells), &c->cap_f[0])) != LBM_OK) return st;
     if ((st = ensure(c, &c->d_f[1], (size_t)(7 * cells), &c->cap_f[1])) != LBM_OK) return st;
     if ((st = ensure(c, &c->d_phase_c, (size_t)cells, &c->cap_phase_c)) != LBM_OK) return st;
+    if ((st = ensure(c, &c->d_tsnap, (size_t)cells, &c->cap_tsnap)) != LBM_OK) return st;
     size_t cap_sb = (size_t)c->cap_sb;
     if ((st = ensure(c, &c->d_sb, sb.size(), &cap_sb)) != LBM_OK) return st;
     c->cap_sb = (int)cap_sb;
@@ -507,7 +511,7 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
         CUDA_TRY(c, cudaMemcpyAsync(c->d_T, op.t_init, sizeof(float) * N, cudaMemcpyHostToDevice, stm));
         tinit = c->d_T;
     }
-    lbm::init_kernel<<<grid_1d(cells), 256, 0, stm>>>(c->d_f[0], cells, L, (float)op.t_hot,
+    lbm::init_kernel<<<grid_1d(cells), 256, 0, stm>>>(c->d_f[0], c->d_tsnap, cells, L, (float)op.t_hot,
                                                       (float)op.t_cold, (float)c->t_ref, tinit);
     CUDA_TRY(c, cudaGetLastError());
     Ctl h{};
@@ -654,6 +658,7 @@ void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->d_f[0]);
     cudaFree(c->d_f[1]);
     cudaFree(c->d_phase_c);
+    cudaFree(c->d_tsnap);
     cudaFree(c->d_sb);
     cudaFree(c->d_part);
     cudaFree(c->d_Q);

@@ -38,6 +38,7 @@ struct StepArgs {
     const uint8_t* __restrict__ phase;  // [nz][ny][pitch], padded with 0
     const float4* __restrict__ sb;   // 2 float4 per phase: (xx, yy, zz, yz), (xz, xy, -, -)
     double* __restrict__ part;       // check partials [3][nz][blocks_per_plane]
+    float* __restrict__ tsnap;       // T - T_ref at the previous check, [nz][ny][pitch]
     long long pstride;               // floats per population = pitch * ny * nz
     int nx, ny, nz, pitch, n_phases;
     int quads_per_plane;             // (pitch / 4) * ny
@@ -48,6 +49,7 @@ struct StepArgs {
 
 struct Ctl {
     long long iter;      // iterations since start
+    long long iter_snap; // iteration of the temperature snapshot
     long long checks;
     double k_eff, r_t, r_q, best_rt;
     int status;          // lbm_status of the last check
@@ -162,15 +164,10 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
 
     const int n_real = active ? min(4, a.nx - x0) : 0;
     float4 o0v, o1v, o2v, o3v, o4v, o5v, o6v;
+    float4 thv, thp = make_float4(0.f, 0.f, 0.f, 0.f);
     double q_sum = 0.0, dT_sum = 0.0, T_sum = 0.0;
-    float4 p3, p4, p5, p6;
-    if (CHECK && active) {
-        // own-node populations of state n-1 give T^(n-1) for the residual
-        p3 = ld4(src + 3 * P + row + x0);
-        p4 = ld4(src + 4 * P + row + x0);
-        p5 = ld4(src + 5 * P + row + x0);
-        p6 = ld4(src + 6 * P + row + x0);
-    }
+    // T - T_ref at the previous check: the residual is the change since then
+    if (CHECK && active) thp = *reinterpret_cast<const float4*>(a.tsnap + row + x0);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const float g0 = comp(c0, k), g1 = comp(f1, k), g2 = comp(f2, k), g3 = comp(c3, k);
@@ -194,12 +191,13 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
         set_comp(o4v, k, real ? fmaf(-0.5f, hy, t8) : 0.f);
         set_comp(o5v, k, real ? fmaf(0.5f, hz, t8) : 0.f);
         set_comp(o6v, k, real ? fmaf(-0.5f, hz, t8) : 0.f);
-        if (CHECK && real) {
-            const float thp = ((comp(c0, k) + comp(c1, k)) + (comp(c2, k) + comp(p3, k))) +
-                              ((comp(p4, k) + comp(p5, k)) + comp(p6, k));
-            q_sum += (double)fmaf(-0.5f, sz, jz);          // (j_z + jhat_z) / 2
-            dT_sum += fabs((double)th - (double)thp);
-            T_sum += fabs((double)th + (double)a.t_ref);
+        if (CHECK) {
+            set_comp(thv, k, real ? th : 0.f);
+            if (real) {
+                q_sum += (double)fmaf(-0.5f, sz, jz);      // (j_z + jhat_z) / 2
+                dT_sum += fabs((double)th - (double)comp(thp, k));
+                T_sum += fabs((double)th + (double)a.t_ref);
+            }
         }
     }
     if (active) {
@@ -211,6 +209,7 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
         st4(dst + 4 * P, o4v);
         st4(dst + 5 * P, o5v);
         st4(dst + 6 * P, o6v);
+        if (CHECK) st4(a.tsnap + row + x0, thv);
     }
 
     if (CHECK) {
@@ -300,7 +299,9 @@ __global__ void __launch_bounds__(kFinalThreads) finalize_kernel(const FinalArgs
         c->checks += 1;
         c->k_eff = a.keff_scale * mean;
         c->r_q = (qmax - qmin) / fabs(mean);
-        c->r_t = dsum / tsum;
+        // mean per-step change of T since the previous check, relative to T
+        c->r_t = dsum / ((double)(c->iter - c->iter_snap) * tsum);
+        c->iter_snap = c->iter;
         int status;
         if (!isfinite(c->r_t) || !isfinite(c->k_eff)) {
             status = 6;                                   // LBM_ERR_DIVERGED
@@ -355,8 +356,8 @@ __global__ void permute_phase_kernel(const uint8_t* __restrict__ in, uint8_t* __
 
 // Initial state fhat^0 = f^eq(T0) (Eq. 6) as deviations from w_i T_ref.
 // T0 is the linear profile between the walls, or a given field (original order).
-__global__ void init_kernel(float* __restrict__ f, long long P, Layout L, float t_hot,
-                            float t_cold, float t_ref, const float* __restrict__ t_init) {
+__global__ void init_kernel(float* __restrict__ f, float* __restrict__ tsnap, long long P, Layout L,
+                            float t_hot, float t_cold, float t_ref, const float* __restrict__ t_init) {
     const long long total = (long long)L.pitch * L.NY * L.NZ;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -375,6 +376,7 @@ __global__ void init_kernel(float* __restrict__ f, long long P, Layout L, float 
             }
         }
         f[i] = 0.25f * th;
+        tsnap[i] = th;
         const float e = xc < L.NX ? 0.125f * th : 0.f;
         for (int q = 1; q < 7; ++q) f[q * P + i] = e;
     }
