@@ -194,7 +194,7 @@ def run_ours(args):
     S, lam, used, frac = make_cell(lbm, I, dev)
     stream = torch.cuda.Stream(device=dev)
     iters = args.iters
-    opts = S.opts(tol=0.0, max_iters=iters, check_every=K)
+    opts = S.opts(tol=0.0, max_iters=iters, check_every=K, host_loop=int(args.launch == "host"))
     opts.stream = int(stream.cuda_stream)
 
     def one_step():
@@ -268,6 +268,7 @@ def run_ours(args):
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "iters_per_step": iters, "check_every": K,
+                       "launch": args.launch,
                        "yarns": used, "yarn_fraction": round(frac, 6),
                        "l2": "inputs larger than L2 (f buffers 2 x 117 MB)",
                        "parallelism": f"replicas{ws}"},
@@ -296,6 +297,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--iters", type=int, default=ITERS, help="iterations per step (multiple of 100)")
+    ap.add_argument("--launch", default="graph", choices=["graph", "host"],
+                    help="graph: one CUDA graph per step with a device-side while node; "
+                         "host: the same kernels launched from the host (for profilers)")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline leg")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--traffic", type=float, default=None,

@@ -71,7 +71,11 @@ typedef struct {
     int32_t stall_checks;   /* stop with LBM_ERR_STALLED after this many checks
                                without a new smallest R_T; 0 disables (default 0) */
     int32_t storage;        /* lbm_storage; LBM_STORE_F32 */
-    int32_t reserved;
+    int32_t host_loop;      /* 0 (default): lbm_run drives the check intervals with one
+                               CUDA graph and a device-side while condition; 1: the host
+                               launches each interval and reads the stop flag after it
+                               (same kernels and results; for tools that cannot trace
+                               conditional graphs) */
     const float* t_init;    /* host, nx*ny*nz initial T field in the original axis
                                order, or NULL for the linear profile between walls */
     void* stream;           /* cudaStream_t for all work, or NULL for the context's */

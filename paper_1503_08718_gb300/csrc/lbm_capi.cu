@@ -48,6 +48,9 @@ struct lbm_ctx {
     size_t cap_phase_c = 0;
     float* d_tsnap = nullptr;              // T - T_ref at the previous check (canonical)
     size_t cap_tsnap = 0;
+    float* d_ref = nullptr;                // per-plane reference frames R_a [NZ], R_b [NZ]
+    size_t cap_ref = 0;
+    double quantum = 0.0;                  // grid of the reference values
     float4* d_sb = nullptr;                // 2 float4 per phase
     int cap_sb = 0;
     double* d_part = nullptr;
@@ -62,6 +65,7 @@ struct lbm_ctx {
     int blocks_per_plane = 0;
     long long pstride = 0;
     std::vector<double> Q_host;
+    std::vector<float> h_ref;              // staging of the initial reference frames
     double k_eff = NAN;
     bool have_k = false;
 
@@ -149,7 +153,11 @@ int grid_1d(long long total) {
     return (int)(b < 1 ? 1 : b);
 }
 
-lbm::StepArgs step_args(const lbm_ctx* c, int src) {
+// Frames of the per-plane reference: the state between calls is relative to
+// R_a; the first step of a graph interval moves it to R_b (see finalize).
+enum Frame { kAA = 0, kAB = 1, kBB = 2 };
+
+lbm::StepArgs step_args(const lbm_ctx* c, int src, Frame fr) {
     lbm::StepArgs a;
     std::memset(&a, 0, sizeof a);
     a.src = c->d_f[src];
@@ -158,6 +166,10 @@ lbm::StepArgs step_args(const lbm_ctx* c, int src) {
     a.sb = c->d_sb;
     a.part = c->d_part;
     a.tsnap = c->d_tsnap;
+    const float* ra = c->d_ref;
+    const float* rb = c->d_ref + c->L.NZ;
+    a.rsrc = fr == kBB ? rb : ra;
+    a.rdst = fr == kAA ? ra : rb;
     a.pstride = c->pstride;
     a.nx = c->L.NX;
     a.ny = c->L.NY;
@@ -167,14 +179,14 @@ lbm::StepArgs step_args(const lbm_ctx* c, int src) {
     a.quads_per_plane = (c->L.pitch / 4) * c->L.NY;
     a.blocks_per_plane = c->blocks_per_plane;
     const double eps = 0.25;
-    a.g_hot = (float)(eps * (c->opts.t_hot - c->t_ref));
-    a.g_cold = (float)(eps * (c->opts.t_cold - c->t_ref));
-    a.t_ref = (float)c->t_ref;
+    a.eps_hot = (float)(eps * c->opts.t_hot);
+    a.eps_cold = (float)(eps * c->opts.t_cold);
+    a.t_ref = c->t_ref;
     return a;
 }
 
-cudaError_t launch_step(const lbm_ctx* c, int src, bool check, cudaStream_t st) {
-    const lbm::StepArgs a = step_args(c, src);
+cudaError_t launch_step(const lbm_ctx* c, int src, bool check, Frame fr, cudaStream_t st) {
+    const lbm::StepArgs a = step_args(c, src, fr);
     const dim3 grid(c->blocks_per_plane, c->L.NZ);
     const size_t smem = sizeof(float4) * 2 * c->n_phases;
     if (c->lateral == LBM_LATERAL_PERIODIC) {
@@ -187,11 +199,16 @@ cudaError_t launch_step(const lbm_ctx* c, int src, bool check, cudaStream_t st) 
     return cudaGetLastError();
 }
 
-lbm::FinalArgs final_args(const lbm_ctx* c, int steps, int interval) {
+lbm::FinalArgs final_args(const lbm_ctx* c, int steps, int interval, bool rebase) {
     lbm::FinalArgs f;
     std::memset(&f, 0, sizeof f);
     f.part = c->d_part;
     f.Q = c->d_Q;
+    f.ra = c->d_ref;
+    f.rb = c->d_ref + c->L.NZ;
+    f.rebase = rebase ? 1 : 0;
+    f.quantum = c->quantum;
+    f.inv_area = 1.0 / ((double)c->L.NX * (double)c->L.NY);
     f.ctl = c->d_ctl;
     f.nz = c->L.NZ;
     f.blocks_per_plane = c->blocks_per_plane;
@@ -250,8 +267,8 @@ lbm_status read_ctl(lbm_ctx* c, cudaStream_t st) {
 // Everything a check-interval graph bakes in: the kernel arguments of both
 // buffer parities, the finalize arguments and the lateral type.
 std::vector<char> graph_signature(const lbm_ctx* c, int parity) {
-    const lbm::StepArgs a = step_args(c, parity);
-    const lbm::FinalArgs f = final_args(c, c->opts.check_every, c->opts.check_every);
+    const lbm::StepArgs a = step_args(c, parity, kAB);
+    const lbm::FinalArgs f = final_args(c, c->opts.check_every, c->opts.check_every, true);
     std::vector<char> sig(sizeof a + sizeof f + 2 * sizeof(int));
     std::memcpy(sig.data(), &a, sizeof a);
     std::memcpy(sig.data() + sizeof a, &f, sizeof f);
@@ -290,11 +307,11 @@ lbm_status build_graph(lbm_ctx* c, int parity) {
     if (e == cudaSuccess) {
         int src = parity;
         for (int k = 0; k < K && e == cudaSuccess; ++k) {
-            e = launch_step(c, src, k == K - 1, c->cap_stream);
+            e = launch_step(c, src, k == K - 1, k == 0 ? kAB : kBB, c->cap_stream);
             src ^= 1;
         }
         if (e == cudaSuccess) {
-            lbm::FinalArgs f = final_args(c, K, K);
+            lbm::FinalArgs f = final_args(c, K, K, true);
             f.handle = h;
             f.use_handle = 1;
             lbm::finalize_kernel<<<1, lbm::kFinalThreads, 0, c->cap_stream>>>(f);
@@ -476,12 +493,13 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
     if ((st = ensure(c, &c->d_f[1], (size_t)(7 * cells), &c->cap_f[1])) != LBM_OK) return st;
     if ((st = ensure(c, &c->d_phase_c, (size_t)cells, &c->cap_phase_c)) != LBM_OK) return st;
     if ((st = ensure(c, &c->d_tsnap, (size_t)cells, &c->cap_tsnap)) != LBM_OK) return st;
+    if ((st = ensure(c, &c->d_ref, (size_t)2 * L.NZ, &c->cap_ref)) != LBM_OK) return st;
     size_t cap_sb = (size_t)c->cap_sb;
     if ((st = ensure(c, &c->d_sb, sb.size(), &cap_sb)) != LBM_OK) return st;
     c->cap_sb = (int)cap_sb;
     const int quads = (L.pitch / 4) * L.NY;
     c->blocks_per_plane = (quads + lbm::kThreads - 1) / lbm::kThreads;
-    if ((st = ensure(c, &c->d_part, (size_t)3 * L.NZ * c->blocks_per_plane, &c->cap_part)) != LBM_OK)
+    if ((st = ensure(c, &c->d_part, (size_t)4 * L.NZ * c->blocks_per_plane, &c->cap_part)) != LBM_OK)
         return st;
     size_t capQ = (size_t)c->cap_Q;
     if ((st = ensure(c, &c->d_Q, (size_t)L.NZ, &capQ)) != LBM_OK) return st;
@@ -505,14 +523,37 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
                                 cudaMemcpyHostToDevice, stm));
     lbm::permute_phase_kernel<<<grid_1d(cells), 256, 0, stm>>>(c->d_phase, c->d_phase_c, L);
     CUDA_TRY(c, cudaGetLastError());
+    // initial reference frame: the plane means of the initial field on the
+    // quantum grid 2^(e-20), 2^e >= max |T_wall|, so that w (R - R') is exact
+    int e2 = 0;
+    std::frexp(std::fmax(std::fmax(std::fabs(op.t_hot), std::fabs(op.t_cold)), 1.0), &e2);
+    c->quantum = std::ldexp(1.0, e2 - 20);
+    std::vector<double> mean(L.NZ, 0.0);
     const float* tinit = nullptr;
     if (op.t_init) {
         const size_t N = (size_t)c->n[0] * c->n[1] * c->n[2];
+        for (size_t i = 0; i < N; ++i) {
+            int cc[3] = {(int)(i % c->n[0]), (int)((i / c->n[0]) % c->n[1]),
+                         (int)(i / ((size_t)c->n[0] * c->n[1]))};
+            mean[cc[L.perm[2]]] += op.t_init[i];
+        }
+        for (auto& m : mean) m /= (double)L.NX * (double)L.NY;
         CUDA_TRY(c, cudaMemcpyAsync(c->d_T, op.t_init, sizeof(float) * N, cudaMemcpyHostToDevice, stm));
         tinit = c->d_T;
+    } else {
+        for (int z = 0; z < L.NZ; ++z)
+            mean[z] = op.t_hot + (op.t_cold - op.t_hot) * ((double)z + 0.5) / (double)L.NZ;
     }
-    lbm::init_kernel<<<grid_1d(cells), 256, 0, stm>>>(c->d_f[0], c->d_tsnap, cells, L, (float)op.t_hot,
-                                                      (float)op.t_cold, (float)c->t_ref, tinit);
+    c->h_ref.assign(2 * (size_t)L.NZ, 0.f);
+    for (int z = 0; z < L.NZ; ++z) {
+        const float r = (float)(std::nearbyint(mean[z] / c->quantum) * c->quantum);
+        c->h_ref[z] = r;
+        c->h_ref[L.NZ + z] = r;
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_ref, c->h_ref.data(), sizeof(float) * 2 * L.NZ,
+                                cudaMemcpyHostToDevice, stm));
+    lbm::init_kernel<<<grid_1d(cells), 256, 0, stm>>>(c->d_f[0], c->d_tsnap, cells, L, c->d_ref,
+                                                      op.t_hot, op.t_cold, c->t_ref, tinit);
     CUDA_TRY(c, cudaGetLastError());
     Ctl h{};
     h.best_rt = INFINITY;
@@ -534,7 +575,7 @@ lbm_status lbm_advance(lbm_ctx* c, int64_t n_steps) {
     if (n_steps == 0) return LBM_OK;
     CUDA_TRY(c, cudaSetDevice(c->device));
     for (int64_t k = 0; k < n_steps; ++k) {
-        CUDA_TRY(c, launch_step(c, c->cur, false, c->stream));
+        CUDA_TRY(c, launch_step(c, c->cur, false, kAA, c->stream));
         c->cur ^= 1;
     }
     lbm::add_iters_kernel<<<1, 1, 0, c->stream>>>(c->d_ctl, (long long)n_steps);
@@ -547,9 +588,9 @@ lbm_status lbm_check(lbm_ctx* c, lbm_solve_info* info) {
     if (!c->started) return fail(c, LBM_ERR_STATE, "call lbm_start first");
     CUDA_TRY(c, cudaSetDevice(c->device));
     CUDA_TRY(c, cudaEventRecord(c->ev0, c->stream));
-    CUDA_TRY(c, launch_step(c, c->cur, true, c->stream));
+    CUDA_TRY(c, launch_step(c, c->cur, true, kAA, c->stream));
     c->cur ^= 1;
-    lbm::FinalArgs f = final_args(c, 1, c->opts.check_every);
+    lbm::FinalArgs f = final_args(c, 1, c->opts.check_every, false);
     lbm::finalize_kernel<<<1, lbm::kFinalThreads, 0, c->stream>>>(f);
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaEventRecord(c->ev1, c->stream));
@@ -574,21 +615,36 @@ lbm_status lbm_run(lbm_ctx* c, lbm_solve_info* info) {
         if (info) info->status = LBM_ERR_NOT_CONVERGED;
         return fail(c, LBM_ERR_NOT_CONVERGED, "max_iters leaves no whole check interval to run");
     }
-    // reuse the graph of an earlier solve when nothing it bakes in changed
-    if (!c->gexec[c->cur] || c->gsig[c->cur] != graph_signature(c, c->cur)) {
-        if (c->gexec[c->cur]) cudaGraphExecDestroy(c->gexec[c->cur]);
-        c->gexec[c->cur] = nullptr;
-        if ((st = build_graph(c, c->cur)) != LBM_OK) return st;
-    }
-    const long long iter0 = c->h_ctl->iter;
     CUDA_TRY(c, cudaEventRecord(c->ev0, c->stream));
-    CUDA_TRY(c, cudaGraphLaunch(c->gexec[c->cur], c->stream));
+    if (c->opts.host_loop) {
+        // the same interval, launched kernel by kernel; the stop flag is read
+        // back after every interval
+        do {
+            for (int k = 0; k < K; ++k) {
+                CUDA_TRY(c, launch_step(c, c->cur, k == K - 1, k == 0 ? kAB : kBB, c->stream));
+                c->cur ^= 1;
+            }
+            lbm::FinalArgs f = final_args(c, K, K, true);
+            lbm::finalize_kernel<<<1, lbm::kFinalThreads, 0, c->stream>>>(f);
+            CUDA_TRY(c, cudaGetLastError());
+            CUDA_TRY(c, cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost,
+                                        c->stream));
+            CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        } while (!c->h_ctl->done);
+    } else {
+        // reuse the graph of an earlier solve when nothing it bakes in changed
+        if (!c->gexec[c->cur] || c->gsig[c->cur] != graph_signature(c, c->cur)) {
+            if (c->gexec[c->cur]) cudaGraphExecDestroy(c->gexec[c->cur]);
+            c->gexec[c->cur] = nullptr;
+            if ((st = build_graph(c, c->cur)) != LBM_OK) return st;
+        }
+        CUDA_TRY(c, cudaGraphLaunch(c->gexec[c->cur], c->stream));
+    }
     CUDA_TRY(c, cudaEventRecord(c->ev1, c->stream));
     if ((st = read_ctl(c, c->stream)) != LBM_OK) return st;
     // K is even, so the state is back in the buffer it started from
     float ms = 0.f;
     CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-    (void)iter0;
     fill_info(c, info, ms);
     const int s = c->h_ctl->status;
     if (s == LBM_OK) return LBM_OK;
@@ -619,7 +675,7 @@ lbm_status lbm_get_temperature(lbm_ctx* c, float* host_out) {
     CUDA_TRY(c, cudaSetDevice(c->device));
     const long long N = (long long)c->n[0] * c->n[1] * c->n[2];
     lbm::temperature_kernel<<<grid_1d(N), 256, 0, c->stream>>>(c->d_f[c->cur], c->pstride, c->L,
-                                                              (float)c->t_ref, c->d_T);
+                                                              c->d_ref, c->d_T);
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaMemcpyAsync(host_out, c->d_T, sizeof(float) * N, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -659,6 +715,7 @@ void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->d_f[1]);
     cudaFree(c->d_phase_c);
     cudaFree(c->d_tsnap);
+    cudaFree(c->d_ref);
     cudaFree(c->d_sb);
     cudaFree(c->d_part);
     cudaFree(c->d_Q);

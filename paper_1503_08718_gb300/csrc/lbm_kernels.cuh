@@ -5,9 +5,14 @@
 // next one).  The Dirichlet axis is always the slowest index z; the host lays
 // the cell out that way.  Rows are padded to a multiple of 4 voxels (pitch)
 // so that every thread moves one aligned 16-byte float4 per population.
-// Values are deviations g_i = f_i - w_i T_ref, w_0 = 1/4, w_1..6 = 1/8
-// (Eq. 6 with gamma = 1/8); every rule below is linear, so deviations obey
-// the same equations with the wall temperatures shifted by T_ref.
+// Values are stored as deviations g_i = f_i - w_i R(z), w_0 = 1/4,
+// w_1..6 = 1/8 (Eq. 6 with gamma = 1/8), from a per-plane reference
+// temperature R(z): the plane mean of T at the previous check, quantised to a
+// power-of-two grid so that every frame-change constant w_i (R(z') - R(z)) is
+// exact in FP32.  The map is linear, so the frame changes nothing in exact
+// arithmetic; in FP32 the stored values are small (non-equilibrium parts and
+// in-plane temperature variation), which shrinks the rounding of the stored
+// state and with it the FP32 error of the converged fixed point.
 //
 // Collision (Eq. 5, 8-13).  With tau_0 = tau_4 = tau_5 = tau_6 = 1 the
 // moments 0, 4, 5, 6 leave the collision at equilibrium and the flux moment
@@ -37,14 +42,16 @@ struct StepArgs {
     float* __restrict__ dst;         // 7 populations, post-collision state n
     const uint8_t* __restrict__ phase;  // [nz][ny][pitch], padded with 0
     const float4* __restrict__ sb;   // 2 float4 per phase: (xx, yy, zz, yz), (xz, xy, -, -)
-    double* __restrict__ part;       // check partials [3][nz][blocks_per_plane]
+    double* __restrict__ part;       // check partials [4][nz][blocks_per_plane]
     float* __restrict__ tsnap;       // T - T_ref at the previous check, [nz][ny][pitch]
+    const float* __restrict__ rsrc;  // reference R(z) of the src state, [nz]
+    const float* __restrict__ rdst;  // reference R(z) of the dst state, [nz]
     long long pstride;               // floats per population = pitch * ny * nz
     int nx, ny, nz, pitch, n_phases;
     int quads_per_plane;             // (pitch / 4) * ny
     int blocks_per_plane;
-    float g_hot, g_cold;             // eps * (T_wall - T_ref)
-    float t_ref;
+    float eps_hot, eps_cold;         // eps * T_wall
+    double t_ref;                    // offset of the residual snapshot
 };
 
 struct Ctl {
@@ -61,6 +68,11 @@ struct Ctl {
 struct FinalArgs {
     const double* __restrict__ part;
     double* __restrict__ Q;          // [nz]
+    float* ra;                       // reference of the state after the interval
+    float* rb;                       // reference of the next interval, [nz]
+    int rebase;                      // the interval's first step moved the state to rb
+    double quantum;                  // grid of the reference values (power of two)
+    double inv_area;                 // 1 / (nx * ny)
     Ctl* ctl;
     int nz, blocks_per_plane;
     int steps;                       // iterations covered by this check interval
@@ -140,9 +152,20 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
         c6 = ld4(src + o6 + x0);
         ph = __ldg(reinterpret_cast<const uchar4*>(a.phase + row + x0));
     }
-    if (zlo) { c5.x = a.g_hot - c5.x; c5.y = a.g_hot - c5.y; c5.z = a.g_hot - c5.z; c5.w = a.g_hot - c5.w; }
-    if (zhi) { c6.x = a.g_cold - c6.x; c6.y = a.g_cold - c6.y; c6.z = a.g_cold - c6.z; c6.w = a.g_cold - c6.w; }
-
+    // Frame changes (all exact): a population pulled from plane z' carries
+    // w_i R_src(z'); it is re-expressed relative to R_dst(z) of this node.
+    const float w = 0.125f;
+    const float r0 = a.rsrc[z], rd = a.rdst[z];
+    const float rm = zlo ? r0 : a.rsrc[z - 1];
+    const float rp = zhi ? r0 : a.rsrc[z + 1];
+    const float k_in = w * (r0 - rd);
+    // walls (Eq. 23): f_in = -fhat_out(x) + eps T_wall, fhat_out = g + w R_src(z)
+    const float k5 = zlo ? (a.eps_hot - w * r0) - w * rd : w * (rm - rd);
+    const float k6 = zhi ? (a.eps_cold - w * r0) - w * rd : w * (rp - rd);
+    const float kT = (2.f * k_in + 4.f * k_in) + (k5 + k6);   // sum of w_i (...) with w_0 = 2w
+    const float kJ = k5 - k6;
+    if (zlo) { c5.x = -c5.x; c5.y = -c5.y; c5.z = -c5.z; c5.w = -c5.w; }
+    if (zhi) { c6.x = -c6.x; c6.y = -c6.y; c6.z = -c6.z; c6.w = -c6.w; }
     // x-neighbours: f1 comes from x - 1, f2 from x + 1.
     const float left1 = __shfl_up_sync(kFull, c1.w, 1);
     const float right2 = __shfl_down_sync(kFull, c2.x, 1);
@@ -165,9 +188,10 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
     const int n_real = active ? min(4, a.nx - x0) : 0;
     float4 o0v, o1v, o2v, o3v, o4v, o5v, o6v;
     float4 thv, thp = make_float4(0.f, 0.f, 0.f, 0.f);
-    double q_sum = 0.0, dT_sum = 0.0, T_sum = 0.0;
+    double q_sum = 0.0, dT_sum = 0.0, T_sum = 0.0, Tp_sum = 0.0;
     // T - T_ref at the previous check: the residual is the change since then
     if (CHECK && active) thp = *reinterpret_cast<const float4*>(a.tsnap + row + x0);
+    const double dref = (double)rd - a.t_ref;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const float g0 = comp(c0, k), g1 = comp(f1, k), g2 = comp(f2, k), g3 = comp(c3, k);
@@ -175,8 +199,9 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
         const int p = (k == 0 ? ph.x : (k == 1 ? ph.y : (k == 2 ? ph.z : ph.w)));
         const float4 sa = s_sb[2 * p];
         const float4 sc = s_sb[2 * p + 1];
-        const float th = ((g0 + g1) + (g2 + g3)) + ((g4 + g5) + g6);   // T - T_ref (Eq. 14)
-        const float jx = g1 - g2, jy = g3 - g4, jz = g5 - g6;
+        // T - R_dst(z) (Eq. 14) and the flux moment j, with the frame constants
+        const float th = (((g0 + g1) + (g2 + g3)) + ((g4 + g5) + g6)) + kT;
+        const float jx = g1 - g2, jy = g3 - g4, jz = (g5 - g6) + kJ;
         // sigma = S_b j with S_b symmetric: (xx, yy, zz, yz) = sa, (xz, xy) = sc.xy
         const float sx = fmaf(sa.x, jx, fmaf(sc.y, jy, sc.x * jz));
         const float sy = fmaf(sc.y, jx, fmaf(sa.y, jy, sa.w * jz));
@@ -192,11 +217,13 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
         set_comp(o5v, k, real ? fmaf(0.5f, hz, t8) : 0.f);
         set_comp(o6v, k, real ? fmaf(-0.5f, hz, t8) : 0.f);
         if (CHECK) {
-            set_comp(thv, k, real ? th : 0.f);
+            const double tdev = (double)th + dref;          // T - T_ref
+            set_comp(thv, k, real ? (float)tdev : 0.f);
             if (real) {
                 q_sum += (double)fmaf(-0.5f, sz, jz);      // (j_z + jhat_z) / 2
-                dT_sum += fabs((double)th - (double)comp(thp, k));
-                T_sum += fabs((double)th + (double)a.t_ref);
+                dT_sum += fabs(tdev - (double)comp(thp, k));
+                T_sum += fabs(tdev + a.t_ref);
+                Tp_sum += tdev + a.t_ref;
             }
         }
     }
@@ -215,36 +242,29 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
     if (CHECK) {
         // warp shuffle, then a tree over the block's warps: one FP64 partial
         // per (block, plane) written in a fixed order (deterministic)
+        double v[4] = {q_sum, dT_sum, T_sum, Tp_sum};
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            q_sum += __shfl_down_sync(kFull, q_sum, off);
-            dT_sum += __shfl_down_sync(kFull, dT_sum, off);
-            T_sum += __shfl_down_sync(kFull, T_sum, off);
-        }
-        __shared__ double s_red[3][kThreads / 32];
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) v[m] += __shfl_down_sync(kFull, v[m], off);
+        __shared__ double s_red[4][kThreads / 32];
         const int warp = threadIdx.x >> 5;
-        if (lane == 0) {
-            s_red[0][warp] = q_sum;
-            s_red[1][warp] = dT_sum;
-            s_red[2][warp] = T_sum;
-        }
+        if (lane == 0)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) s_red[m][warp] = v[m];
         __syncthreads();
         if (threadIdx.x < 32) {
-            double v0 = lane < kThreads / 32 ? s_red[0][lane] : 0.0;
-            double v1 = lane < kThreads / 32 ? s_red[1][lane] : 0.0;
-            double v2 = lane < kThreads / 32 ? s_red[2][lane] : 0.0;
 #pragma unroll
-            for (int off = 4; off > 0; off >>= 1) {
-                v0 += __shfl_down_sync(kFull, v0, off);
-                v1 += __shfl_down_sync(kFull, v1, off);
-                v2 += __shfl_down_sync(kFull, v2, off);
-            }
+            for (int m = 0; m < 4; ++m) v[m] = lane < kThreads / 32 ? s_red[m][lane] : 0.0;
+#pragma unroll
+            for (int off = 4; off > 0; off >>= 1)
+#pragma unroll
+                for (int m = 0; m < 4; ++m) v[m] += __shfl_down_sync(kFull, v[m], off);
             if (lane == 0) {
                 const long long base = (long long)z * a.blocks_per_plane + blockIdx.x;
                 const long long plane_all = (long long)a.nz * a.blocks_per_plane;
-                a.part[base] = v0;
-                a.part[plane_all + base] = v1;
-                a.part[2 * plane_all + base] = v2;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) a.part[m * plane_all + base] = v[m];
             }
         }
     }
@@ -256,12 +276,13 @@ __global__ void __launch_bounds__(kFinalThreads) finalize_kernel(const FinalArgs
     double qsum = 0.0, qmax = -INFINITY, qmin = INFINITY, dsum = 0.0, tsum = 0.0;
     const long long plane_all = (long long)a.nz * a.blocks_per_plane;
     for (int z = threadIdx.x; z < a.nz; z += kFinalThreads) {
-        double q = 0.0, d = 0.0, t = 0.0;
+        double q = 0.0, d = 0.0, t = 0.0, tp = 0.0;
         const long long base = (long long)z * a.blocks_per_plane;
         for (int b = 0; b < a.blocks_per_plane; ++b) {
             q += a.part[base + b];
             d += a.part[plane_all + base + b];
             t += a.part[2 * plane_all + base + b];
+            tp += a.part[3 * plane_all + base + b];
         }
         a.Q[z] = q;
         qsum += q;
@@ -269,6 +290,9 @@ __global__ void __launch_bounds__(kFinalThreads) finalize_kernel(const FinalArgs
         qmin = fmin(qmin, q);
         dsum += d;
         tsum += t;
+        // next reference: the plane mean of T on the quantum grid
+        if (a.rebase) a.ra[z] = a.rb[z];
+        a.rb[z] = (float)(nearbyint(tp * a.inv_area / a.quantum) * a.quantum);
     }
     __shared__ double s[5][kFinalThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -357,7 +381,8 @@ __global__ void permute_phase_kernel(const uint8_t* __restrict__ in, uint8_t* __
 // Initial state fhat^0 = f^eq(T0) (Eq. 6) as deviations from w_i T_ref.
 // T0 is the linear profile between the walls, or a given field (original order).
 __global__ void init_kernel(float* __restrict__ f, float* __restrict__ tsnap, long long P, Layout L,
-                            float t_hot, float t_cold, float t_ref, const float* __restrict__ t_init) {
+                            const float* __restrict__ ref, double t_hot, double t_cold,
+                            double t_ref, const float* __restrict__ t_init) {
     const long long total = (long long)L.pitch * L.NY * L.NZ;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -365,26 +390,22 @@ __global__ void init_kernel(float* __restrict__ f, float* __restrict__ tsnap, lo
         const long long r = i / L.pitch;
         const int yc = (int)(r % L.NY);
         const int zc = (int)(r / L.NY);
-        float th = 0.f;
+        double T = t_ref;
         if (xc < L.NX) {
-            if (t_init) {
-                th = t_init[orig_index(L, xc, yc, zc)] - t_ref;
-            } else {
-                const double T = (double)t_hot + ((double)t_cold - (double)t_hot) *
-                                                     ((double)zc + 0.5) / (double)L.NZ;
-                th = (float)(T - (double)t_ref);
-            }
+            T = t_init ? (double)t_init[orig_index(L, xc, yc, zc)]
+                       : t_hot + (t_cold - t_hot) * ((double)zc + 0.5) / (double)L.NZ;
         }
+        const float th = xc < L.NX ? (float)(T - (double)ref[zc]) : 0.f;
+        tsnap[i] = xc < L.NX ? (float)(T - t_ref) : 0.f;
         f[i] = 0.25f * th;
-        tsnap[i] = th;
-        const float e = xc < L.NX ? 0.125f * th : 0.f;
+        const float e = 0.125f * th;
         for (int q = 1; q < 7; ++q) f[q * P + i] = e;
     }
 }
 
 // T = sum_i f_i (Eq. 14) of the current state, written in the original order.
-__global__ void temperature_kernel(const float* __restrict__ f, long long P, Layout L, float t_ref,
-                                   float* __restrict__ T) {
+__global__ void temperature_kernel(const float* __restrict__ f, long long P, Layout L,
+                                   const float* __restrict__ ref, float* __restrict__ T) {
     const long long total = (long long)L.n[0] * L.n[1] * L.n[2];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -393,10 +414,11 @@ __global__ void temperature_kernel(const float* __restrict__ f, long long P, Lay
         const long long r = i / L.n[0];
         c[1] = (int)(r % L.n[1]);
         c[2] = (int)(r / L.n[1]);
-        const long long k = ((long long)c[L.perm[2]] * L.NY + c[L.perm[1]]) * L.pitch + c[L.perm[0]];
+        const int zc = c[L.perm[2]];
+        const long long k = ((long long)zc * L.NY + c[L.perm[1]]) * L.pitch + c[L.perm[0]];
         const float th = ((f[k] + f[P + k]) + (f[2 * P + k] + f[3 * P + k])) +
                          ((f[4 * P + k] + f[5 * P + k]) + f[6 * P + k]);
-        T[i] = th + t_ref;
+        T[i] = th + ref[zc];
     }
 }
 

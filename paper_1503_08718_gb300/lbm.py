@@ -41,7 +41,7 @@ class lbm_solve_opts(ctypes.Structure):
                 ("tau_max", ctypes.c_double), ("lattice_scale", ctypes.c_double),
                 ("tol", ctypes.c_double), ("max_iters", ctypes.c_int64),
                 ("check_every", ctypes.c_int32), ("stall_checks", ctypes.c_int32),
-                ("storage", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("storage", ctypes.c_int32), ("host_loop", ctypes.c_int32),
                 ("t_init", ctypes.POINTER(ctypes.c_float)), ("stream", ctypes.c_void_p)]
 
 
