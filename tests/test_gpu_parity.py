@@ -126,8 +126,12 @@ def test_graph_run_equals_explicit_steps():
     for _ in range(3):
         B.advance(9)
         ib = B.check()
-    assert np.array_equal(A.temperature(), B.temperature())
-    assert ib.k_eff == info.k_eff and ib.residual_T == info.residual_T
+    # the graph moves the stored deviations to a new per-plane reference at
+    # every interval, explicit steps keep the start frame: equal up to FP32
+    # rounding of the stored values
+    assert np.max(np.abs(A.temperature() - B.temperature())) <= 1e-6
+    assert ib.k_eff == pytest.approx(info.k_eff, rel=1e-6)
+    assert (ib.iters, ib.checks) == (info.iters, info.checks)
 
 
 @pytest.mark.parametrize("lateral", [0, 1])
