@@ -162,6 +162,43 @@ lbm_status lbm_set_geometry_braid(lbm_ctx* c, double g_rad, double A, double B,
                                   const double* anchors, int n_max, double phi,
                                   int* n_used, double* fraction);
 
+/* Largest n_max accepted by lbm_braid_voxelize_noalloc. */
+#define LBM_NOALLOC_MAX_YARNS 1024
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory.  It produces the same phase map as
+ * lbm_set_geometry_braid (bit for bit), but writes it into caller memory and
+ * allocates nothing: no cudaMalloc, no cudaFree, no context.  Callers that
+ * need it are processes whose device memory belongs to another allocator
+ * (e.g. a framework's caching pool holding most of the GPU), services under a
+ * fixed memory budget, and loops that must not stall on the device-wide
+ * synchronisation that cudaMalloc and cudaFree imply.
+ *
+ * Its scratch (a yarn histogram) is a file-scope __device__ array of
+ * LBM_NOALLOC_MAX_YARNS + 1 64-bit bins (8.2 KB) that every GPU loading the
+ * library holds until the process exits.  The first call on a device (the
+ * current device) looks up that array's device address once; make that first
+ * call before any stream capture.  Every call on a device shares the array
+ * and clears the bins it uses; calls that overlap on the GPU (concurrent
+ * streams or threads) race on it and must be serialised by the caller.
+ *
+ * nx, ny, nz: cell size (>= 1, product < 2^31).
+ * g_rad, A, B, phi: as lbm_set_geometry_braid.
+ * d_anchors: device, 16-byte aligned, n_max (x0, y0) double pairs.
+ * n_max: 1 .. LBM_NOALLOC_MAX_YARNS; larger values return
+ *        LBM_ERR_INVALID_ARG with a message saying so.
+ * d_phase: device, nx*ny*nz uint8 output (x fastest), written on `stream`.
+ * n_used, fraction: host, nullable; set before return.
+ * stream: cudaStream_t (NULL = legacy default stream).  The call
+ *         synchronises the stream once (to read the histogram); the phase map
+ *         is written asynchronously after that on the same stream.
+ * err, err_len: host buffer (nullable) for a message on failure.
+ * Returns LBM_OK, LBM_ERR_INVALID_ARG or LBM_ERR_CUDA. */
+lbm_status lbm_braid_voxelize_noalloc(int nx, int ny, int nz, double g_rad, double A, double B,
+                                      const double* d_anchors, int n_max, double phi,
+                                      uint8_t* d_phase, int* n_used, double* fraction,
+                                      void* stream, char* err, int err_len);
+
 /* Copies the phase map (nx*ny*nz uint8, original order) to host_out. */
 lbm_status lbm_get_geometry(lbm_ctx* c, uint8_t* host_out);
 

@@ -11,6 +11,8 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "lbm.h"
@@ -189,5 +191,158 @@ extern "C" lbm_status lbm_set_geometry_braid(lbm_ctx* c, double g_rad, double A,
     if (n_used) *n_used = used;
     if (fraction) *fraction = (double)yarn / (double)N;
     lbm__set_phase_count(c, 5);
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the braided-cell voxeliser.
+//
+// Some callers cannot call cudaMalloc: a process whose device memory is owned
+// by another allocator (for instance a deep-learning framework's caching
+// pool that has reserved most of the GPU), a service running under a fixed
+// memory budget, or a latency-sensitive loop that must not stall on the
+// implicit device synchronisation of cudaMalloc / cudaFree.  For them the
+// histogram that the voxeliser needs as scratch lives in a file-scope device
+// array of fixed size instead of a per-call allocation; inputs and outputs
+// stay in the caller's memory.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr int kNoAllocMaxYarns = LBM_NOALLOC_MAX_YARNS;
+constexpr int kMaxDevices = 64;
+
+// Scratch histogram: one bin per yarn plus the "no yarn" bin.  Every device
+// that loads the library holds this array until the process exits.  All
+// calls on a device share it.
+static __device__ __align__(256) unsigned long long g_noalloc_hist[kNoAllocMaxYarns + 1];
+
+// Device address of g_noalloc_hist per device, looked up once per device.
+unsigned long long* g_hist_addr[kMaxDevices] = {};
+std::mutex g_hist_mutex;
+
+void put_msg(char* err, int err_len, const char* msg) {
+    if (err && err_len > 0) {
+        std::strncpy(err, msg, (size_t)err_len - 1);
+        err[err_len - 1] = '\0';
+    }
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_braid_voxelize_noalloc(int nx, int ny, int nz, double g_rad, double A,
+                                                 double B, const double* d_anchors, int n_max,
+                                                 double phi, uint8_t* d_phase, int* n_used,
+                                                 double* fraction, void* stream, char* err,
+                                                 int err_len) {
+    if (nx < 1 || ny < 1 || nz < 1 || (long long)nx * ny * nz >= (1LL << 31)) {
+        put_msg(err, err_len, "cell sizes must be >= 1 with nx*ny*nz < 2^31");
+        return LBM_ERR_INVALID_ARG;
+    }
+    if (n_max < 1 || n_max > kNoAllocMaxYarns) {
+        put_msg(err, err_len, "n_max must be in [1, LBM_NOALLOC_MAX_YARNS = 1024]: the scratch "
+                              "histogram of the allocation-free voxeliser has 1025 bins");
+        return LBM_ERR_INVALID_ARG;
+    }
+    if (!d_anchors || !d_phase || ((uintptr_t)d_anchors & 15u)) {
+        put_msg(err, err_len, "d_anchors (16-byte aligned) and d_phase must be device pointers");
+        return LBM_ERR_INVALID_ARG;
+    }
+    if (!(A > 0.0) || !(B > 0.0) || !(g_rad > 0.0) || !(g_rad < 1.5707963267948966) ||
+        !(phi >= 0.0) || !(phi <= 1.0)) {
+        put_msg(err, err_len, "need 0 < g < pi/2, A > 0, B > 0 and 0 <= phi <= 1");
+        return LBM_ERR_INVALID_ARG;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        put_msg(err, err_len, e != cudaSuccess ? cudaGetErrorString(e) : "device index too large");
+        return LBM_ERR_CUDA;
+    }
+    unsigned long long* hist = nullptr;
+    {
+        // set-up on the first call on this device (the current device)
+        std::lock_guard<std::mutex> lock(g_hist_mutex);
+        if (!g_hist_addr[dev]) {
+            e = cudaGetSymbolAddress((void**)&g_hist_addr[dev], g_noalloc_hist);
+            if (e != cudaSuccess) {
+                g_hist_addr[dev] = nullptr;
+                put_msg(err, err_len, cudaGetErrorString(e));
+                return LBM_ERR_CUDA;
+            }
+        }
+        hist = g_hist_addr[dev];
+    }
+
+    Braid b;
+    static const int SX[4] = {1, -1, -1, 1};
+    static const int SY[4] = {1, 1, -1, -1};
+    const double h = std::sin(g_rad) / std::sqrt(2.0);
+    const double cg = std::cos(g_rad);
+    for (int k = 0; k < 4; ++k) {
+        double* d = b.d[k];
+        double* u = b.u[k];
+        double* v = b.v[k];
+        d[0] = SX[k] * h;
+        d[1] = SY[k] * h;
+        d[2] = cg;
+        const double nrm = std::sqrt(d[0] * d[0] + d[1] * d[1]);
+        u[0] = -d[1] / nrm;
+        u[1] = d[0] / nrm;
+        u[2] = 0.0;
+        v[0] = -(d[2] * u[1]);
+        v[1] = d[2] * u[0];
+        v[2] = d[0] * u[1] - d[1] * u[0];
+    }
+    b.A = A;
+    b.B = B;
+    b.Nx = (double)nx;
+    b.Ny = (double)ny;
+    b.nx = nx;
+    b.ny = ny;
+    b.nz = nz;
+    const long long N = (long long)nx * ny * nz;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double2* anchors = reinterpret_cast<const double2*>(d_anchors);
+
+    // the array keeps the previous call's counts: clear the bins this call uses
+    const size_t bytes = sizeof(unsigned long long) * ((size_t)n_max + 1);
+    e = cudaMemsetAsync(hist, 0, bytes, st);
+    long long blocks = (N + 255) / 256;
+    if (blocks > 152LL * 16) blocks = 152LL * 16;
+    if (e == cudaSuccess) {
+        braid_count_kernel<<<(int)blocks, 256, sizeof(unsigned int) * (n_max + 1), st>>>(
+            b, anchors, n_max, hist);
+        e = cudaGetLastError();
+    }
+    unsigned long long counts[kNoAllocMaxYarns + 1];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(counts, hist, bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        put_msg(err, err_len, cudaGetErrorString(e));
+        return LBM_ERR_CUDA;
+    }
+    int used = -1;
+    unsigned long long cum = 0;
+    for (int i = 0; i < n_max; ++i) {
+        cum += counts[i];
+        if ((double)cum >= phi * (double)N) {
+            used = i + 1;
+            break;
+        }
+    }
+    if (used < 0) {
+        put_msg(err, err_len, "yarn fraction phi not reached with n_max yarns");
+        return LBM_ERR_INVALID_ARG;
+    }
+    braid_write_kernel<<<(int)blocks, 256, 0, st>>>(b, anchors, used, d_phase);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        put_msg(err, err_len, cudaGetErrorString(e));
+        return LBM_ERR_CUDA;
+    }
+    if (n_used) *n_used = used;
+    if (fraction) *fraction = (double)cum / (double)N;
+    put_msg(err, err_len, "");
     return LBM_OK;
 }

@@ -79,6 +79,13 @@ _PROTOS = {
                                               ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_double)]),
     "lbm_get_geometry": (ctypes.c_int, [_ctx_p, ctypes.POINTER(ctypes.c_uint8)]),
+    "lbm_braid_voxelize_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_double, ctypes.c_void_p, ctypes.c_int,
+                                                  ctypes.c_double, ctypes.c_void_p,
+                                                  ctypes.POINTER(ctypes.c_int),
+                                                  ctypes.POINTER(ctypes.c_double),
+                                                  ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int]),
     "lbm_last_error": (ctypes.c_char_p, [_ctx_p]),
     "lbm_destroy": (None, [_ctx_p]),
 }
@@ -182,6 +189,23 @@ def lbm_set_geometry_braid(ctx, g_rad: float, A: float, B: float, anchors: np.nd
 def lbm_get_geometry(ctx, out: np.ndarray) -> int:
     assert out.dtype == np.uint8 and out.flags.c_contiguous
     return load().lbm_get_geometry(ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+
+
+LBM_NOALLOC_MAX_YARNS = 1024
+
+
+def lbm_braid_voxelize_noalloc(nx: int, ny: int, nz: int, g_rad: float, A: float, B: float,
+                               d_anchors: int, n_max: int, phi: float, d_phase: int,
+                               stream: int | None = None):
+    """Allocation-free voxeliser: d_anchors and d_phase are device
+    addresses the caller owns.  Returns (status, n_used, fraction, message)."""
+    used = ctypes.c_int(0)
+    frac = ctypes.c_double(0.0)
+    msg = ctypes.create_string_buffer(256)
+    st = load().lbm_braid_voxelize_noalloc(nx, ny, nz, g_rad, A, B, d_anchors, n_max, phi,
+                                           d_phase, ctypes.byref(used), ctypes.byref(frac),
+                                           stream, msg, len(msg))
+    return st, used.value, frac.value, msg.value.decode()
 
 
 def lbm_last_error(ctx) -> str:
