@@ -48,15 +48,17 @@ struct lbm_ctx {
     size_t cap_phase_c = 0;
     float* d_tsnap = nullptr;              // T - T_ref at the previous check (canonical)
     size_t cap_tsnap = 0;
-    float* d_ref = nullptr;                // per-plane reference frames R_a [NZ], R_b [NZ]
-    size_t cap_ref = 0;
+    float* d_ref = nullptr;                // frames R_a, R_b, R_c [NZ each], then the
+    size_t cap_ref = 0;                    // init tables T0 - R and T0 - T_ref [NZ each]
     double quantum = 0.0;                  // grid of the reference values
     float4* d_sb = nullptr;                // 2 float4 per phase
     int cap_sb = 0;
     double* d_part = nullptr;
     size_t cap_part = 0;
-    double* d_Q = nullptr;
+    double* d_Q = nullptr;                 // [NZ] plane flux, then [2][NZ] plane |dT|, |T|
     int cap_Q = 0;
+    int* d_plane_cnt = nullptr;            // closing tickets per plane
+    size_t cap_cnt = 0;
     float* d_T = nullptr;                  // nx*ny*nz staging (T output / t_init input)
     Ctl* d_ctl = nullptr;
     Ctl* h_ctl = nullptr;                  // pinned mirror
@@ -154,26 +156,36 @@ int grid_1d(long long total) {
 }
 
 // Frames of the per-plane reference: the state between calls is relative to
-// R_a; the first step of a graph interval moves it to R_b (see finalize).
+// R_a; the first step of a graph interval moves it to R_b, and the check
+// that closes the interval rotates R_a <- R_b <- new plane means.
 enum Frame { kAA = 0, kAB = 1, kBB = 2 };
 
-lbm::StepArgs step_args(const lbm_ctx* c, int src, Frame fr) {
+// How a check step closes: which frames rotate, how many iterations it
+// closes and whether it drives a graph's while condition.
+struct Closing {
+    int rebase = 0;
+    int steps = 1;
+    cudaGraphConditionalHandle handle = 0;
+    int use_handle = 0;
+};
+
+lbm::StepArgs step_args(const lbm_ctx* c, int src, Frame fr, const Closing& cl = Closing()) {
     lbm::StepArgs a;
     std::memset(&a, 0, sizeof a);
     a.src = c->d_f[src];
     a.dst = c->d_f[src ^ 1];
     a.phase = c->d_phase_c;
     a.sb = c->d_sb;
-    a.part = c->d_part;
     a.tsnap = c->d_tsnap;
-    const float* ra = c->d_ref;
-    const float* rb = c->d_ref + c->L.NZ;
+    const int NZ = c->L.NZ;
+    float* ra = c->d_ref;
+    float* rb = c->d_ref + NZ;
     a.rsrc = fr == kBB ? rb : ra;
     a.rdst = fr == kAA ? ra : rb;
     a.pstride = c->pstride;
     a.nx = c->L.NX;
     a.ny = c->L.NY;
-    a.nz = c->L.NZ;
+    a.nz = NZ;
     a.pitch = c->L.pitch;
     a.n_phases = c->n_phases;
     a.quads_per_plane = (c->L.pitch / 4) * c->L.NY;
@@ -182,11 +194,34 @@ lbm::StepArgs step_args(const lbm_ctx* c, int src, Frame fr) {
     a.eps_hot = (float)(eps * c->opts.t_hot);
     a.eps_cold = (float)(eps * c->opts.t_cold);
     a.t_ref = c->t_ref;
+    lbm::CheckArgs& k = a.ck;
+    k.part = c->d_part;
+    k.Q = c->d_Q;
+    k.plane = c->d_Q + NZ;
+    k.plane_cnt = c->d_plane_cnt;
+    k.ctl = c->d_ctl;
+    k.ra = ra;
+    k.rb = rb;
+    k.rc = c->d_ref + 2 * NZ;
+    k.rebase = cl.rebase;
+    k.steps = cl.steps;
+    k.stall_checks = c->opts.stall_checks;
+    k.interval = c->opts.check_every;
+    k.max_iters = c->opts.max_iters;
+    k.tol = c->opts.tol;
+    k.keff_scale = (double)NZ /
+                   (c->s * (c->opts.t_hot - c->opts.t_cold) * (double)c->L.NX * (double)c->L.NY);
+    k.inv_area = 1.0 / ((double)c->L.NX * (double)c->L.NY);
+    k.quantum = c->quantum;
+    k.inv_quantum = 1.0 / c->quantum;
+    k.handle = cl.handle;
+    k.use_handle = cl.use_handle;
     return a;
 }
 
-cudaError_t launch_step(const lbm_ctx* c, int src, bool check, Frame fr, cudaStream_t st) {
-    const lbm::StepArgs a = step_args(c, src, fr);
+cudaError_t launch_step(const lbm_ctx* c, int src, bool check, Frame fr, cudaStream_t st,
+                        const Closing& cl = Closing()) {
+    const lbm::StepArgs a = step_args(c, src, fr, cl);
     const dim3 grid(c->blocks_per_plane, c->L.NZ);
     const size_t smem = sizeof(float4) * 2 * c->n_phases;
     if (c->lateral == LBM_LATERAL_PERIODIC) {
@@ -199,30 +234,13 @@ cudaError_t launch_step(const lbm_ctx* c, int src, bool check, Frame fr, cudaStr
     return cudaGetLastError();
 }
 
-lbm::FinalArgs final_args(const lbm_ctx* c, int steps, int interval, bool rebase) {
-    lbm::FinalArgs f;
-    std::memset(&f, 0, sizeof f);
-    f.part = c->d_part;
-    f.Q = c->d_Q;
-    f.ra = c->d_ref;
-    f.rb = c->d_ref + c->L.NZ;
-    f.rebase = rebase ? 1 : 0;
-    f.quantum = c->quantum;
-    f.inv_area = 1.0 / ((double)c->L.NX * (double)c->L.NY);
-    f.ctl = c->d_ctl;
-    f.nz = c->L.NZ;
-    f.blocks_per_plane = c->blocks_per_plane;
-    f.steps = steps;
-    f.stall_checks = c->opts.stall_checks;
-    f.max_iters = c->opts.max_iters;
-    f.interval = interval;
-    f.tol = c->opts.tol;
-    f.keff_scale = (double)c->L.NZ /
-                   (c->s * (c->opts.t_hot - c->opts.t_cold) * (double)c->L.NX * (double)c->L.NY);
-    f.t_ref = c->t_ref;
-    f.handle = 0;
-    f.use_handle = 0;
-    return f;
+// The closing of a graph or host-loop interval: the first step moved the
+// state to frame R_b, and the check closes K iterations.
+Closing interval_closing(const lbm_ctx* c) {
+    Closing cl;
+    cl.rebase = 1;
+    cl.steps = c->opts.check_every;
+    return cl;
 }
 
 template <typename T>
@@ -265,19 +283,18 @@ lbm_status read_ctl(lbm_ctx* c, cudaStream_t st) {
 }
 
 // Everything a check-interval graph bakes in: the kernel arguments of both
-// buffer parities, the finalize arguments and the lateral type.
+// buffer parities, the closing arguments and the lateral type.
 std::vector<char> graph_signature(const lbm_ctx* c, int parity) {
-    const lbm::StepArgs a = step_args(c, parity, kAB);
-    const lbm::FinalArgs f = final_args(c, c->opts.check_every, c->opts.check_every, true);
-    std::vector<char> sig(sizeof a + sizeof f + 2 * sizeof(int));
+    const lbm::StepArgs a = step_args(c, parity, kAB, interval_closing(c));
+    std::vector<char> sig(sizeof a + 2 * sizeof(int));
     std::memcpy(sig.data(), &a, sizeof a);
-    std::memcpy(sig.data() + sizeof a, &f, sizeof f);
     const int extra[2] = {c->lateral, c->opts.check_every};
-    std::memcpy(sig.data() + sizeof a + sizeof f, extra, sizeof extra);
+    std::memcpy(sig.data() + sizeof a, extra, sizeof extra);
     return sig;
 }
 
-// Builds the executable graph: while (cond) { K-1 steps; check step; finalize }.
+// Builds the executable graph: while (cond) { K-1 steps; check step }; the
+// check step's closing block sets the condition.
 lbm_status build_graph(lbm_ctx* c, int parity) {
     const int K = c->opts.check_every;
     cudaGraph_t g = nullptr;
@@ -306,16 +323,12 @@ lbm_status build_graph(lbm_ctx* c, int parity) {
                                       cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         int src = parity;
+        Closing cl = interval_closing(c);
+        cl.handle = h;
+        cl.use_handle = 1;
         for (int k = 0; k < K && e == cudaSuccess; ++k) {
-            e = launch_step(c, src, k == K - 1, k == 0 ? kAB : kBB, c->cap_stream);
+            e = launch_step(c, src, k == K - 1, k == 0 ? kAB : kBB, c->cap_stream, cl);
             src ^= 1;
-        }
-        if (e == cudaSuccess) {
-            lbm::FinalArgs f = final_args(c, K, K, true);
-            f.handle = h;
-            f.use_handle = 1;
-            lbm::finalize_kernel<<<1, lbm::kFinalThreads, 0, c->cap_stream>>>(f);
-            e = cudaGetLastError();
         }
         cudaGraph_t captured = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &captured);
@@ -493,7 +506,8 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
     if ((st = ensure(c, &c->d_f[1], (size_t)(7 * cells), &c->cap_f[1])) != LBM_OK) return st;
     if ((st = ensure(c, &c->d_phase_c, (size_t)cells, &c->cap_phase_c)) != LBM_OK) return st;
     if ((st = ensure(c, &c->d_tsnap, (size_t)cells, &c->cap_tsnap)) != LBM_OK) return st;
-    if ((st = ensure(c, &c->d_ref, (size_t)2 * L.NZ, &c->cap_ref)) != LBM_OK) return st;
+    if ((st = ensure(c, &c->d_ref, (size_t)5 * L.NZ, &c->cap_ref)) != LBM_OK) return st;
+    if ((st = ensure(c, &c->d_plane_cnt, (size_t)L.NZ, &c->cap_cnt)) != LBM_OK) return st;
     size_t cap_sb = (size_t)c->cap_sb;
     if ((st = ensure(c, &c->d_sb, sb.size(), &cap_sb)) != LBM_OK) return st;
     c->cap_sb = (int)cap_sb;
@@ -502,7 +516,7 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
     if ((st = ensure(c, &c->d_part, (size_t)4 * L.NZ * c->blocks_per_plane, &c->cap_part)) != LBM_OK)
         return st;
     size_t capQ = (size_t)c->cap_Q;
-    if ((st = ensure(c, &c->d_Q, (size_t)L.NZ, &capQ)) != LBM_OK) return st;
+    if ((st = ensure(c, &c->d_Q, (size_t)3 * L.NZ, &capQ)) != LBM_OK) return st;
     c->cap_Q = (int)capQ;
     c->Q_host.assign(L.NZ, 0.0);
 
@@ -544,16 +558,22 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
         for (int z = 0; z < L.NZ; ++z)
             mean[z] = op.t_hot + (op.t_cold - op.t_hot) * ((double)z + 0.5) / (double)L.NZ;
     }
-    c->h_ref.assign(2 * (size_t)L.NZ, 0.f);
+    c->h_ref.assign(5 * (size_t)L.NZ, 0.f);
     for (int z = 0; z < L.NZ; ++z) {
-        const float r = (float)(std::nearbyint(mean[z] / c->quantum) * c->quantum);
-        c->h_ref[z] = r;
-        c->h_ref[L.NZ + z] = r;
+        const double r = std::nearbyint(mean[z] / c->quantum) * c->quantum;
+        const double T0 = op.t_hot + (op.t_cold - op.t_hot) * ((double)z + 0.5) / (double)L.NZ;
+        c->h_ref[z] = (float)r;
+        c->h_ref[L.NZ + z] = (float)r;
+        c->h_ref[2 * L.NZ + z] = (float)r;
+        c->h_ref[3 * L.NZ + z] = (float)(T0 - r);
+        c->h_ref[4 * L.NZ + z] = (float)(T0 - c->t_ref);
     }
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_ref, c->h_ref.data(), sizeof(float) * 2 * L.NZ,
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_ref, c->h_ref.data(), sizeof(float) * 5 * L.NZ,
                                 cudaMemcpyHostToDevice, stm));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_plane_cnt, 0, sizeof(int) * L.NZ, stm));
     lbm::init_kernel<<<grid_1d(cells), 256, 0, stm>>>(c->d_f[0], c->d_tsnap, cells, L, c->d_ref,
-                                                      op.t_hot, op.t_cold, c->t_ref, tinit);
+                                                      c->d_ref + 3 * L.NZ, c->d_ref + 4 * L.NZ,
+                                                      (float)c->t_ref, tinit);
     CUDA_TRY(c, cudaGetLastError());
     Ctl h{};
     h.best_rt = INFINITY;
@@ -590,9 +610,6 @@ lbm_status lbm_check(lbm_ctx* c, lbm_solve_info* info) {
     CUDA_TRY(c, cudaEventRecord(c->ev0, c->stream));
     CUDA_TRY(c, launch_step(c, c->cur, true, kAA, c->stream));
     c->cur ^= 1;
-    lbm::FinalArgs f = final_args(c, 1, c->opts.check_every, false);
-    lbm::finalize_kernel<<<1, lbm::kFinalThreads, 0, c->stream>>>(f);
-    CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaEventRecord(c->ev1, c->stream));
     lbm_status st = read_ctl(c, c->stream);
     if (st != LBM_OK) return st;
@@ -621,12 +638,10 @@ lbm_status lbm_run(lbm_ctx* c, lbm_solve_info* info) {
         // back after every interval
         do {
             for (int k = 0; k < K; ++k) {
-                CUDA_TRY(c, launch_step(c, c->cur, k == K - 1, k == 0 ? kAB : kBB, c->stream));
+                CUDA_TRY(c, launch_step(c, c->cur, k == K - 1, k == 0 ? kAB : kBB, c->stream,
+                                        interval_closing(c)));
                 c->cur ^= 1;
             }
-            lbm::FinalArgs f = final_args(c, K, K, true);
-            lbm::finalize_kernel<<<1, lbm::kFinalThreads, 0, c->stream>>>(f);
-            CUDA_TRY(c, cudaGetLastError());
             CUDA_TRY(c, cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost,
                                         c->stream));
             CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -719,6 +734,7 @@ void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->d_sb);
     cudaFree(c->d_part);
     cudaFree(c->d_Q);
+    cudaFree(c->d_plane_cnt);
     cudaFree(c->d_T);
     cudaFree(c->d_phase);
     cudaFree(c->d_ctl);

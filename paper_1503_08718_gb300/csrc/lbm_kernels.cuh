@@ -34,25 +34,7 @@
 namespace lbm {
 
 constexpr int kThreads = 256;        // threads per step block
-constexpr int kFinalThreads = 512;   // threads of the finalize block
 constexpr unsigned kFull = 0xffffffffu;
-
-struct StepArgs {
-    const float* __restrict__ src;   // 7 populations, post-collision state n-1
-    float* __restrict__ dst;         // 7 populations, post-collision state n
-    const uint8_t* __restrict__ phase;  // [nz][ny][pitch], padded with 0
-    const float4* __restrict__ sb;   // 2 float4 per phase: (xx, yy, zz, yz), (xz, xy, -, -)
-    double* __restrict__ part;       // check partials [4][nz][blocks_per_plane]
-    float* __restrict__ tsnap;       // T - T_ref at the previous check, [nz][ny][pitch]
-    const float* __restrict__ rsrc;  // reference R(z) of the src state, [nz]
-    const float* __restrict__ rdst;  // reference R(z) of the dst state, [nz]
-    long long pstride;               // floats per population = pitch * ny * nz
-    int nx, ny, nz, pitch, n_phases;
-    int quads_per_plane;             // (pitch / 4) * ny
-    int blocks_per_plane;
-    float eps_hot, eps_cold;         // eps * T_wall
-    double t_ref;                    // offset of the residual snapshot
-};
 
 struct Ctl {
     long long iter;      // iterations since start
@@ -62,28 +44,48 @@ struct Ctl {
     int status;          // lbm_status of the last check
     int since_best;
     int done;
-    int pad;
+    unsigned glob_cnt;   // planes closed in the current check (0 between checks)
 };
 
-struct FinalArgs {
-    const double* __restrict__ part;
-    double* __restrict__ Q;          // [nz]
-    float* ra;                       // reference of the state after the interval
-    float* rb;                       // reference of the next interval, [nz]
-    int rebase;                      // the interval's first step moved the state to rb
-    double quantum;                  // grid of the reference values (power of two)
-    double inv_area;                 // 1 / (nx * ny)
+// What the blocks that close a check need: per-plane and global reductions,
+// the next reference frame and the stop rule.
+struct CheckArgs {
+    double* part;                    // block partials [4][nz][blocks_per_plane]
+    double* Q;                       // plane flux sums [nz]
+    double* plane;                   // per-plane sum |dT| [nz] and sum |T| [nz]
+    int* plane_cnt;                  // closing tickets per plane [nz], 0 between checks
     Ctl* ctl;
-    int nz, blocks_per_plane;
-    int steps;                       // iterations covered by this check interval
+    float* ra;                       // frame of the state between calls [nz]
+    float* rb;                       // frame of the next interval [nz]
+    float* rc;                       // staging of the new plane means [nz]
+    int rebase;                      // the interval's first step moved the state to rb
+    int steps;                       // iterations this check closes
     int stall_checks;
-    long long max_iters;
     int interval;                    // steps the next interval would add
+    long long max_iters;
     double tol;
     double keff_scale;               // nz / (s * dT * nx * ny)
-    double t_ref;
+    double inv_area;                 // 1 / (nx * ny)
+    double quantum, inv_quantum;     // grid of the reference values (power of two)
     cudaGraphConditionalHandle handle;
     int use_handle;
+};
+
+struct StepArgs {
+    const float* __restrict__ src;   // 7 populations, post-collision state n-1
+    float* __restrict__ dst;         // 7 populations, post-collision state n
+    const uint8_t* __restrict__ phase;  // [nz][ny][pitch], padded with 0
+    const float4* __restrict__ sb;   // 2 float4 per phase: (xx, yy, zz, yz), (xz, xy, -, -)
+    float* __restrict__ tsnap;       // T - T_ref at the previous check, [nz][ny][pitch]
+    const float* __restrict__ rsrc;  // reference R(z) of the src state, [nz]
+    const float* __restrict__ rdst;  // reference R(z) of the dst state, [nz]
+    long long pstride;               // floats per population = pitch * ny * nz
+    int nx, ny, nz, pitch, n_phases;
+    int quads_per_plane;             // (pitch / 4) * ny
+    int blocks_per_plane;
+    float eps_hot, eps_cold;         // eps * T_wall
+    double t_ref;                    // offset of the residual snapshot
+    CheckArgs ck;
 };
 
 __device__ __forceinline__ float4 ld4(const float* p) {
@@ -103,6 +105,120 @@ __device__ __forceinline__ void set_comp(float4& v, int k, float s) {
     else if (k == 1) v.y = s;
     else if (k == 2) v.z = s;
     else v.w = s;
+}
+
+// Closing a check (Eq. 15-16 plane sums, Eq. 22, the stop rule).  Every
+// block of a check step writes its FP64 partials and takes a ticket on its
+// plane's counter; the block that takes the last ticket sums the plane's
+// partials in block order, and the block that closes the last plane sums the
+// planes in plane order and applies the stop rule.  No block ever waits:
+// the work falls to whichever block finishes last, and the result is
+// deterministic.
+
+__device__ void close_check(const StepArgs& a) {
+    const CheckArgs& ck = a.ck;
+    double qsum = 0.0, qmax = -INFINITY, qmin = INFINITY, dsum = 0.0, tsum = 0.0;
+    for (int z = threadIdx.x; z < a.nz; z += kThreads) {
+        const double q = __ldcg(ck.Q + z);
+        qsum += q;
+        qmax = fmax(qmax, q);
+        qmin = fmin(qmin, q);
+        dsum += __ldcg(ck.plane + z);
+        tsum += __ldcg(ck.plane + a.nz + z);
+    }
+    __shared__ double s[5][kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        qsum += __shfl_down_sync(kFull, qsum, off);
+        qmax = fmax(qmax, __shfl_down_sync(kFull, qmax, off));
+        qmin = fmin(qmin, __shfl_down_sync(kFull, qmin, off));
+        dsum += __shfl_down_sync(kFull, dsum, off);
+        tsum += __shfl_down_sync(kFull, tsum, off);
+    }
+    if (lane == 0) {
+        s[0][warp] = qsum; s[1][warp] = qmax; s[2][warp] = qmin; s[3][warp] = dsum; s[4][warp] = tsum;
+    }
+    __syncthreads();
+    // rotate the reference frames: every block of this kernel has finished
+    // reading them (their tickets were all taken)
+    for (int z = threadIdx.x; z < a.nz; z += kThreads) {
+        if (ck.rebase) ck.ra[z] = ck.rb[z];
+        ck.rb[z] = __ldcg(ck.rc + z);
+    }
+    if (threadIdx.x == 0) {
+        qsum = 0.0; qmax = -INFINITY; qmin = INFINITY; dsum = 0.0; tsum = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            qsum += s[0][w];
+            qmax = fmax(qmax, s[1][w]);
+            qmin = fmin(qmin, s[2][w]);
+            dsum += s[3][w];
+            tsum += s[4][w];
+        }
+        Ctl* c = ck.ctl;
+        const double mean = qsum / (double)a.nz;
+        c->iter += ck.steps;
+        c->checks += 1;
+        c->k_eff = ck.keff_scale * mean;
+        c->r_q = (qmax - qmin) / fabs(mean);
+        // mean per-step change of T since the previous check, relative to T
+        c->r_t = dsum / ((double)(c->iter - c->iter_snap) * tsum);
+        c->iter_snap = c->iter;
+        int status;
+        if (!isfinite(c->r_t) || !isfinite(c->k_eff)) {
+            status = 6;                                   // LBM_ERR_DIVERGED
+        } else if (c->r_t <= ck.tol) {
+            status = 0;                                   // LBM_OK (converged)
+        } else {
+            if (c->r_t < c->best_rt) {
+                c->best_rt = c->r_t;
+                c->since_best = 0;
+            } else {
+                c->since_best += 1;
+            }
+            if (ck.stall_checks > 0 && c->since_best >= ck.stall_checks) status = 7;   // STALLED
+            else status = 5;                              // LBM_ERR_NOT_CONVERGED (so far)
+        }
+        c->status = status;
+        const bool stop = status != 5 || c->iter + ck.interval > ck.max_iters;
+        c->done = stop ? 1 : 0;
+        c->glob_cnt = 0u;
+        if (ck.use_handle) cudaGraphSetConditional(ck.handle, stop ? 0u : 1u);
+    }
+}
+
+__device__ void close_plane(const StepArgs& a, int z) {
+    const CheckArgs& ck = a.ck;
+    __shared__ int s_last_plane;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const long long plane_all = (long long)a.nz * a.blocks_per_plane;
+        const long long base = (long long)z * a.blocks_per_plane;
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int b = lane; b < a.blocks_per_plane; b += 32)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) v[m] += __ldcg(ck.part + m * plane_all + base + b);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) v[m] += __shfl_down_sync(kFull, v[m], off);
+        if (lane == 0) {
+            ck.Q[z] = v[0];
+            ck.plane[z] = v[1];
+            ck.plane[a.nz + z] = v[2];
+            // next reference: the plane mean of T on the quantum grid
+            ck.rc[z] = (float)(nearbyint(v[3] * ck.inv_area * ck.inv_quantum) * ck.quantum);
+            ck.plane_cnt[z] = 0;
+            __threadfence();
+            const unsigned ticket = atomicAdd(&ck.ctl->glob_cnt, 1u);
+            s_last_plane = ticket == (unsigned)a.nz - 1u;
+        }
+    }
+    __syncthreads();
+    if (s_last_plane) {
+        __threadfence();
+        close_check(a);
+    }
 }
 
 // One fused pull-stream + collide step over 4 consecutive voxels of a row per
@@ -188,10 +304,13 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
     const int n_real = active ? min(4, a.nx - x0) : 0;
     float4 o0v, o1v, o2v, o3v, o4v, o5v, o6v;
     float4 thv, thp = make_float4(0.f, 0.f, 0.f, 0.f);
-    double q_sum = 0.0, dT_sum = 0.0, T_sum = 0.0, Tp_sum = 0.0;
+    // per-thread (4 voxels) and per-warp sums of positive FP32 terms stay in
+    // FP32; the block tree, the plane sums and the residual sums are FP64
+    float q_sum = 0.f, dT_sum = 0.f, T_sum = 0.f, Tp_sum = 0.f;
     // T - T_ref at the previous check: the residual is the change since then
     if (CHECK && active) thp = *reinterpret_cast<const float4*>(a.tsnap + row + x0);
-    const double dref = (double)rd - a.t_ref;
+    const float dref = (float)((double)rd - a.t_ref);
+    const float tref = (float)a.t_ref;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const float g0 = comp(c0, k), g1 = comp(f1, k), g2 = comp(f2, k), g3 = comp(c3, k);
@@ -217,13 +336,13 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
         set_comp(o5v, k, real ? fmaf(0.5f, hz, t8) : 0.f);
         set_comp(o6v, k, real ? fmaf(-0.5f, hz, t8) : 0.f);
         if (CHECK) {
-            const double tdev = (double)th + dref;          // T - T_ref
-            set_comp(thv, k, real ? (float)tdev : 0.f);
+            const float tdev = th + dref;                    // T - T_ref
+            set_comp(thv, k, real ? tdev : 0.f);
             if (real) {
-                q_sum += (double)fmaf(-0.5f, sz, jz);      // (j_z + jhat_z) / 2
-                dT_sum += fabs(tdev - (double)comp(thp, k));
-                T_sum += fabs(tdev + a.t_ref);
-                Tp_sum += tdev + a.t_ref;
+                q_sum += fmaf(-0.5f, sz, jz);                // (j_z + jhat_z) / 2
+                dT_sum += fabsf(tdev - comp(thp, k));
+                T_sum += fabsf(tdev + tref);
+                Tp_sum += tdev + tref;
             }
         }
     }
@@ -242,16 +361,18 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
     if (CHECK) {
         // warp shuffle, then a tree over the block's warps: one FP64 partial
         // per (block, plane) written in a fixed order (deterministic)
-        double v[4] = {q_sum, dT_sum, T_sum, Tp_sum};
+        float vf[4] = {q_sum, dT_sum, T_sum, Tp_sum};
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
-            for (int m = 0; m < 4; ++m) v[m] += __shfl_down_sync(kFull, v[m], off);
+            for (int m = 0; m < 4; ++m) vf[m] += __shfl_down_sync(kFull, vf[m], off);
+        double v[4];
         __shared__ double s_red[4][kThreads / 32];
+        __shared__ int s_last;
         const int warp = threadIdx.x >> 5;
         if (lane == 0)
 #pragma unroll
-            for (int m = 0; m < 4; ++m) s_red[m][warp] = v[m];
+            for (int m = 0; m < 4; ++m) s_red[m][warp] = (double)vf[m];
         __syncthreads();
         if (threadIdx.x < 32) {
 #pragma unroll
@@ -261,90 +382,19 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
 #pragma unroll
                 for (int m = 0; m < 4; ++m) v[m] += __shfl_down_sync(kFull, v[m], off);
             if (lane == 0) {
+                const CheckArgs& ck = a.ck;
                 const long long base = (long long)z * a.blocks_per_plane + blockIdx.x;
                 const long long plane_all = (long long)a.nz * a.blocks_per_plane;
 #pragma unroll
-                for (int m = 0; m < 4; ++m) a.part[m * plane_all + base] = v[m];
+                for (int m = 0; m < 4; ++m) ck.part[m * plane_all + base] = v[m];
+                // the last block of this plane to finish closes the plane
+                __threadfence();
+                const int ticket = atomicAdd(&ck.plane_cnt[z], 1);
+                s_last = ticket == a.blocks_per_plane - 1;
             }
         }
-    }
-}
-
-// Plane sums Q[k], the mean flux, R_Q, R_T and k_eff (Eq. 22), then the stop
-// rule; in a graph it sets the while-condition of the enclosing loop.
-__global__ void __launch_bounds__(kFinalThreads) finalize_kernel(const FinalArgs a) {
-    double qsum = 0.0, qmax = -INFINITY, qmin = INFINITY, dsum = 0.0, tsum = 0.0;
-    const long long plane_all = (long long)a.nz * a.blocks_per_plane;
-    for (int z = threadIdx.x; z < a.nz; z += kFinalThreads) {
-        double q = 0.0, d = 0.0, t = 0.0, tp = 0.0;
-        const long long base = (long long)z * a.blocks_per_plane;
-        for (int b = 0; b < a.blocks_per_plane; ++b) {
-            q += a.part[base + b];
-            d += a.part[plane_all + base + b];
-            t += a.part[2 * plane_all + base + b];
-            tp += a.part[3 * plane_all + base + b];
-        }
-        a.Q[z] = q;
-        qsum += q;
-        qmax = fmax(qmax, q);
-        qmin = fmin(qmin, q);
-        dsum += d;
-        tsum += t;
-        // next reference: the plane mean of T on the quantum grid
-        if (a.rebase) a.ra[z] = a.rb[z];
-        a.rb[z] = (float)(nearbyint(tp * a.inv_area / a.quantum) * a.quantum);
-    }
-    __shared__ double s[5][kFinalThreads / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        qsum += __shfl_down_sync(kFull, qsum, off);
-        qmax = fmax(qmax, __shfl_down_sync(kFull, qmax, off));
-        qmin = fmin(qmin, __shfl_down_sync(kFull, qmin, off));
-        dsum += __shfl_down_sync(kFull, dsum, off);
-        tsum += __shfl_down_sync(kFull, tsum, off);
-    }
-    if (lane == 0) {
-        s[0][warp] = qsum; s[1][warp] = qmax; s[2][warp] = qmin; s[3][warp] = dsum; s[4][warp] = tsum;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        qsum = 0.0; qmax = -INFINITY; qmin = INFINITY; dsum = 0.0; tsum = 0.0;
-        for (int w = 0; w < kFinalThreads / 32; ++w) {
-            qsum += s[0][w];
-            qmax = fmax(qmax, s[1][w]);
-            qmin = fmin(qmin, s[2][w]);
-            dsum += s[3][w];
-            tsum += s[4][w];
-        }
-        Ctl* c = a.ctl;
-        const double mean = qsum / (double)a.nz;
-        c->iter += a.steps;
-        c->checks += 1;
-        c->k_eff = a.keff_scale * mean;
-        c->r_q = (qmax - qmin) / fabs(mean);
-        // mean per-step change of T since the previous check, relative to T
-        c->r_t = dsum / ((double)(c->iter - c->iter_snap) * tsum);
-        c->iter_snap = c->iter;
-        int status;
-        if (!isfinite(c->r_t) || !isfinite(c->k_eff)) {
-            status = 6;                                   // LBM_ERR_DIVERGED
-        } else if (c->r_t <= a.tol) {
-            status = 0;                                   // LBM_OK (converged)
-        } else {
-            if (c->r_t < c->best_rt) {
-                c->best_rt = c->r_t;
-                c->since_best = 0;
-            } else {
-                c->since_best += 1;
-            }
-            if (a.stall_checks > 0 && c->since_best >= a.stall_checks) status = 7;   // STALLED
-            else status = 5;                              // LBM_ERR_NOT_CONVERGED (so far)
-        }
-        c->status = status;
-        const bool stop = status != 5 || c->iter + a.interval > a.max_iters;
-        c->done = stop ? 1 : 0;
-        if (a.use_handle) cudaGraphSetConditional(a.handle, stop ? 0u : 1u);
+        __syncthreads();
+        if (s_last) close_plane(a, z);
     }
 }
 
@@ -380,9 +430,12 @@ __global__ void permute_phase_kernel(const uint8_t* __restrict__ in, uint8_t* __
 
 // Initial state fhat^0 = f^eq(T0) (Eq. 6) as deviations from w_i T_ref.
 // T0 is the linear profile between the walls, or a given field (original order).
+// plane_th[z] = T0(z) - R(z) and plane_ts[z] = T0(z) - T_ref for the linear
+// start (host FP64, rounded once); a caller field t_init replaces T0.
 __global__ void init_kernel(float* __restrict__ f, float* __restrict__ tsnap, long long P, Layout L,
-                            const float* __restrict__ ref, double t_hot, double t_cold,
-                            double t_ref, const float* __restrict__ t_init) {
+                            const float* __restrict__ ref, const float* __restrict__ plane_th,
+                            const float* __restrict__ plane_ts, float t_ref,
+                            const float* __restrict__ t_init) {
     const long long total = (long long)L.pitch * L.NY * L.NZ;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -390,13 +443,18 @@ __global__ void init_kernel(float* __restrict__ f, float* __restrict__ tsnap, lo
         const long long r = i / L.pitch;
         const int yc = (int)(r % L.NY);
         const int zc = (int)(r / L.NY);
-        double T = t_ref;
+        float th = 0.f, ts = 0.f;
         if (xc < L.NX) {
-            T = t_init ? (double)t_init[orig_index(L, xc, yc, zc)]
-                       : t_hot + (t_cold - t_hot) * ((double)zc + 0.5) / (double)L.NZ;
+            if (t_init) {
+                const float T = t_init[orig_index(L, xc, yc, zc)];
+                th = T - ref[zc];
+                ts = T - t_ref;
+            } else {
+                th = plane_th[zc];
+                ts = plane_ts[zc];
+            }
         }
-        const float th = xc < L.NX ? (float)(T - (double)ref[zc]) : 0.f;
-        tsnap[i] = xc < L.NX ? (float)(T - t_ref) : 0.f;
+        tsnap[i] = ts;
         f[i] = 0.25f * th;
         const float e = 0.125f * th;
         for (int q = 1; q < 7; ++q) f[q * P + i] = e;
