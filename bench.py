@@ -40,7 +40,8 @@ NX, NY, NZ = 128, 128, 256
 G_DEG, PHI, SEED, NMAX = 30.0, 0.45, 42, 128
 K = 100
 ITERS = 1000
-BYTES_PER_LUP = 57          # 7 x 4 B read + 7 x 4 B written + 1 B phase id
+BYTES_PER_LUP = {"f32": 57, "bf16": 29, "f16": 29}   # 7 values read + 7 written + 1 B phase id
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 WORKLOAD = (f"braid {NX}x{NY}x{NZ} g=30deg phi=0.45 seed=42, dT along z, periodic laterals, "
             f"FP32 D3Q7 MRT")
 
@@ -194,7 +195,8 @@ def run_ours(args):
     S, lam, used, frac = make_cell(lbm, I, dev)
     stream = torch.cuda.Stream(device=dev)
     iters = args.iters
-    opts = S.opts(tol=0.0, max_iters=iters, check_every=K, host_loop=int(args.launch == "host"))
+    opts = S.opts(tol=0.0, max_iters=iters, check_every=K, host_loop=int(args.launch == "host"),
+                  storage=STORAGE[args.storage])
     opts.stream = int(stream.cuda_stream)
 
     def one_step():
@@ -232,7 +234,7 @@ def run_ours(args):
     # roofline of the dominant kernel (the fused step): algorithmic bytes per
     # launch over the average launch time of the timed region
     per_launch_s = (ms / 1000.0) / (args.steps * iters)
-    achieved = BYTES_PER_LUP * n_vox / per_launch_s / 1e9
+    achieved = BYTES_PER_LUP[args.storage] * n_vox / per_launch_s / 1e9
     peak, peak_kind = peaks()
 
     # end to end through the public API with host buffers
@@ -266,15 +268,17 @@ def run_ours(args):
             "metric": "GLUPS", "value": glups, "unit": "GLUPS", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else f"f32 (storage {args.storage})",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "iters_per_step": iters, "check_every": K,
+                       "storage": args.storage,
                        "launch": args.launch,
                        "yarns": used, "yarn_fraction": round(frac, 6),
                        "l2": "inputs larger than L2 (f buffers 2 x 117 MB)",
                        "parallelism": f"replicas{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": args.traffic,
-                         "peak_source": peak_kind, "bytes_per_lup": BYTES_PER_LUP},
+                         "peak_source": peak_kind, "bytes_per_lup": BYTES_PER_LUP[args.storage]},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_glups, "unit": "GLUPS",
                     "h2d_bytes_per_step": n_vox + lam.nbytes,
@@ -300,6 +304,8 @@ def main():
     ap.add_argument("--launch", default="graph", choices=["graph", "host"],
                     help="graph: one CUDA graph per step with a device-side while node; "
                          "host: the same kernels launched from the host (for profilers)")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
+                    help="distribution storage (collision is FP32 in every mode)")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline leg")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--traffic", type=float, default=None,

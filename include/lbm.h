@@ -59,7 +59,10 @@ typedef enum {
 
 typedef enum { LBM_AXIS_X = 0, LBM_AXIS_Y = 1, LBM_AXIS_Z = 2 } lbm_axis;
 typedef enum { LBM_LATERAL_PERIODIC = 0, LBM_LATERAL_ADIABATIC = 1 } lbm_lateral;
-typedef enum { LBM_STORE_F32 = 0 } lbm_storage;
+/* Storage of the distributions between steps; the collision is FP32 in every
+ * mode.  BF16 and FP16 halve the memory traffic (29 instead of 57 bytes per
+ * lattice update) and are rounded stochastically on store. */
+typedef enum { LBM_STORE_F32 = 0, LBM_STORE_BF16 = 1, LBM_STORE_F16 = 2 } lbm_storage;
 
 typedef struct {
     double t_hot, t_cold;   /* wall temperatures (defaults 1, 0); t_hot != t_cold */
@@ -70,7 +73,7 @@ typedef struct {
     int32_t check_every;    /* K: steps per check interval, even, in [2, 4096] (default 100) */
     int32_t stall_checks;   /* stop with LBM_ERR_STALLED after this many checks
                                without a new smallest R_T; 0 disables (default 0) */
-    int32_t storage;        /* lbm_storage; LBM_STORE_F32 */
+    int32_t storage;        /* lbm_storage (default LBM_STORE_F32) */
     int32_t host_loop;      /* 0 (default): lbm_run drives the check intervals with one
                                CUDA graph and a device-side while condition; 1: the host
                                launches each interval and reads the stop flag after it

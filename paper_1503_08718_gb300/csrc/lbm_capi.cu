@@ -41,8 +41,9 @@ struct lbm_ctx {
     lbm_solve_opts opts{};
     cudaStream_t stream = nullptr;         // stream used by the current solve
     Layout L{};
-    float* d_f[2] = {nullptr, nullptr};
-    size_t cap_f[2] = {0, 0};              // capacity of the f buffers (floats)
+    char* d_f[2] = {nullptr, nullptr};     // distributions (4 or 2 bytes per value)
+    size_t cap_f[2] = {0, 0};              // capacity of the f buffers (bytes)
+    int fmt = 0;                           // lbm_storage of the current solve
     int cur = 0;                           // buffer holding the current state
     uint8_t* d_phase_c = nullptr;          // canonical padded phase map
     size_t cap_phase_c = 0;
@@ -163,6 +164,7 @@ enum Frame { kAA = 0, kAB = 1, kBB = 2 };
 // How a check step closes: which frames rotate, how many iterations it
 // closes and whether it drives a graph's while condition.
 struct Closing {
+    unsigned rseed = 0;                    // launch salt of the stochastic rounding
     int rebase = 0;
     int steps = 1;
     cudaGraphConditionalHandle handle = 0;
@@ -188,12 +190,13 @@ lbm::StepArgs step_args(const lbm_ctx* c, int src, Frame fr, const Closing& cl =
     a.nz = NZ;
     a.pitch = c->L.pitch;
     a.n_phases = c->n_phases;
-    a.quads_per_plane = (c->L.pitch / 4) * c->L.NY;
+    a.quads_per_plane = (c->L.pitch / (c->fmt == LBM_STORE_F32 ? 4 : 8)) * c->L.NY;
     a.blocks_per_plane = c->blocks_per_plane;
     const double eps = 0.25;
     a.eps_hot = (float)(eps * c->opts.t_hot);
     a.eps_cold = (float)(eps * c->opts.t_cold);
     a.t_ref = c->t_ref;
+    a.rseed = cl.rseed;
     lbm::CheckArgs& k = a.ck;
     k.part = c->d_part;
     k.Q = c->d_Q;
@@ -219,18 +222,35 @@ lbm::StepArgs step_args(const lbm_ctx* c, int src, Frame fr, const Closing& cl =
     return a;
 }
 
+template <int FMT, bool RAGGED>
+void launch_fmt(const lbm::StepArgs& a, bool periodic, bool check, dim3 grid, size_t smem,
+                cudaStream_t st) {
+    if (periodic) {
+        if (check) lbm::step_kernel<FMT, true, true, RAGGED><<<grid, lbm::kThreads, smem, st>>>(a);
+        else lbm::step_kernel<FMT, true, false, RAGGED><<<grid, lbm::kThreads, smem, st>>>(a);
+    } else {
+        if (check) lbm::step_kernel<FMT, false, true, RAGGED><<<grid, lbm::kThreads, smem, st>>>(a);
+        else lbm::step_kernel<FMT, false, false, RAGGED><<<grid, lbm::kThreads, smem, st>>>(a);
+    }
+}
+
+template <int FMT>
+void launch_fmt(const lbm::StepArgs& a, bool periodic, bool check, bool ragged, dim3 grid,
+                size_t smem, cudaStream_t st) {
+    if (ragged) launch_fmt<FMT, true>(a, periodic, check, grid, smem, st);
+    else launch_fmt<FMT, false>(a, periodic, check, grid, smem, st);
+}
+
 cudaError_t launch_step(const lbm_ctx* c, int src, bool check, Frame fr, cudaStream_t st,
                         const Closing& cl = Closing()) {
     const lbm::StepArgs a = step_args(c, src, fr, cl);
     const dim3 grid(c->blocks_per_plane, c->L.NZ);
     const size_t smem = sizeof(float4) * 2 * c->n_phases;
-    if (c->lateral == LBM_LATERAL_PERIODIC) {
-        if (check) lbm::step_kernel<true, true><<<grid, lbm::kThreads, smem, st>>>(a);
-        else lbm::step_kernel<true, false><<<grid, lbm::kThreads, smem, st>>>(a);
-    } else {
-        if (check) lbm::step_kernel<false, true><<<grid, lbm::kThreads, smem, st>>>(a);
-        else lbm::step_kernel<false, false><<<grid, lbm::kThreads, smem, st>>>(a);
-    }
+    const bool periodic = c->lateral == LBM_LATERAL_PERIODIC;
+    const bool ragged = c->L.NX != c->L.pitch;
+    if (c->fmt == LBM_STORE_BF16) launch_fmt<1>(a, periodic, check, ragged, grid, smem, st);
+    else if (c->fmt == LBM_STORE_F16) launch_fmt<2>(a, periodic, check, ragged, grid, smem, st);
+    else launch_fmt<0>(a, periodic, check, ragged, grid, smem, st);
     return cudaGetLastError();
 }
 
@@ -327,6 +347,7 @@ lbm_status build_graph(lbm_ctx* c, int parity) {
         cl.handle = h;
         cl.use_handle = 1;
         for (int k = 0; k < K && e == cudaSuccess; ++k) {
+            cl.rseed = (unsigned)k;
             e = launch_step(c, src, k == K - 1, k == 0 ? kAB : kBB, c->cap_stream, cl);
             src ^= 1;
         }
@@ -456,7 +477,8 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
     if (op.check_every < 2 || (op.check_every & 1) || op.check_every > 4096)
         return fail(c, LBM_ERR_INVALID_ARG, "check_every must be even and in [2, 4096]");
     if (op.max_iters < 0) return fail(c, LBM_ERR_INVALID_ARG, "max_iters must be >= 0");
-    if (op.storage != LBM_STORE_F32) return fail(c, LBM_ERR_INVALID_ARG, "unsupported storage");
+    if (op.storage != LBM_STORE_F32 && op.storage != LBM_STORE_BF16 && op.storage != LBM_STORE_F16)
+        return fail(c, LBM_ERR_INVALID_ARG, "unsupported storage");
     if (!(op.lattice_scale > 0.0) && !(op.tau_max > 0.5))
         return fail(c, LBM_ERR_INVALID_ARG, "tau_max must exceed 1/2");
     CUDA_TRY(c, cudaSetDevice(c->device));
@@ -480,7 +502,9 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
     L.NX = c->n[L.perm[0]];
     L.NY = c->n[L.perm[1]];
     L.NZ = c->n[L.perm[2]];
-    L.pitch = (L.NX + 3) & ~3;
+    const int V = op.storage == LBM_STORE_F32 ? 4 : 8;       // voxels per thread
+    const size_t esize = op.storage == LBM_STORE_F32 ? 4 : 2;
+    L.pitch = (L.NX + V - 1) / V * V;
     if (L.NZ > 65535)
         return fail(c, LBM_ERR_INVALID_ARG, "the temperature-difference axis may have at most 65535 nodes");
     std::vector<float4> sb(2 * (size_t)c->n_phases);
@@ -502,8 +526,8 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
     // buffers
     const long long cells = (long long)L.pitch * L.NY * L.NZ;
     lbm_status st;
-    if ((st = ensure(c, &c->d_f[0], (size_t)(7 * cells), &c->cap_f[0])) != LBM_OK) return st;
-    if ((st = ensure(c, &c->d_f[1], (size_t)(7 * cells), &c->cap_f[1])) != LBM_OK) return st;
+    if ((st = ensure(c, &c->d_f[0], (size_t)(7 * cells) * esize, &c->cap_f[0])) != LBM_OK) return st;
+    if ((st = ensure(c, &c->d_f[1], (size_t)(7 * cells) * esize, &c->cap_f[1])) != LBM_OK) return st;
     if ((st = ensure(c, &c->d_phase_c, (size_t)cells, &c->cap_phase_c)) != LBM_OK) return st;
     if ((st = ensure(c, &c->d_tsnap, (size_t)cells, &c->cap_tsnap)) != LBM_OK) return st;
     if ((st = ensure(c, &c->d_ref, (size_t)5 * L.NZ, &c->cap_ref)) != LBM_OK) return st;
@@ -511,7 +535,7 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
     size_t cap_sb = (size_t)c->cap_sb;
     if ((st = ensure(c, &c->d_sb, sb.size(), &cap_sb)) != LBM_OK) return st;
     c->cap_sb = (int)cap_sb;
-    const int quads = (L.pitch / 4) * L.NY;
+    const int quads = (L.pitch / V) * L.NY;
     c->blocks_per_plane = (quads + lbm::kThreads - 1) / lbm::kThreads;
     if ((st = ensure(c, &c->d_part, (size_t)4 * L.NZ * c->blocks_per_plane, &c->cap_part)) != LBM_OK)
         return st;
@@ -521,6 +545,7 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
     c->Q_host.assign(L.NZ, 0.0);
 
     c->opts = op;
+    c->fmt = op.storage;
     c->axis = axis;
     c->lateral = lateral;
     c->L = L;
@@ -571,9 +596,20 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
     CUDA_TRY(c, cudaMemcpyAsync(c->d_ref, c->h_ref.data(), sizeof(float) * 5 * L.NZ,
                                 cudaMemcpyHostToDevice, stm));
     CUDA_TRY(c, cudaMemsetAsync(c->d_plane_cnt, 0, sizeof(int) * L.NZ, stm));
-    lbm::init_kernel<<<grid_1d(cells), 256, 0, stm>>>(c->d_f[0], c->d_tsnap, cells, L, c->d_ref,
-                                                      c->d_ref + 3 * L.NZ, c->d_ref + 4 * L.NZ,
-                                                      (float)c->t_ref, tinit);
+    {
+        const float* th = c->d_ref + 3 * L.NZ;
+        const float* ts = c->d_ref + 4 * L.NZ;
+        const int g = grid_1d(cells);
+        if (op.storage == LBM_STORE_BF16)
+            lbm::init_kernel<1><<<g, 256, 0, stm>>>(c->d_f[0], c->d_tsnap, cells, L, c->d_ref, th, ts,
+                                                   (float)c->t_ref, tinit);
+        else if (op.storage == LBM_STORE_F16)
+            lbm::init_kernel<2><<<g, 256, 0, stm>>>(c->d_f[0], c->d_tsnap, cells, L, c->d_ref, th, ts,
+                                                   (float)c->t_ref, tinit);
+        else
+            lbm::init_kernel<0><<<g, 256, 0, stm>>>(c->d_f[0], c->d_tsnap, cells, L, c->d_ref, th, ts,
+                                                   (float)c->t_ref, tinit);
+    }
     CUDA_TRY(c, cudaGetLastError());
     Ctl h{};
     h.best_rt = INFINITY;
@@ -595,7 +631,9 @@ lbm_status lbm_advance(lbm_ctx* c, int64_t n_steps) {
     if (n_steps == 0) return LBM_OK;
     CUDA_TRY(c, cudaSetDevice(c->device));
     for (int64_t k = 0; k < n_steps; ++k) {
-        CUDA_TRY(c, launch_step(c, c->cur, false, kAA, c->stream));
+        Closing cl;
+        cl.rseed = 0x10000u + (unsigned)k;
+        CUDA_TRY(c, launch_step(c, c->cur, false, kAA, c->stream, cl));
         c->cur ^= 1;
     }
     lbm::add_iters_kernel<<<1, 1, 0, c->stream>>>(c->d_ctl, (long long)n_steps);
@@ -608,7 +646,9 @@ lbm_status lbm_check(lbm_ctx* c, lbm_solve_info* info) {
     if (!c->started) return fail(c, LBM_ERR_STATE, "call lbm_start first");
     CUDA_TRY(c, cudaSetDevice(c->device));
     CUDA_TRY(c, cudaEventRecord(c->ev0, c->stream));
-    CUDA_TRY(c, launch_step(c, c->cur, true, kAA, c->stream));
+    Closing cl;
+    cl.rseed = 0x5bd1e995u;
+    CUDA_TRY(c, launch_step(c, c->cur, true, kAA, c->stream, cl));
     c->cur ^= 1;
     CUDA_TRY(c, cudaEventRecord(c->ev1, c->stream));
     lbm_status st = read_ctl(c, c->stream);
@@ -638,8 +678,9 @@ lbm_status lbm_run(lbm_ctx* c, lbm_solve_info* info) {
         // back after every interval
         do {
             for (int k = 0; k < K; ++k) {
-                CUDA_TRY(c, launch_step(c, c->cur, k == K - 1, k == 0 ? kAB : kBB, c->stream,
-                                        interval_closing(c)));
+                Closing cl = interval_closing(c);
+                cl.rseed = (unsigned)k;
+                CUDA_TRY(c, launch_step(c, c->cur, k == K - 1, k == 0 ? kAB : kBB, c->stream, cl));
                 c->cur ^= 1;
             }
             CUDA_TRY(c, cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost,
@@ -689,8 +730,15 @@ lbm_status lbm_get_temperature(lbm_ctx* c, float* host_out) {
     if (!c->started) return fail(c, LBM_ERR_STATE, "no solve state");
     CUDA_TRY(c, cudaSetDevice(c->device));
     const long long N = (long long)c->n[0] * c->n[1] * c->n[2];
-    lbm::temperature_kernel<<<grid_1d(N), 256, 0, c->stream>>>(c->d_f[c->cur], c->pstride, c->L,
-                                                              c->d_ref, c->d_T);
+    if (c->fmt == LBM_STORE_BF16)
+        lbm::temperature_kernel<1><<<grid_1d(N), 256, 0, c->stream>>>(c->d_f[c->cur], c->pstride, c->L,
+                                                                     c->d_ref, c->d_T);
+    else if (c->fmt == LBM_STORE_F16)
+        lbm::temperature_kernel<2><<<grid_1d(N), 256, 0, c->stream>>>(c->d_f[c->cur], c->pstride, c->L,
+                                                                     c->d_ref, c->d_T);
+    else
+        lbm::temperature_kernel<0><<<grid_1d(N), 256, 0, c->stream>>>(c->d_f[c->cur], c->pstride, c->L,
+                                                                     c->d_ref, c->d_T);
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaMemcpyAsync(host_out, c->d_T, sizeof(float) * N, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));

@@ -1,10 +1,11 @@
 // Device kernels of the D3Q7 MRT lattice Boltzmann hot path for sm_103a.
 //
-// Storage: structure of arrays f[i][z][y][x] (population-major), FP32, two
-// buffers (pull scheme: read the previous post-collision state, write the
-// next one).  The Dirichlet axis is always the slowest index z; the host lays
-// the cell out that way.  Rows are padded to a multiple of 4 voxels (pitch)
-// so that every thread moves one aligned 16-byte float4 per population.
+// Storage: structure of arrays f[i][z][y][x] (population-major), FP32, BF16 or
+// FP16, two buffers (pull scheme: read the previous post-collision state,
+// write the next one).  The Dirichlet axis is always the slowest index z; the
+// host lays the cell out that way.  Rows are padded to a multiple of V voxels
+// (pitch) so that every thread moves one aligned 16-byte vector per
+// population (V = 4 FP32 or 8 16-bit values).
 // Values are stored as deviations g_i = f_i - w_i R(z), w_0 = 1/4,
 // w_1..6 = 1/8 (Eq. 6 with gamma = 1/8), from a per-plane reference
 // temperature R(z): the plane mean of T at the previous check, quantised to a
@@ -28,6 +29,8 @@
 // q = -D grad T = (I - S_b / 2) j = (j + jhat) / 2 at every node.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -72,18 +75,19 @@ struct CheckArgs {
 };
 
 struct StepArgs {
-    const float* __restrict__ src;   // 7 populations, post-collision state n-1
-    float* __restrict__ dst;         // 7 populations, post-collision state n
+    const void* __restrict__ src;    // 7 populations, post-collision state n-1
+    void* __restrict__ dst;          // 7 populations, post-collision state n
     const uint8_t* __restrict__ phase;  // [nz][ny][pitch], padded with 0
     const float4* __restrict__ sb;   // 2 float4 per phase: (xx, yy, zz, yz), (xz, xy, -, -)
     float* __restrict__ tsnap;       // T - T_ref at the previous check, [nz][ny][pitch]
     const float* __restrict__ rsrc;  // reference R(z) of the src state, [nz]
     const float* __restrict__ rdst;  // reference R(z) of the dst state, [nz]
-    long long pstride;               // floats per population = pitch * ny * nz
+    long long pstride;               // elements per population = pitch * ny * nz
     int nx, ny, nz, pitch, n_phases;
-    int quads_per_plane;             // (pitch / 4) * ny
+    int quads_per_plane;             // (pitch / V) * ny vectors per plane
     int blocks_per_plane;
     float eps_hot, eps_cold;         // eps * T_wall
+    unsigned rseed;                  // launch salt of the stochastic rounding
     double t_ref;                    // offset of the residual snapshot
     CheckArgs ck;
 };
@@ -221,26 +225,110 @@ __device__ void close_plane(const StepArgs& a, int z) {
     }
 }
 
-// One fused pull-stream + collide step over 4 consecutive voxels of a row per
-// thread.  Threads of a block cover consecutive quads of one z-plane, so the
-// x-neighbours of a quad sit in the adjacent lanes (warp shuffles) except at
-// warp and row boundaries, where a scalar load or a face rule supplies them.
-template <bool PERIODIC, bool CHECK>
-__global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
+// Storage policies.  FP32 moves 4 voxels per thread as one float4 per
+// population; BF16 and FP16 move 8 voxels per thread as one uint4 (eight
+// 16-bit values) per population, converted to FP32 for the collision and
+// rounded back stochastically (cvt.rs: the rounding direction is drawn with
+// probability proportional to the distance to each neighbour, so the stored
+// value is unbiased and updates below half an ulp are not lost on average).
+template <int FMT> struct Pol;
+
+template <> struct Pol<0> {
+    using T = float;
+    using Raw = float4;
+    static constexpr int V = 4;
+    __device__ static Raw zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ static Raw load(const T* p) { return ld4(p); }
+    __device__ static float get(const Raw& r, int k) { return comp(r, k); }
+    __device__ static float scalar(const T* p) { return __ldg(p); }
+    __device__ static Raw neg(Raw r) { return make_float4(-r.x, -r.y, -r.z, -r.w); }
+    __device__ static void store(T* p, const float (&o)[V], unsigned) {
+        st4(p, make_float4(o[0], o[1], o[2], o[3]));
+    }
+};
+
+__device__ __forceinline__ unsigned word(const uint4& r, int m) {
+    return m == 0 ? r.x : (m == 1 ? r.y : (m == 2 ? r.z : r.w));
+}
+
+__device__ __forceinline__ unsigned hash32(unsigned x) {   // lowbias32 (C. Wellons)
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+template <int FMT> struct Pol16 {
+    using T = uint16_t;
+    using Raw = uint4;
+    static constexpr int V = 8;
+    __device__ static Raw zero() { return make_uint4(0u, 0u, 0u, 0u); }
+    __device__ static Raw load(const T* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
+    __device__ static float from16(unsigned h) {
+        if (FMT == 1) return __uint_as_float(h << 16);                  // bf16
+        return __half2float(__ushort_as_half((unsigned short)h));       // fp16
+    }
+    __device__ static float get(const Raw& r, int k) {
+        const unsigned w = word(r, k >> 1);
+        return from16((k & 1) ? (w >> 16) : (w & 0xffffu));
+    }
+    __device__ static float scalar(const T* p) { return from16(__ldg(p)); }
+    __device__ static Raw neg(Raw r) {
+        return make_uint4(r.x ^ 0x80008000u, r.y ^ 0x80008000u, r.z ^ 0x80008000u, r.w ^ 0x80008000u);
+    }
+    // pairs (o[2m], o[2m+1]) -> low and high half of word m; rbits[31:16]
+    // round the high half, rbits[15:0] the low half
+    __device__ static unsigned pack(float lo, float hi, unsigned rbits) {
+        unsigned d;
+        if (FMT == 1)
+            asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+        else
+            asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+        return d;
+    }
+    // one hash per vector; the four words are distinct affine maps of it
+    // (each uniform on its own, which is all an unbiased rounding needs)
+    __device__ static void store(T* p, const float (&o)[V], unsigned key) {
+        const unsigned h = hash32(key);
+        uint4 r;
+        r.x = pack(o[0], o[1], h);
+        r.y = pack(o[2], o[3], h * 0x2C1B3C6Du + 0x297A2D39u);
+        r.z = pack(o[4], o[5], h * 0x85EBCA6Bu + 0x68E31DA4u);
+        r.w = pack(o[6], o[7], h * 0xCC9E2D51u + 0x1B873593u);
+        *reinterpret_cast<uint4*>(p) = r;
+    }
+};
+template <> struct Pol<1> : Pol16<1> {};
+template <> struct Pol<2> : Pol16<2> {};
+
+// One fused pull-stream + collide step over V consecutive voxels of a row per
+// thread (V = 4 in FP32, 8 in 16-bit storage).  Threads of a block cover
+// consecutive vectors of one z-plane, so the x-neighbours of a vector sit in
+// the adjacent lanes (warp shuffles) except at warp and row boundaries, where
+// a scalar load or a face rule supplies them.  RAGGED: nx is not a multiple
+// of V, so the last vector of a row holds padding.
+template <int FMT, bool PERIODIC, bool CHECK, bool RAGGED>
+__global__ void __launch_bounds__(kThreads, CHECK ? 1 : 4) step_kernel(const StepArgs a) {
+    using S = Pol<FMT>;
+    using T = typename S::T;
+    using Raw = typename S::Raw;
+    constexpr int V = S::V;
     extern __shared__ float4 s_sb[];
     for (int i = threadIdx.x; i < 2 * a.n_phases; i += kThreads) s_sb[i] = a.sb[i];
     __syncthreads();
 
-    const int nq = a.pitch >> 2;
-    const int t = blockIdx.x * kThreads + threadIdx.x;    // quad index within the plane
+    const int nq = a.pitch / V;
+    const int t = blockIdx.x * kThreads + threadIdx.x;    // vector index within the plane
     const int z = blockIdx.y;
     const bool active = t < a.quads_per_plane;
     const int y = active ? t / nq : 0;
     const int qx = active ? t - y * nq : 0;
-    const int x0 = qx << 2;
+    const int x0 = qx * V;
     const int lane = threadIdx.x & 31;
     const long long P = a.pstride;
-    const float* __restrict__ src = a.src;
+    const T* __restrict__ src = reinterpret_cast<const T*>(a.src);
 
     const long long row = ((long long)z * a.ny + y) * a.pitch;
     // y-neighbour rows: periodic wrap (Eq. 25) or bounce-back into the own node (Eq. 24)
@@ -256,17 +344,18 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
     const long long o5 = zlo ? row + 6 * P : row - (long long)a.ny * a.pitch + 5 * P;
     const long long o6 = zhi ? row + 5 * P : row + (long long)a.ny * a.pitch + 6 * P;
 
-    float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0, c2 = c0, c3 = c0, c4 = c0, c5 = c0, c6 = c0;
-    uchar4 ph = make_uchar4(0, 0, 0, 0);
+    Raw c0 = S::zero(), c1 = c0, c2 = c0, c3 = c0, c4 = c0, c5 = c0, c6 = c0;
+    uint2 ph = make_uint2(0u, 0u);
     if (active) {
-        c0 = ld4(src + row + x0);
-        c1 = ld4(src + P + row + x0);
-        c2 = ld4(src + 2 * P + row + x0);
-        c3 = ld4(src + o3 + x0);
-        c4 = ld4(src + o4 + x0);
-        c5 = ld4(src + o5 + x0);
-        c6 = ld4(src + o6 + x0);
-        ph = __ldg(reinterpret_cast<const uchar4*>(a.phase + row + x0));
+        c0 = S::load(src + row + x0);
+        c1 = S::load(src + P + row + x0);
+        c2 = S::load(src + 2 * P + row + x0);
+        c3 = S::load(src + o3 + x0);
+        c4 = S::load(src + o4 + x0);
+        c5 = S::load(src + o5 + x0);
+        c6 = S::load(src + o6 + x0);
+        if (V == 8) ph = __ldg(reinterpret_cast<const uint2*>(a.phase + row + x0));
+        else ph.x = __ldg(reinterpret_cast<const unsigned*>(a.phase + row + x0));
     }
     // Frame changes (all exact): a population pulled from plane z' carries
     // w_i R_src(z'); it is re-expressed relative to R_dst(z) of this node.
@@ -280,42 +369,52 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
     const float k6 = zhi ? (a.eps_cold - w * r0) - w * rd : w * (rp - rd);
     const float kT = (2.f * k_in + 4.f * k_in) + (k5 + k6);   // sum of w_i (...) with w_0 = 2w
     const float kJ = k5 - k6;
-    if (zlo) { c5.x = -c5.x; c5.y = -c5.y; c5.z = -c5.z; c5.w = -c5.w; }
-    if (zhi) { c6.x = -c6.x; c6.y = -c6.y; c6.z = -c6.z; c6.w = -c6.w; }
+    if (zlo) c5 = S::neg(c5);
+    if (zhi) c6 = S::neg(c6);
     // x-neighbours: f1 comes from x - 1, f2 from x + 1.
-    const float left1 = __shfl_up_sync(kFull, c1.w, 1);
-    const float right2 = __shfl_down_sync(kFull, c2.x, 1);
-    float4 f1, f2;
-    f1.y = c1.x; f1.z = c1.y; f1.w = c1.z;
-    f2.x = c2.y; f2.y = c2.z; f2.z = c2.w;
-    if (lane > 0 && qx > 0) f1.x = left1;
-    else if (qx > 0) f1.x = active ? __ldg(src + P + row + x0 - 1) : 0.f;
-    else f1.x = PERIODIC ? (active ? __ldg(src + P + row + a.nx - 1) : 0.f) : c2.x;
+    const float left1 = __shfl_up_sync(kFull, S::get(c1, V - 1), 1);
+    const float right2 = __shfl_down_sync(kFull, S::get(c2, 0), 1);
+    float f1_0, f2_last;
+    if (lane > 0 && qx > 0) f1_0 = left1;
+    else if (qx > 0) f1_0 = active ? S::scalar(src + P + row + x0 - 1) : 0.f;
+    else f1_0 = PERIODIC ? (active ? S::scalar(src + P + row + a.nx - 1) : 0.f) : S::get(c2, 0);
+    // the last real voxel of the row sits in the row's last vector, at e_last
+    const int e_last = (RAGGED && qx == nq - 1) ? a.nx - 1 - x0 : V;
+    float edge2 = 0.f;
     if (qx < nq - 1) {
-        f2.w = (lane < 31) ? right2 : (active ? __ldg(src + 2 * P + row + x0 + 4) : 0.f);
+        f2_last = (lane < 31) ? right2 : (active ? S::scalar(src + 2 * P + row + x0 + V) : 0.f);
     } else {
-        f2.w = 0.f;
-        // the last real voxel of the row sits in this quad
-        const int e = a.nx - 1 - x0;
-        const float edge = PERIODIC ? (active ? __ldg(src + 2 * P + row) : 0.f) : comp(c1, e);
-        set_comp(f2, e, edge);
+        edge2 = PERIODIC ? (active ? S::scalar(src + 2 * P + row) : 0.f) : S::get(c1, V - 1);
+        f2_last = RAGGED ? 0.f : edge2;
+        if (RAGGED && !PERIODIC) edge2 = 0.f;
     }
 
-    const int n_real = active ? min(4, a.nx - x0) : 0;
-    float4 o0v, o1v, o2v, o3v, o4v, o5v, o6v;
-    float4 thv, thp = make_float4(0.f, 0.f, 0.f, 0.f);
-    // per-thread (4 voxels) and per-warp sums of positive FP32 terms stay in
-    // FP32; the block tree, the plane sums and the residual sums are FP64
+    const int n_real = active ? min(V, a.nx - x0) : 0;
+    // per-thread and per-warp sums of positive FP32 terms stay in FP32; the
+    // block tree, the plane sums and the residual sums are FP64
     float q_sum = 0.f, dT_sum = 0.f, T_sum = 0.f, Tp_sum = 0.f;
+    float thp[V], thv[V];
     // T - T_ref at the previous check: the residual is the change since then
-    if (CHECK && active) thp = *reinterpret_cast<const float4*>(a.tsnap + row + x0);
+    if (CHECK) {
+#pragma unroll
+        for (int v4 = 0; v4 < V / 4; ++v4) {
+            const float4 q4 = active ? *reinterpret_cast<const float4*>(a.tsnap + row + x0 + 4 * v4)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+            thp[4 * v4] = q4.x; thp[4 * v4 + 1] = q4.y; thp[4 * v4 + 2] = q4.z; thp[4 * v4 + 3] = q4.w;
+        }
+    }
     const float dref = (float)((double)rd - a.t_ref);
     const float tref = (float)a.t_ref;
+    float o[7][V];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float g0 = comp(c0, k), g1 = comp(f1, k), g2 = comp(f2, k), g3 = comp(c3, k);
-        const float g4 = comp(c4, k), g5 = comp(c5, k), g6 = comp(c6, k);
-        const int p = (k == 0 ? ph.x : (k == 1 ? ph.y : (k == 2 ? ph.z : ph.w)));
+    for (int k = 0; k < V; ++k) {
+        const float g0 = S::get(c0, k);
+        const float g1 = k == 0 ? f1_0 : S::get(c1, k - 1);
+        float g2 = k == V - 1 ? f2_last : S::get(c2, k + 1);
+        if (RAGGED && k == e_last) g2 = PERIODIC ? edge2 : S::get(c1, k);
+        const float g3 = S::get(c3, k), g4 = S::get(c4, k);
+        const float g5 = S::get(c5, k), g6 = S::get(c6, k);
+        const int p = (k < 4 ? (ph.x >> (8 * k)) : (ph.y >> (8 * (k - 4)))) & 0xff;
         const float4 sa = s_sb[2 * p];
         const float4 sc = s_sb[2 * p + 1];
         // T - R_dst(z) (Eq. 14) and the flux moment j, with the frame constants
@@ -327,35 +426,52 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
         const float sz = fmaf(sc.x, jx, fmaf(sa.w, jy, sa.z * jz));
         const float hx = jx - sx, hy = jy - sy, hz = jz - sz;
         const float t8 = 0.125f * th;
-        const bool real = k < n_real;
-        set_comp(o0v, k, real ? 0.25f * th : 0.f);
-        set_comp(o1v, k, real ? fmaf(0.5f, hx, t8) : 0.f);
-        set_comp(o2v, k, real ? fmaf(-0.5f, hx, t8) : 0.f);
-        set_comp(o3v, k, real ? fmaf(0.5f, hy, t8) : 0.f);
-        set_comp(o4v, k, real ? fmaf(-0.5f, hy, t8) : 0.f);
-        set_comp(o5v, k, real ? fmaf(0.5f, hz, t8) : 0.f);
-        set_comp(o6v, k, real ? fmaf(-0.5f, hz, t8) : 0.f);
+        const bool real = RAGGED ? k < n_real : active;   // n_real is 0 for inactive threads
+        o[0][k] = 0.25f * th;
+        o[1][k] = fmaf(0.5f, hx, t8);
+        o[2][k] = fmaf(-0.5f, hx, t8);
+        o[3][k] = fmaf(0.5f, hy, t8);
+        o[4][k] = fmaf(-0.5f, hy, t8);
+        o[5][k] = fmaf(0.5f, hz, t8);
+        o[6][k] = fmaf(-0.5f, hz, t8);
         if (CHECK) {
             const float tdev = th + dref;                    // T - T_ref
-            set_comp(thv, k, real ? tdev : 0.f);
+            thv[k] = tdev;
             if (real) {
                 q_sum += fmaf(-0.5f, sz, jz);                // (j_z + jhat_z) / 2
-                dT_sum += fabsf(tdev - comp(thp, k));
+                dT_sum += fabsf(tdev - thp[k]);
                 T_sum += fabsf(tdev + tref);
                 Tp_sum += tdev + tref;
             }
         }
     }
+    if (RAGGED && n_real < V) {
+        // padding voxels of the row's last vector stay zero
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+            if (k >= n_real) {
+#pragma unroll
+                for (int i = 0; i < 7; ++i) o[i][k] = 0.f;
+                if (CHECK) thv[k] = 0.f;
+            }
+    }
     if (active) {
-        float* __restrict__ dst = a.dst + row + x0;
-        st4(dst, o0v);
-        st4(dst + P, o1v);
-        st4(dst + 2 * P, o2v);
-        st4(dst + 3 * P, o3v);
-        st4(dst + 4 * P, o4v);
-        st4(dst + 5 * P, o5v);
-        st4(dst + 6 * P, o6v);
-        if (CHECK) st4(a.tsnap + row + x0, thv);
+        T* __restrict__ dst = reinterpret_cast<T*>(a.dst) + row + x0;
+        // random bits for stochastic rounding: a hash of the element's
+        // position and population, salted by the iteration and the launch
+        unsigned key = 0u;
+        if (FMT != 0) {
+            const unsigned seed = hash32((unsigned)__ldcg(&a.ck.ctl->iter) * 0x9E3779B9u + a.rseed);
+            key = seed ^ (unsigned)((row + x0) >> 1) * 0x85ebca6bu;
+        }
+#pragma unroll
+        for (int i = 0; i < 7; ++i) S::store(dst + i * P, o[i], key + 0x9E3779B9u * (unsigned)i);
+        if (CHECK) {
+#pragma unroll
+            for (int v4 = 0; v4 < V / 4; ++v4)
+                st4(a.tsnap + row + x0 + 4 * v4,
+                    make_float4(thv[4 * v4], thv[4 * v4 + 1], thv[4 * v4 + 2], thv[4 * v4 + 3]));
+        }
     }
 
     if (CHECK) {
@@ -430,12 +546,25 @@ __global__ void permute_phase_kernel(const uint8_t* __restrict__ in, uint8_t* __
 
 // Initial state fhat^0 = f^eq(T0) (Eq. 6) as deviations from w_i T_ref.
 // T0 is the linear profile between the walls, or a given field (original order).
+// Value -> storage element (round to nearest; used only for the initial state).
+template <int FMT> __device__ __forceinline__ typename Pol<FMT>::T to_store(float v);
+template <> __device__ __forceinline__ float to_store<0>(float v) { return v; }
+template <> __device__ __forceinline__ uint16_t to_store<1>(float v) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+template <> __device__ __forceinline__ uint16_t to_store<2>(float v) {
+    return __half_as_ushort(__float2half_rn(v));
+}
+
 // plane_th[z] = T0(z) - R(z) and plane_ts[z] = T0(z) - T_ref for the linear
 // start (host FP64, rounded once); a caller field t_init replaces T0.
-__global__ void init_kernel(float* __restrict__ f, float* __restrict__ tsnap, long long P, Layout L,
+template <int FMT>
+__global__ void init_kernel(void* __restrict__ fv, float* __restrict__ tsnap, long long P, Layout L,
                             const float* __restrict__ ref, const float* __restrict__ plane_th,
                             const float* __restrict__ plane_ts, float t_ref,
                             const float* __restrict__ t_init) {
+    using T = typename Pol<FMT>::T;
+    T* f = reinterpret_cast<T*>(fv);
     const long long total = (long long)L.pitch * L.NY * L.NZ;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -446,24 +575,27 @@ __global__ void init_kernel(float* __restrict__ f, float* __restrict__ tsnap, lo
         float th = 0.f, ts = 0.f;
         if (xc < L.NX) {
             if (t_init) {
-                const float T = t_init[orig_index(L, xc, yc, zc)];
-                th = T - ref[zc];
-                ts = T - t_ref;
+                const float T0 = t_init[orig_index(L, xc, yc, zc)];
+                th = T0 - ref[zc];
+                ts = T0 - t_ref;
             } else {
                 th = plane_th[zc];
                 ts = plane_ts[zc];
             }
         }
         tsnap[i] = ts;
-        f[i] = 0.25f * th;
-        const float e = 0.125f * th;
+        f[i] = to_store<FMT>(0.25f * th);
+        const T e = to_store<FMT>(0.125f * th);
         for (int q = 1; q < 7; ++q) f[q * P + i] = e;
     }
 }
 
 // T = sum_i f_i (Eq. 14) of the current state, written in the original order.
-__global__ void temperature_kernel(const float* __restrict__ f, long long P, Layout L,
+template <int FMT>
+__global__ void temperature_kernel(const void* __restrict__ fv, long long P, Layout L,
                                    const float* __restrict__ ref, float* __restrict__ T) {
+    using S = Pol<FMT>;
+    const typename S::T* f = reinterpret_cast<const typename S::T*>(fv);
     const long long total = (long long)L.n[0] * L.n[1] * L.n[2];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -474,8 +606,10 @@ __global__ void temperature_kernel(const float* __restrict__ f, long long P, Lay
         c[2] = (int)(r / L.n[1]);
         const int zc = c[L.perm[2]];
         const long long k = ((long long)zc * L.NY + c[L.perm[1]]) * L.pitch + c[L.perm[0]];
-        const float th = ((f[k] + f[P + k]) + (f[2 * P + k] + f[3 * P + k])) +
-                         ((f[4 * P + k] + f[5 * P + k]) + f[6 * P + k]);
+        const float th = ((S::scalar(f + k) + S::scalar(f + P + k)) +
+                          (S::scalar(f + 2 * P + k) + S::scalar(f + 3 * P + k))) +
+                         ((S::scalar(f + 4 * P + k) + S::scalar(f + 5 * P + k)) +
+                          S::scalar(f + 6 * P + k));
         T[i] = th + ref[zc];
     }
 }

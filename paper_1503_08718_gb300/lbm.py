@@ -33,7 +33,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "STATE", 3: "CUDA", 4: "OUT_OF_MEM
 
 LBM_AXIS_X, LBM_AXIS_Y, LBM_AXIS_Z = 0, 1, 2
 LBM_LATERAL_PERIODIC, LBM_LATERAL_ADIABATIC = 0, 1
-LBM_STORE_F32 = 0
+LBM_STORE_F32, LBM_STORE_BF16, LBM_STORE_F16 = 0, 1, 2
 
 
 class lbm_solve_opts(ctypes.Structure):
