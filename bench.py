@@ -237,6 +237,36 @@ def run_ours(args):
     achieved = BYTES_PER_LUP[args.storage] * n_vox / per_launch_s / 1e9
     peak, peak_kind = peaks()
 
+    # the same step with 16-bit distribution storage (FP32 collision,
+    # stochastic rounding): GLUPS and the roofline at 29 B/LUP
+    variants = {}
+    if args.storage == "f32" and not args.no_variants:
+        for name in ("bf16", "f16"):
+            o16 = S.opts(tol=0.0, max_iters=iters, check_every=K, storage=STORAGE[name],
+                         host_loop=int(args.launch == "host"))
+            o16.stream = int(stream.cuda_stream)
+            for _ in range(args.warmup):
+                S.start(2, 0, o16)
+                S.run()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            n16 = max(3, args.steps // 2)
+            e0.record(stream)
+            for _ in range(n16):
+                S.start(2, 0, o16)
+                i16 = S.run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms16 = e0.elapsed_time(e1)
+            g16 = n_vox * iters * n16 / (ms16 / 1000.0) / 1e9
+            a16 = BYTES_PER_LUP[name] * n_vox / ((ms16 / 1000.0) / (n16 * iters)) / 1e9
+            variants[name] = {"value": g16, "unit": "GLUPS", "steps": n16,
+                              "ms_per_step": ms16 / n16, "bytes_per_lup": BYTES_PER_LUP[name],
+                              "roofline_frac": a16 / peak,
+                              "k_eff_after_step": i16.k_eff,
+                              "k_eff_rel_vs_f32": (i16.k_eff - info.k_eff) / info.k_eff}
+
     # end to end through the public API with host buffers
     anchors = I.braid_anchors(NX, NY, SEED, n_max=NMAX)
     phase_h = S.geometry()
@@ -286,6 +316,7 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(),
             "k_eff_after_step": info.k_eff,
+            "storage_variants": variants or None,
             "wall_s_timed": wall,
         }
         print(json.dumps(line), flush=True)
@@ -306,6 +337,8 @@ def main():
                          "host: the same kernels launched from the host (for profilers)")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
                     help="distribution storage (collision is FP32 in every mode)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="omit the BF16/FP16 storage variants of the step")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline leg")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--traffic", type=float, default=None,

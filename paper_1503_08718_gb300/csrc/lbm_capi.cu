@@ -303,12 +303,12 @@ lbm_status read_ctl(lbm_ctx* c, cudaStream_t st) {
 }
 
 // Everything a check-interval graph bakes in: the kernel arguments of both
-// buffer parities, the closing arguments and the lateral type.
+// buffer parities, the closing arguments, the lateral type and the storage.
 std::vector<char> graph_signature(const lbm_ctx* c, int parity) {
     const lbm::StepArgs a = step_args(c, parity, kAB, interval_closing(c));
-    std::vector<char> sig(sizeof a + 2 * sizeof(int));
+    std::vector<char> sig(sizeof a + 3 * sizeof(int));
     std::memcpy(sig.data(), &a, sizeof a);
-    const int extra[2] = {c->lateral, c->opts.check_every};
+    const int extra[3] = {c->lateral, c->opts.check_every, c->fmt};
     std::memcpy(sig.data() + sizeof a, extra, sizeof extra);
     return sig;
 }
