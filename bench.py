@@ -179,7 +179,7 @@ def run_ours(args):
 
     from paper_1503_08718_gb300 import build as B
     from paper_1503_08718_gb300 import inputs as I
-    from paper_1503_08718_gb300 import lbm
+    from paper_1503_08718_gb300 import lbm, replicas
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -224,9 +224,7 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     if ws > 1:
         torch.distributed.barrier()
-        t = torch.tensor([ms], device=f"cuda:{dev}", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(ms, device=f"cuda:{dev}")
     n_vox = NX * NY * NZ
     lups = n_vox * iters * args.steps * ws
     glups = lups / (ms / 1000.0) / 1e9
@@ -284,7 +282,8 @@ def run_ours(args):
         t1 = time.perf_counter()
         if i >= args.warmup:
             e2e_ms.append((t1 - t0) * 1000)
-    e2e_glups = n_vox * iters * len(e2e_ms) * ws / (sum(e2e_ms) / 1000.0) / 1e9
+    e2e_total_ms = replicas.max_over_ranks(sum(e2e_ms), device=f"cuda:{dev}")
+    e2e_glups = n_vox * iters * len(e2e_ms) * ws / (e2e_total_ms / 1000.0) / 1e9
     del anchors
 
     if rank == 0:

@@ -202,6 +202,28 @@ lbm_status lbm_braid_voxelize_noalloc(int nx, int ny, int nz, double g_rad, doub
                                       uint8_t* d_phase, int* n_used, double* fraction,
                                       void* stream, char* err, int err_len);
 
+/* Yarn conductivities from the fibre and matrix conductivities (Section 4.2):
+ * longitudinal lam_L = lam_fL phi_fy + lam_m (1 - phi_fy) (Eq. 36) and
+ * transverse lam_T = lam_m + phi_fy / (1/(lam_fT - lam_m) + (1 - phi_fy)/(2 lam_m))
+ * (Eq. 37, whose printed numerator 1 - phi_fy contradicts Table II; phi_fy
+ * reproduces it).  phi_fy: fibre fraction inside the yarn, in (0, 1).
+ * Host-only, no device work.  Returns LBM_ERR_INVALID_ARG on non-positive
+ * conductivities, lam_fT == lam_m or phi_fy outside (0, 1). */
+lbm_status lbm_yarn_conductivity(double lam_fL, double lam_fT, double lam_m, double phi_fy,
+                                 double* lam_L, double* lam_T);
+
+/* Unit cell of the four-directional braid (Section 4.1, Eq. 32-35): yarn
+ * volume fraction phi_y = pi sqrt(3) / 8 (Eq. 35), phi_fy = phi_f / phi_y, yarn
+ * section area A = n_f pi d_f^2 / 4 / phi_fy = pi d c (Eq. 34) with
+ * c = d sqrt(3) cos(gamma) (Eq. 33), cell side a = 8 d (Eq. 32) and braiding
+ * pitch h = a / tan(gamma) (the paper takes h from its reference [17]; this
+ * relation reproduces its worked example).  Lengths in the unit of d_f.
+ * Host-only.  Outputs (host, nullable): a, h, c (semi-major), d (semi-minor),
+ * phi_fy.  Returns LBM_ERR_INVALID_ARG unless 0 < phi_f < phi_y, n_f >= 1,
+ * d_f > 0 and 0 < gamma < pi/2. */
+lbm_status lbm_braid_unit_cell(double phi_f, int n_f, double d_f, double gamma_rad, double* a,
+                               double* h, double* c, double* d, double* phi_fy);
+
 /* Copies the phase map (nx*ny*nz uint8, original order) to host_out. */
 lbm_status lbm_get_geometry(lbm_ctx* c, uint8_t* host_out);
 

@@ -764,6 +764,37 @@ lbm_status lbm_get_geometry(lbm_ctx* c, uint8_t* host_out) {
     return LBM_OK;
 }
 
+lbm_status lbm_yarn_conductivity(double lam_fL, double lam_fT, double lam_m, double phi_fy,
+                                 double* lam_L, double* lam_T) {
+    if (!(lam_fL > 0.0) || !(lam_fT > 0.0) || !(lam_m > 0.0) || !(phi_fy > 0.0) ||
+        !(phi_fy < 1.0) || lam_fT == lam_m)
+        return LBM_ERR_INVALID_ARG;
+    if (lam_L) *lam_L = lam_fL * phi_fy + lam_m * (1.0 - phi_fy);
+    if (lam_T) *lam_T = lam_m + phi_fy / (1.0 / (lam_fT - lam_m) + (1.0 - phi_fy) / (2.0 * lam_m));
+    return LBM_OK;
+}
+
+lbm_status lbm_braid_unit_cell(double phi_f, int n_f, double d_f, double gamma_rad, double* a,
+                               double* h, double* c, double* d, double* phi_fy) {
+    const double pi = 3.14159265358979323846;
+    const double phi_y = pi * std::sqrt(3.0) / 8.0;
+    if (!(phi_f > 0.0) || !(phi_f < phi_y) || n_f < 1 || !(d_f > 0.0) || !(gamma_rad > 0.0) ||
+        !(gamma_rad < pi / 2))
+        return LBM_ERR_INVALID_ARG;
+    const double pfy = phi_f / phi_y;
+    const double area = (double)n_f * pi * d_f * d_f / 4.0 / pfy;
+    const double cg = std::cos(gamma_rad);
+    const double dd = std::sqrt(area / (pi * std::sqrt(3.0) * cg));
+    const double cc = dd * std::sqrt(3.0) * cg;
+    const double aa = 8.0 * dd;
+    if (a) *a = aa;
+    if (h) *h = aa / std::tan(gamma_rad);
+    if (c) *c = cc;
+    if (d) *d = dd;
+    if (phi_fy) *phi_fy = pfy;
+    return LBM_OK;
+}
+
 const char* lbm_last_error(const lbm_ctx* c) {
     if (!c) return "null context";
     return c->err.c_str();

@@ -86,6 +86,10 @@ _PROTOS = {
                                                   ctypes.POINTER(ctypes.c_int),
                                                   ctypes.POINTER(ctypes.c_double),
                                                   ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int]),
+    "lbm_yarn_conductivity": (ctypes.c_int, [ctypes.c_double] * 4 +
+                              [ctypes.POINTER(ctypes.c_double)] * 2),
+    "lbm_braid_unit_cell": (ctypes.c_int, [ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_double] + [ctypes.POINTER(ctypes.c_double)] * 5),
     "lbm_last_error": (ctypes.c_char_p, [_ctx_p]),
     "lbm_destroy": (None, [_ctx_p]),
 }
@@ -189,6 +193,20 @@ def lbm_set_geometry_braid(ctx, g_rad: float, A: float, B: float, anchors: np.nd
 def lbm_get_geometry(ctx, out: np.ndarray) -> int:
     assert out.dtype == np.uint8 and out.flags.c_contiguous
     return load().lbm_get_geometry(ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+
+
+def lbm_yarn_conductivity(lam_fL: float, lam_fT: float, lam_m: float, phi_fy: float):
+    """Returns (status, lam_L, lam_T) of Eq. 36-37."""
+    L, T = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = load().lbm_yarn_conductivity(lam_fL, lam_fT, lam_m, phi_fy, ctypes.byref(L), ctypes.byref(T))
+    return st, L.value, T.value
+
+
+def lbm_braid_unit_cell(phi_f: float, n_f: int, d_f: float, gamma_rad: float):
+    """Returns (status, a, h, c, d, phi_fy) of Eq. 32-35."""
+    out = [ctypes.c_double(0.0) for _ in range(5)]
+    st = load().lbm_braid_unit_cell(phi_f, n_f, d_f, gamma_rad, *[ctypes.byref(o) for o in out])
+    return (st,) + tuple(o.value for o in out)
 
 
 LBM_NOALLOC_MAX_YARNS = 1024
