@@ -165,6 +165,53 @@ lbm_status lbm_set_geometry_braid(lbm_ctx* c, double g_rad, double A, double B,
                                   const double* anchors, int n_max, double phi,
                                   int* n_used, double* fraction);
 
+/* ---- Batched solves (the paper's sweeps over fibre fraction, braiding
+ * angle and direction, Section 5 and Fig. 9) ------------------------------ */
+
+typedef struct lbm_batch lbm_batch; /* opaque, owned by the library */
+
+typedef struct {
+    int32_t n_solves;       /* solves in the batch */
+    int32_t n_converged;    /* solves that met R_T <= tol */
+    int64_t total_updates;  /* lattice updates performed (voxels x iterations, summed) */
+    double elapsed_ms;      /* device time of the graph launch (CUDA events) */
+    int32_t block_threads;  /* block size the autotuner picked (128, 256 or 512) */
+    int32_t status;         /* LBM_OK if every solve converged, else LBM_ERR_NOT_CONVERGED */
+} lbm_batch_info;
+
+/* Creates an empty batch on CUDA device cuda_device. */
+lbm_status lbm_batch_create(int cuda_device, lbm_batch** out);
+
+/* Adds one steady solve: an nx*ny*nz cell (phase map and n_phases tensors,
+ * host, copied; same layout and checks as lbm_set_geometry / lbm_set_tensors)
+ * with the temperature difference along `axis`.  *id (nullable) receives the
+ * solve's index. */
+lbm_status lbm_batch_add(lbm_batch* b, int nx, int ny, int nz, const uint8_t* phase, int n_phases,
+                         const double* lambda, lbm_axis axis, int* id);
+
+/* Solves every added problem with one lateral type and one set of options
+ * (each solve takes its own lattice scale from its tensors unless
+ * opts.lattice_scale is set; t_init must be NULL).  All solves stay resident
+ * in device memory; one CUDA graph launch advances every unconverged solve by
+ * whole check intervals until each has met tol or max_iters.  Before the
+ * launch the block size is picked among 128, 256 and 512 threads by timing
+ * steps of the batch.  Synchronous. */
+lbm_status lbm_batch_solve(lbm_batch* b, lbm_lateral lateral, const lbm_solve_opts* o,
+                           lbm_batch_info* info);
+
+/* Result of solve `id` after lbm_batch_solve (iterations, k_eff, residuals,
+ * lattice scale, status). */
+lbm_status lbm_batch_result(const lbm_batch* b, int id, lbm_solve_info* info);
+
+/* Final temperature of solve `id` (nx*ny*nz floats, original axis order). */
+lbm_status lbm_batch_get_temperature(lbm_batch* b, int id, float* host_out);
+
+/* Message of the last failed batch call (batch-owned string). NULL-safe. */
+const char* lbm_batch_last_error(const lbm_batch* b);
+
+/* Frees the batch and its device memory. NULL-safe. */
+void lbm_batch_destroy(lbm_batch* b);
+
 /* Largest n_max accepted by lbm_braid_voxelize_noalloc. */
 #define LBM_NOALLOC_MAX_YARNS 1024
 

@@ -119,10 +119,11 @@ __device__ __forceinline__ void set_comp(float4& v, int k, float s) {
 // the work falls to whichever block finishes last, and the result is
 // deterministic.
 
+template <int THREADS>
 __device__ void close_check(const StepArgs& a) {
     const CheckArgs& ck = a.ck;
     double qsum = 0.0, qmax = -INFINITY, qmin = INFINITY, dsum = 0.0, tsum = 0.0;
-    for (int z = threadIdx.x; z < a.nz; z += kThreads) {
+    for (int z = threadIdx.x; z < a.nz; z += THREADS) {
         const double q = __ldcg(ck.Q + z);
         qsum += q;
         qmax = fmax(qmax, q);
@@ -130,7 +131,7 @@ __device__ void close_check(const StepArgs& a) {
         dsum += __ldcg(ck.plane + z);
         tsum += __ldcg(ck.plane + a.nz + z);
     }
-    __shared__ double s[5][kThreads / 32];
+    __shared__ double s[5][THREADS / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -146,13 +147,13 @@ __device__ void close_check(const StepArgs& a) {
     __syncthreads();
     // rotate the reference frames: every block of this kernel has finished
     // reading them (their tickets were all taken)
-    for (int z = threadIdx.x; z < a.nz; z += kThreads) {
+    for (int z = threadIdx.x; z < a.nz; z += THREADS) {
         if (ck.rebase) ck.ra[z] = ck.rb[z];
         ck.rb[z] = __ldcg(ck.rc + z);
     }
     if (threadIdx.x == 0) {
         qsum = 0.0; qmax = -INFINITY; qmin = INFINITY; dsum = 0.0; tsum = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) {
+        for (int w = 0; w < THREADS / 32; ++w) {
             qsum += s[0][w];
             qmax = fmax(qmax, s[1][w]);
             qmin = fmin(qmin, s[2][w]);
@@ -191,6 +192,7 @@ __device__ void close_check(const StepArgs& a) {
     }
 }
 
+template <int THREADS>
 __device__ void close_plane(const StepArgs& a, int z) {
     const CheckArgs& ck = a.ck;
     __shared__ int s_last_plane;
@@ -221,7 +223,7 @@ __device__ void close_plane(const StepArgs& a, int z) {
     __syncthreads();
     if (s_last_plane) {
         __threadfence();
-        close_check(a);
+        close_check<THREADS>(a);
     }
 }
 
@@ -309,19 +311,19 @@ template <> struct Pol<2> : Pol16<2> {};
 // the adjacent lanes (warp shuffles) except at warp and row boundaries, where
 // a scalar load or a face rule supplies them.  RAGGED: nx is not a multiple
 // of V, so the last vector of a row holds padding.
-template <int FMT, bool PERIODIC, bool CHECK, bool RAGGED>
-__global__ void __launch_bounds__(kThreads, CHECK ? 1 : 4) step_kernel(const StepArgs a) {
+template <int FMT, bool PERIODIC, bool CHECK, bool RAGGED, int THREADS>
+__device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const int z,
+                                          const unsigned rseed) {
     using S = Pol<FMT>;
     using T = typename S::T;
     using Raw = typename S::Raw;
     constexpr int V = S::V;
     extern __shared__ float4 s_sb[];
-    for (int i = threadIdx.x; i < 2 * a.n_phases; i += kThreads) s_sb[i] = a.sb[i];
+    for (int i = threadIdx.x; i < 2 * a.n_phases; i += THREADS) s_sb[i] = a.sb[i];
     __syncthreads();
 
     const int nq = a.pitch / V;
-    const int t = blockIdx.x * kThreads + threadIdx.x;    // vector index within the plane
-    const int z = blockIdx.y;
+    const int t = bx * THREADS + threadIdx.x;             // vector index within the plane
     const bool active = t < a.quads_per_plane;
     const int y = active ? t / nq : 0;
     const int qx = active ? t - y * nq : 0;
@@ -461,7 +463,7 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 1 : 4) step_kernel(const Ste
         // position and population, salted by the iteration and the launch
         unsigned key = 0u;
         if (FMT != 0) {
-            const unsigned seed = hash32((unsigned)__ldcg(&a.ck.ctl->iter) * 0x9E3779B9u + a.rseed);
+            const unsigned seed = hash32((unsigned)__ldcg(&a.ck.ctl->iter) * 0x9E3779B9u + rseed);
             key = seed ^ (unsigned)((row + x0) >> 1) * 0x85ebca6bu;
         }
 #pragma unroll
@@ -483,7 +485,7 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 1 : 4) step_kernel(const Ste
 #pragma unroll
             for (int m = 0; m < 4; ++m) vf[m] += __shfl_down_sync(kFull, vf[m], off);
         double v[4];
-        __shared__ double s_red[4][kThreads / 32];
+        __shared__ double s_red[4][THREADS / 32];
         __shared__ int s_last;
         const int warp = threadIdx.x >> 5;
         if (lane == 0)
@@ -492,14 +494,14 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 1 : 4) step_kernel(const Ste
         __syncthreads();
         if (threadIdx.x < 32) {
 #pragma unroll
-            for (int m = 0; m < 4; ++m) v[m] = lane < kThreads / 32 ? s_red[m][lane] : 0.0;
+            for (int m = 0; m < 4; ++m) v[m] = lane < THREADS / 32 ? s_red[m][lane] : 0.0;
 #pragma unroll
-            for (int off = 4; off > 0; off >>= 1)
+            for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
                 for (int m = 0; m < 4; ++m) v[m] += __shfl_down_sync(kFull, v[m], off);
             if (lane == 0) {
                 const CheckArgs& ck = a.ck;
-                const long long base = (long long)z * a.blocks_per_plane + blockIdx.x;
+                const long long base = (long long)z * a.blocks_per_plane + bx;
                 const long long plane_all = (long long)a.nz * a.blocks_per_plane;
 #pragma unroll
                 for (int m = 0; m < 4; ++m) ck.part[m * plane_all + base] = v[m];
@@ -510,11 +512,18 @@ __global__ void __launch_bounds__(kThreads, CHECK ? 1 : 4) step_kernel(const Ste
             }
         }
         __syncthreads();
-        if (s_last) close_plane(a, z);
+        if (s_last) close_plane<THREADS>(a, z);
     }
 }
 
-__global__ void add_iters_kernel(Ctl* c, long long n) { c->iter += n; }
+// The single-solve step: blockIdx.x is the block within the plane,
+// blockIdx.y the plane.
+template <int FMT, bool PERIODIC, bool CHECK, bool RAGGED>
+__global__ void __launch_bounds__(kThreads, CHECK ? 1 : 4) step_kernel(const StepArgs a) {
+    step_body<FMT, PERIODIC, CHECK, RAGGED, kThreads>(a, blockIdx.x, blockIdx.y, a.rseed);
+}
+
+static __global__ void add_iters_kernel(Ctl* c, long long n) { c->iter += n; }
 
 // Canonical layout: new axis i is old axis perm[i]; rows padded to pitch.
 struct Layout {
@@ -532,7 +541,7 @@ __device__ __forceinline__ long long orig_index(const Layout& L, int xc, int yc,
 }
 
 // Gathers the phase map into the canonical padded layout.
-__global__ void permute_phase_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, Layout L) {
+static __global__ void permute_phase_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, Layout L) {
     const long long total = (long long)L.pitch * L.NY * L.NZ;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {

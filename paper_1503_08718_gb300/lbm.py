@@ -45,6 +45,15 @@ class lbm_solve_opts(ctypes.Structure):
                 ("t_init", ctypes.POINTER(ctypes.c_float)), ("stream", ctypes.c_void_p)]
 
 
+class lbm_batch_info(ctypes.Structure):
+    _fields_ = [("n_solves", ctypes.c_int32), ("n_converged", ctypes.c_int32),
+                ("total_updates", ctypes.c_int64), ("elapsed_ms", ctypes.c_double),
+                ("block_threads", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class lbm_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("k_eff", ctypes.c_double),
                 ("residual_T", ctypes.c_double), ("residual_Q", ctypes.c_double),
@@ -90,6 +99,18 @@ _PROTOS = {
                               [ctypes.POINTER(ctypes.c_double)] * 2),
     "lbm_braid_unit_cell": (ctypes.c_int, [ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_double] + [ctypes.POINTER(ctypes.c_double)] * 5),
+    "lbm_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_ctx_p)]),
+    "lbm_batch_add": (ctypes.c_int, [_ctx_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_uint8), ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_int)]),
+    "lbm_batch_solve": (ctypes.c_int, [_ctx_p, ctypes.c_int, ctypes.POINTER(lbm_solve_opts),
+                                       ctypes.POINTER(lbm_batch_info)]),
+    "lbm_batch_result": (ctypes.c_int, [_ctx_p, ctypes.c_int, ctypes.POINTER(lbm_solve_info)]),
+    "lbm_batch_get_temperature": (ctypes.c_int, [_ctx_p, ctypes.c_int,
+                                                 ctypes.POINTER(ctypes.c_float)]),
+    "lbm_batch_last_error": (ctypes.c_char_p, [_ctx_p]),
+    "lbm_batch_destroy": (None, [_ctx_p]),
     "lbm_last_error": (ctypes.c_char_p, [_ctx_p]),
     "lbm_destroy": (None, [_ctx_p]),
 }
@@ -235,6 +256,46 @@ def lbm_destroy(ctx) -> None:
     load().lbm_destroy(ctx)
 
 
+def lbm_batch_create(cuda_device: int = 0):
+    h = _ctx_p()
+    st = load().lbm_batch_create(cuda_device, ctypes.byref(h))
+    return st, h
+
+
+def lbm_batch_add(b, phase: np.ndarray, n_phases: int, lam: np.ndarray, axis: int):
+    phase = np.ascontiguousarray(phase, dtype=np.uint8)
+    lam = np.ascontiguousarray(lam, dtype=np.float64).reshape(-1)
+    nz, ny, nx = phase.shape
+    i = ctypes.c_int(-1)
+    st = load().lbm_batch_add(b, nx, ny, nz, phase.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                              int(n_phases), _f64(lam), int(axis), ctypes.byref(i))
+    return st, i.value
+
+
+def lbm_batch_solve(b, lateral: int, opts: lbm_solve_opts | None = None,
+                    info: lbm_batch_info | None = None) -> int:
+    return load().lbm_batch_solve(b, lateral, ctypes.byref(opts) if opts is not None else None,
+                                  ctypes.byref(info) if info is not None else None)
+
+
+def lbm_batch_result(b, i: int, info: lbm_solve_info) -> int:
+    return load().lbm_batch_result(b, i, ctypes.byref(info))
+
+
+def lbm_batch_get_temperature(b, i: int, out: np.ndarray) -> int:
+    assert out.dtype == np.float32 and out.flags.c_contiguous
+    return load().lbm_batch_get_temperature(b, i, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+
+
+def lbm_batch_last_error(b) -> str:
+    s = load().lbm_batch_last_error(b)
+    return s.decode() if s else ""
+
+
+def lbm_batch_destroy(b) -> None:
+    load().lbm_batch_destroy(b)
+
+
 # ---- convenience object ---------------------------------------------------
 
 class LBMError(RuntimeError):
@@ -332,3 +393,49 @@ class Solver:
         out = np.empty(n_axis, np.float64)
         self._ok(lbm_get_plane_flux(self.h, out))
         return out
+
+
+class Batch:
+    """Many independent solves advanced together by one graph launch."""
+
+    def __init__(self, device: int = 0):
+        st, h = lbm_batch_create(device)
+        if st != LBM_OK:
+            raise LBMError(st, "lbm_batch_create failed")
+        self.h = h
+        self.shapes = []
+
+    def _ok(self, st, allow=()):
+        if st != LBM_OK and st not in allow:
+            raise LBMError(st, lbm_batch_last_error(self.h))
+        return st
+
+    def add(self, phase, lam, axis) -> int:
+        lam = np.asarray(lam, dtype=np.float64).reshape(-1, 6)
+        st, i = lbm_batch_add(self.h, phase, lam.shape[0], lam, axis)
+        self._ok(st)
+        self.shapes.append(np.asarray(phase).shape)
+        return i
+
+    def solve(self, lateral=0, opts=None) -> lbm_batch_info:
+        info = lbm_batch_info()
+        self._ok(lbm_batch_solve(self.h, lateral, opts, info))
+        return info
+
+    def result(self, i) -> lbm_solve_info:
+        info = lbm_solve_info()
+        self._ok(lbm_batch_result(self.h, i, info))
+        return info
+
+    def temperature(self, i) -> np.ndarray:
+        out = np.empty(self.shapes[i], np.float32)
+        self._ok(lbm_batch_get_temperature(self.h, i, out))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()

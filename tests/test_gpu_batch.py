@@ -1,0 +1,121 @@
+"""The batched solver (many uneven cells in one graph launch) against the
+single-solve path and the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1503_08718_gb300 import inputs as I
+from paper_1503_08718_gb300 import lbm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1503_08718_gb300 import build
+    build.build()
+    lbm.load()
+
+
+def _cells(seed=0):
+    """Uneven cells: ragged rows, odd sizes, every axis, 2 to 4 phases."""
+    rng = np.random.default_rng(seed)
+    spec = [((37, 30, 20), 2), ((21, 18, 26), 0), ((16, 9, 12), 1), ((40, 24, 18), 2),
+            ((13, 10, 8), 0), ((32, 32, 32), 1)]
+    out = []
+    for (nx, ny, nz), axis in spec:
+        n_ph = int(rng.integers(2, 5))
+        lam = np.stack([I.random_spd(rng) for _ in range(n_ph)])
+        out.append((I.random_phase(rng, nx, ny, nz, n_ph), lam, axis))
+    return out
+
+
+def _single(phase, lam, axis, lateral, opts):
+    nz, ny, nx = phase.shape
+    S = lbm.Solver(nx, ny, nz)
+    S.set_geometry(phase, lam.shape[0])
+    S.set_tensors(lam)
+    info = S.solve(axis, lateral, opts)
+    return info, S.temperature()
+
+
+@pytest.mark.parametrize("lateral", [0, 1])
+def test_batch_matches_single_solves_and_oracle(lateral):
+    cells = _cells(lateral)
+    B = lbm.Batch()
+    for ph, lam, axis in cells:
+        B.add(ph, lam, axis)
+    opts = lbm.Solver.opts(tol=0.0, max_iters=600, check_every=100)
+    binfo = B.solve(lateral, opts)
+    assert binfo.n_solves == len(cells) and binfo.block_threads in (128, 256, 512)
+    assert binfo.total_updates == 600 * sum(ph.size for ph, _, _ in cells)
+    for i, (ph, lam, axis) in enumerate(cells):
+        r = B.result(i)
+        assert r.iters == 600 and r.checks == 6
+        s_info, T_single = _single(ph, lam, axis, lateral, opts)
+        T = B.temperature(i)
+        assert np.max(np.abs(T - T_single)) <= 1e-6
+        assert r.k_eff == pytest.approx(s_info.k_eff, rel=1e-6)
+        ref = O.Lattice(ph, lam, r.lattice_scale, axis, lateral)
+        ref.init_linear()
+        ref.step(600)
+        assert np.max(np.abs(T - ref.temperature())) <= 1e-5
+        assert r.k_eff == pytest.approx(ref.k_eff()[0], rel=1e-5)
+
+
+def test_batch_solves_converge_independently():
+    """Cells converge after different iteration counts; each stops on its
+    own and gives the single-solve result."""
+    yarn = I.transversely_isotropic(6.0, 0.8, I.axis_in_xz_from_z(30.0))
+    lam = np.stack([I.isotropic(0.2), yarn])
+    B = lbm.Batch()
+    sizes = [(8, 8, 16), (8, 8, 32), (12, 12, 24)]
+    for nx, ny, nz in sizes:
+        B.add(I.layered_phase(nx, ny, nz, layer=nz // 4), lam, 2)
+    opts = lbm.Solver.opts(tol=1e-8, max_iters=2_000_000)
+    binfo = B.solve(0, opts)
+    assert binfo.n_converged == len(sizes) and binfo.status == lbm.LBM_OK
+    iters = []
+    for i, (nx, ny, nz) in enumerate(sizes):
+        r = B.result(i)
+        s_info, _ = _single(I.layered_phase(nx, ny, nz, layer=nz // 4), lam, 2, 0, opts)
+        assert r.status == lbm.LBM_OK and r.residual_T <= 1e-8
+        assert r.iters == s_info.iters
+        assert r.k_eff == pytest.approx(s_info.k_eff, rel=1e-6)
+        assert r.k_eff == pytest.approx(94.0 / 245.0, rel=2e-3)
+        iters.append(r.iters)
+    assert len(set(iters)) > 1
+
+
+@pytest.mark.parametrize("storage", [lbm.LBM_STORE_BF16, lbm.LBM_STORE_F16])
+def test_batch_16bit_storage(storage):
+    cells = _cells(7)[:4]
+    B = lbm.Batch()
+    for ph, lam, axis in cells:
+        B.add(ph, lam, axis)
+    opts = lbm.Solver.opts(tol=0.0, max_iters=400, storage=storage)
+    B.solve(0, opts)
+    for i, (ph, lam, axis) in enumerate(cells):
+        r = B.result(i)
+        s_info, T_single = _single(ph, lam, axis, 0, opts)
+        assert r.k_eff == pytest.approx(s_info.k_eff, rel=1e-4)
+        assert np.max(np.abs(B.temperature(i) - T_single)) <= 2e-3
+
+
+def test_batch_errors():
+    B = lbm.Batch()
+    with pytest.raises(lbm.LBMError) as e:
+        B.solve(0)
+    assert e.value.status == lbm.LBM_ERR_STATE
+    bad = np.zeros((4, 4, 4), np.uint8)
+    bad[0, 0, 0] = 3
+    with pytest.raises(lbm.LBMError):
+        B.add(bad, np.stack([I.isotropic(1.0)] * 2), 2)
+    with pytest.raises(lbm.LBMError):
+        B.add(np.zeros((4, 4, 4), np.uint8), I.sym6(np.diag([1.0, -2.0, 1.0]))[None], 2)
+    B.add(np.zeros((4, 4, 4), np.uint8), I.isotropic(1.0)[None], 2)
+    with pytest.raises(lbm.LBMError):
+        B.solve(0, lbm.Solver.opts(check_every=5))
