@@ -122,6 +122,74 @@ def make_cell(lbm, I, device):
     return S, lam, used, frac
 
 
+def time_to_keff(lbm, S, stream, iters_ref=250_000, rel=1e-4):
+    """Time to k_eff within `rel` of the reference on the bench cell from the
+    linear start: the first check after which every later k_eff stays within
+    rel of the FP32 value after iters_ref iterations, times the measured
+    device time per iteration.  For FP32 and for 16-bit storage."""
+    out = {}
+    k_ref = None
+    for name in ("f32", "bf16", "f16"):
+        o = S.opts(tol=0.0, max_iters=iters_ref, check_every=K, storage=STORAGE[name])
+        o.stream = int(stream.cuda_stream)
+        S.start(2, 0, o)
+        info = S.run()
+        h = S.history()
+        if k_ref is None:
+            k_ref = float(h[-1, 1])
+        err = np.abs(h[:, 1] / k_ref - 1.0)
+        bad = np.nonzero(err > rel)[0]
+        first = 0 if bad.size == 0 else int(bad[-1]) + 1
+        ms_per_iter = info.elapsed_ms / info.iters
+        reached = first < len(h)
+        n_it = int(h[first, 0]) if reached else None
+        out[name] = {"iters": n_it, "ms": n_it * ms_per_iter if reached else None,
+                     "ms_per_iter": ms_per_iter,
+                     "k_final_rel_vs_ref": float(h[-1, 1] / k_ref - 1.0)}
+    out["k_ref"] = k_ref
+    out["k_ref_iters"] = iters_ref
+    out["rel"] = rel
+    if out["f32"]["ms"] and out["bf16"]["ms"]:
+        out["speedup_bf16_vs_f32"] = out["f32"]["ms"] / out["bf16"]["ms"]
+    return out
+
+
+def sweep(lbm, I, n_cells=64, iters=500):
+    """The braid sweep of uneven cells (N_xy 64..160, N_z up to 320, yarn
+    fraction 0.30-0.60, braiding angle 20-45 deg), every cell along x, y and
+    z: one batched graph launch against the same solves run one by one."""
+    cells = I.braid_sweep_cells(n_cells)
+    phases = []
+    for c in cells:
+        with lbm.Solver(c["nx"], c["ny"], c["nz"]) as V:
+            V.set_geometry_braid(math.radians(c["g_deg"]),
+                                 I.braid_anchors(c["nx"], c["ny"], c["seed"], n_max=256), c["phi"])
+            phases.append((V.geometry(), I.braid_tensors(c["g_deg"])))
+    opts = lbm.Solver.opts(tol=0.0, max_iters=iters)
+    B = lbm.Batch()
+    for ph, lam in phases:
+        for axis in (0, 1, 2):
+            B.add(ph, lam, axis)
+    info = B.solve(0, opts)
+    batched = info.total_updates / info.elapsed_ms / 1e6
+    B.close()
+    seq_ms, seq_upd = 0.0, 0
+    for ph, lam in phases:
+        nz, ny, nx = ph.shape
+        with lbm.Solver(nx, ny, nz) as S1:
+            S1.set_geometry(ph, 5)
+            S1.set_tensors(lam)
+            for axis in (0, 1, 2):
+                r = S1.solve(axis, 0, opts)
+                seq_ms += r.elapsed_ms
+                seq_upd += r.iters * ph.size
+    return {"solves": 3 * len(cells), "cells": len(cells),
+            "voxels_per_axis": int(sum(p.size for p, _ in phases)), "iters_per_solve": iters,
+            "batched_glups": batched, "sequential_glups": seq_upd / seq_ms / 1e6,
+            "batched_ms": info.elapsed_ms, "sequential_ms": seq_ms,
+            "block_threads": info.block_threads, "unit": "GLUPS"}
+
+
 def cpu_oracle_sample(seconds_target=15.0):
     """Times the FP64 oracle on the host cores on the same cell: a fixed
     number of iterations of the full 128x128x256 lattice."""
@@ -265,6 +333,11 @@ def run_ours(args):
                               "k_eff_after_step": i16.k_eff,
                               "k_eff_rel_vs_f32": (i16.k_eff - info.k_eff) / info.k_eff}
 
+    extras = {}
+    if not args.no_extras:
+        extras["time_to_keff"] = time_to_keff(lbm, S, stream)
+        extras["sweep"] = sweep(lbm, I)
+
     # end to end through the public API with host buffers
     anchors = I.braid_anchors(NX, NY, SEED, n_max=NMAX)
     phase_h = S.geometry()
@@ -316,6 +389,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "k_eff_after_step": info.k_eff,
             "storage_variants": variants or None,
+            **extras,
             "wall_s_timed": wall,
         }
         print(json.dumps(line), flush=True)
@@ -338,6 +412,8 @@ def main():
                     help="distribution storage (collision is FP32 in every mode)")
     ap.add_argument("--no-variants", action="store_true",
                     help="omit the BF16/FP16 storage variants of the step")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="omit the time-to-k_eff runs and the batched sweep")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline leg")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--traffic", type=float, default=None,

@@ -147,6 +147,12 @@ lbm_status lbm_k_eff(const lbm_ctx* c, double* out);
  * original axis order). Synchronous. */
 lbm_status lbm_get_temperature(lbm_ctx* c, float* host_out);
 
+/* Convergence history of the current solve: for each of the most recent
+ * min(checks, max_entries, 65536) checks, oldest first, four doubles
+ * (iteration, k_eff, R_T, R_Q) into host_out.  *n_out (nullable) receives
+ * the number of entries written.  Synchronous. */
+lbm_status lbm_get_history(lbm_ctx* c, double* host_out, int max_entries, int* n_out);
+
 /* Plane sums Q[k] of the axial flux at the last check (n == N_axis doubles). */
 lbm_status lbm_get_plane_flux(const lbm_ctx* c, double* host_out, int n);
 

@@ -1,0 +1,93 @@
+"""FP64 CPU reference of the learned warm-start network (test infrastructure
+only: the tests compare the CUDA layer kernels and the whole network's
+gradients against it; the product never imports it).
+
+The network maps a cell's material field to a temperature correction
+relative to the linear profile between the walls (the temperature-difference
+axis is z).  Layers follow one written specification shared with the CUDA
+path only through this docstring:
+
+  input  x: 7 channels = 6 tensor components (xx, yy, zz, yz, xz, xy) divided
+            by the largest diagonal entry, and the linear profile T_lin(z)
+  conv3(7->32) relu, conv3(32->32) relu                      -> s1   (full)
+  avgpool2, conv3(32->64) relu, conv3(64->64) relu            -> s2   (1/2)
+  avgpool2, conv3(64->128) relu, conv3(128->128) relu               (1/4)
+  upsample2, concat[up, s2], conv3(192->64) relu, conv3(64->64) relu (1/2)
+  upsample2, concat[up, s1], conv3(96->32) relu                     (full)
+  conv1(32->1)                                          -> dT, T = T_lin + dT
+
+conv3: 3x3x3 cross-correlation with bias, periodic (circular) padding in x
+and y, zero padding in z.  avgpool2: mean of 2x2x2 blocks.  upsample2:
+nearest neighbour.  Loss: mean squared error of T over all voxels.
+
+Plain PyTorch CPU ops in float64; reverse-mode differentiation of those ops
+gives the reference gradients.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+import torch.nn.functional as F
+
+CONV3 = [(7, 32), (32, 32), (32, 64), (64, 64), (64, 128), (128, 128),
+         (192, 64), (64, 64), (96, 32)]
+HEAD = (32, 1)
+
+
+def init_params(seed: int = 0):
+    """He-normal weights (torch layout [Cout, Cin, 3, 3, 3]) and zero biases."""
+    g = np.random.default_rng(seed)
+    params = []
+    for ci, co in CONV3:
+        w = g.standard_normal((co, ci, 3, 3, 3)) * np.sqrt(2.0 / (27 * ci))
+        params.append((w, np.zeros(co)))
+    ci, co = HEAD
+    params.append((g.standard_normal((co, ci, 1, 1, 1)) * np.sqrt(1.0 / ci), np.zeros(co)))
+    return params
+
+
+def conv3(x, w, b):
+    """x [N, C, D, H, W]; circular pad in H, W (y, x), zero pad in D (z)."""
+    xp = F.pad(x, (1, 1, 1, 1, 0, 0), mode="circular")
+    xp = F.pad(xp, (0, 0, 0, 0, 1, 1))
+    return F.conv3d(xp, w, b)
+
+
+def forward(params, x):
+    """x: torch float64 [N, 7, D, H, W] -> dT [N, 1, D, H, W]."""
+    p = [(torch.as_tensor(w), torch.as_tensor(b)) for w, b in params]
+    h = F.relu(conv3(x, *p[0]))
+    s1 = F.relu(conv3(h, *p[1]))
+    h = F.avg_pool3d(s1, 2)
+    h = F.relu(conv3(h, *p[2]))
+    s2 = F.relu(conv3(h, *p[3]))
+    h = F.avg_pool3d(s2, 2)
+    h = F.relu(conv3(h, *p[4]))
+    h = F.relu(conv3(h, *p[5]))
+    h = F.interpolate(h, scale_factor=2, mode="nearest")
+    h = torch.cat([h, s2], dim=1)
+    h = F.relu(conv3(h, *p[6]))
+    h = F.relu(conv3(h, *p[7]))
+    h = F.interpolate(h, scale_factor=2, mode="nearest")
+    h = torch.cat([h, s1], dim=1)
+    h = F.relu(conv3(h, *p[8]))
+    return F.conv3d(h, *p[9])
+
+
+def loss_and_grads(params, x, t_lin, target):
+    """MSE of T = T_lin + dT against target; returns (loss, [(dW, db), ...])."""
+    p = [(torch.tensor(w, requires_grad=True), torch.tensor(b, requires_grad=True))
+         for w, b in params]
+    dT = forward([(w, b) for w, b in p], torch.as_tensor(x))
+    T = torch.as_tensor(t_lin) + dT
+    loss = ((T - torch.as_tensor(target)) ** 2).mean()
+    loss.backward()
+    return float(loss), [(w.grad.numpy(), b.grad.numpy()) for w, b in p]
+
+
+def conv3_np(x_ndhwc, w_t, b):
+    """Single layer in the device layout: x [N, D, H, W, Cin], w_t torch
+    layout [Cout, Cin, 3, 3, 3] -> y [N, D, H, W, Cout] (no activation)."""
+    x = torch.as_tensor(np.moveaxis(x_ndhwc, -1, 1))
+    y = conv3(x, torch.as_tensor(w_t), torch.as_tensor(b))
+    return np.moveaxis(y.numpy(), 1, -1)

@@ -63,6 +63,7 @@ struct lbm_ctx {
     float* d_T = nullptr;                  // nx*ny*nz staging (T output / t_init input)
     Ctl* d_ctl = nullptr;
     Ctl* h_ctl = nullptr;                  // pinned mirror
+    double* d_hist = nullptr;              // per-check history ring [kHistCap][4]
     double s = 0.0;
     double t_ref = 0.0;
     int blocks_per_plane = 0;
@@ -80,6 +81,8 @@ struct lbm_ctx {
 };
 
 namespace {
+
+constexpr int kHistCap = 1 << 16;          // checks kept in the history ring
 
 lbm_status fail(lbm_ctx* c, lbm_status st, const char* fmt, ...) {
     char buf[512];
@@ -219,6 +222,8 @@ lbm::StepArgs step_args(const lbm_ctx* c, int src, Frame fr, const Closing& cl =
     k.inv_quantum = 1.0 / c->quantum;
     k.handle = cl.handle;
     k.use_handle = cl.use_handle;
+    k.hist = c->d_hist;
+    k.hist_cap = kHistCap;
     return a;
 }
 
@@ -412,6 +417,7 @@ lbm_status lbm_create(int nx, int ny, int nz, int cuda_device, lbm_ctx** out) {
               cudaMalloc((void**)&c->d_phase, (size_t)N) == cudaSuccess &&
               cudaMalloc((void**)&c->d_T, sizeof(float) * (size_t)N) == cudaSuccess &&
               cudaMalloc((void**)&c->d_ctl, sizeof(Ctl)) == cudaSuccess &&
+              cudaMalloc((void**)&c->d_hist, sizeof(double) * 4 * kHistCap) == cudaSuccess &&
               cudaMallocHost((void**)&c->h_ctl, sizeof(Ctl)) == cudaSuccess &&
               cudaEventCreate(&c->ev0) == cudaSuccess && cudaEventCreate(&c->ev1) == cudaSuccess;
     if (!ok) {
@@ -754,6 +760,29 @@ lbm_status lbm_get_plane_flux(const lbm_ctx* c, double* host_out, int n) {
     return LBM_OK;
 }
 
+lbm_status lbm_get_history(lbm_ctx* c, double* host_out, int max_entries, int* n_out) {
+    CHECK_CTX(c);
+    if (!host_out || max_entries < 0) return fail(c, LBM_ERR_INVALID_ARG, "bad output buffer");
+    if (!c->started) return fail(c, LBM_ERR_STATE, "no solve state");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    lbm_status st = read_ctl(c, c->stream);
+    if (st != LBM_OK) return st;
+    const long long checks = c->h_ctl->checks;
+    const long long kept = checks < kHistCap ? checks : kHistCap;
+    const long long n = kept < max_entries ? kept : max_entries;
+    std::vector<double> ring(4 * (size_t)kHistCap);
+    if (n > 0)
+        CUDA_TRY(c, cudaMemcpy(ring.data(), c->d_hist, sizeof(double) * 4 * kHistCap,
+                               cudaMemcpyDeviceToHost));
+    // the n most recent checks, oldest first
+    for (long long i = 0; i < n; ++i) {
+        const long long chk = checks - n + i;           // 0-based check index
+        std::memcpy(host_out + 4 * i, &ring[4 * (size_t)(chk % kHistCap)], sizeof(double) * 4);
+    }
+    if (n_out) *n_out = (int)n;
+    return LBM_OK;
+}
+
 lbm_status lbm_get_geometry(lbm_ctx* c, uint8_t* host_out) {
     CHECK_CTX(c);
     if (!host_out) return fail(c, LBM_ERR_INVALID_ARG, "host_out is NULL");
@@ -817,6 +846,7 @@ void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->d_T);
     cudaFree(c->d_phase);
     cudaFree(c->d_ctl);
+    cudaFree(c->d_hist);
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);

@@ -72,6 +72,8 @@ struct CheckArgs {
     double quantum, inv_quantum;     // grid of the reference values (power of two)
     cudaGraphConditionalHandle handle;
     int use_handle;
+    double* hist;                    // history ring [hist_cap][4] or null
+    int hist_cap;
 };
 
 struct StepArgs {
@@ -185,6 +187,13 @@ __device__ void close_check(const StepArgs& a) {
             else status = 5;                              // LBM_ERR_NOT_CONVERGED (so far)
         }
         c->status = status;
+        if (ck.hist) {
+            double* hrow = ck.hist + 4 * ((c->checks - 1) % ck.hist_cap);
+            hrow[0] = (double)c->iter;
+            hrow[1] = c->k_eff;
+            hrow[2] = c->r_t;
+            hrow[3] = c->r_q;
+        }
         const bool stop = status != 5 || c->iter + ck.interval > ck.max_iters;
         c->done = stop ? 1 : 0;
         c->glob_cnt = 0u;

@@ -82,6 +82,8 @@ _PROTOS = {
     "lbm_k_eff": (ctypes.c_int, [_ctx_p, ctypes.POINTER(ctypes.c_double)]),
     "lbm_get_temperature": (ctypes.c_int, [_ctx_p, ctypes.POINTER(ctypes.c_float)]),
     "lbm_get_plane_flux": (ctypes.c_int, [_ctx_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    "lbm_get_history": (ctypes.c_int, [_ctx_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int)]),
     "lbm_set_geometry_braid": (ctypes.c_int, [_ctx_p, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                               ctypes.c_int, ctypes.c_double,
@@ -198,6 +200,14 @@ def lbm_get_temperature(ctx, out: np.ndarray) -> int:
 def lbm_get_plane_flux(ctx, out: np.ndarray) -> int:
     assert out.dtype == np.float64 and out.flags.c_contiguous
     return load().lbm_get_plane_flux(ctx, _f64(out), out.size)
+
+
+def lbm_get_history(ctx, max_entries: int = 1 << 16):
+    """Returns (status, array (n, 4) of iteration, k_eff, R_T, R_Q)."""
+    out = np.zeros((max_entries, 4), np.float64)
+    n = ctypes.c_int(0)
+    st = load().lbm_get_history(ctx, _f64(out), max_entries, ctypes.byref(n))
+    return st, out[: n.value]
 
 
 def lbm_set_geometry_braid(ctx, g_rad: float, A: float, B: float, anchors: np.ndarray,
@@ -388,6 +398,11 @@ class Solver:
             out = np.empty(self.shape, np.float32)
         self._ok(lbm_get_temperature(self.h, out))
         return out
+
+    def history(self) -> np.ndarray:
+        st, h = lbm_get_history(self.h)
+        self._ok(st)
+        return h
 
     def plane_flux(self, n_axis: int) -> np.ndarray:
         out = np.empty(n_axis, np.float64)

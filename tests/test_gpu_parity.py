@@ -302,3 +302,23 @@ def test_section33_dual_component_cube():
     ref.init_linear()
     ref.step(info.iters)
     assert info.k_eff == pytest.approx(ref.k_eff()[0], rel=K_TOL)
+
+
+def test_history_records_every_check():
+    rng = np.random.default_rng(12)
+    lam = np.stack([I.random_spd(rng) for _ in range(2)])
+    phase = I.random_phase(rng, 16, 12, 20, 2)
+    S = lbm.Solver(16, 12, 20)
+    S.set_geometry(phase, 2)
+    S.set_tensors(lam)
+    info = S.solve(2, 0, S.opts(tol=0.0, max_iters=1000, check_every=50))
+    h = S.history()
+    assert h.shape == (20, 4)
+    assert np.array_equal(h[:, 0], np.arange(50, 1001, 50))
+    assert h[-1, 1] == info.k_eff and h[-1, 2] == info.residual_T
+    # the oracle's k_eff along the same trajectory
+    ref = O.Lattice(phase, lam, info.lattice_scale, 2, 0)
+    ref.init_linear()
+    for row in h[:4]:
+        ref.step(int(row[0]) - ref.iter)
+        assert row[1] == pytest.approx(ref.k_eff()[0], rel=K_TOL)
