@@ -218,6 +218,78 @@ const char* lbm_batch_last_error(const lbm_batch* b);
 /* Frees the batch and its device memory. NULL-safe. */
 void lbm_batch_destroy(lbm_batch* b);
 
+/* ---- Learned warm start: layers of the 3D convolutional network ---------
+ * The paper's method only needs the steady state (Section 2.3, Eq. 20), so
+ * the iteration may start from any field; these layers predict that field
+ * from the material so the iteration starts near it.  The converged lattice
+ * Boltzmann solve remains the answer.  All tensors are device pointers in
+ * caller memory, channels last: element [v][c] at v * C + c with the voxel
+ * index v = ((n * d + z) * h + y) * w + x over a batch of n cells of d x h x w
+ * (z the temperature-difference axis).  Activations and weights are BF16,
+ * accumulation FP32.  stream: cudaStream_t (NULL = legacy default stream).
+ * Calls are asynchronous; they return LBM_ERR_INVALID_ARG on a bad size or
+ * NULL pointer and LBM_ERR_CUDA on a launch error. */
+
+/* y = act(bias + conv(x, w)): ksize 3 (27 taps, periodic in x and y, zero
+ * outside in z) or 1.  x [V][cin] (cin a multiple of 16), w [taps][cin][cout]
+ * (tap = (dz*3 + dy)*3 + dx), bias [cout] FP32 or NULL, y [V][cout] BF16, or
+ * FP32 if out_f32 (cout a multiple of 32).  relu != 0 applies max(., 0).
+ * Runs on the tensor cores (mma.sync m16n8k16, implicit GEMM). */
+lbm_status lbm_nn_conv3d(const void* x, int cin, const void* w, const float* bias, void* y, int cout,
+                         int n, int d, int h, int wdt, int ksize, int relu, int out_f32,
+                         void* stream);
+
+/* dw[tap][ci][co] += sum_v x[v + tap][ci] g[v][co] (FP32 accumulation into dw;
+ * zero dw first).  Same layouts and padding as lbm_nn_conv3d. */
+lbm_status lbm_nn_conv3d_wgrad(const void* x, int cin, const void* g, int cout, float* dw, int n,
+                               int d, int h, int wdt, int ksize, void* stream);
+
+/* wf[tap][co][ci] = w[taps-1-tap][ci][co]: with it lbm_nn_conv3d computes the
+ * gradient with respect to the conv's input. */
+lbm_status lbm_nn_flip_weights(const void* w, void* wf, int cin, int cout, int ksize, void* stream);
+
+/* db[c] += sum_v g[v][c] (c <= 1024). */
+lbm_status lbm_nn_bias_grad(const void* g, int c, long long nvox, float* db, void* stream);
+
+/* g = dy where y > 0, else 0 (backward of a fused ReLU whose output is y). */
+lbm_status lbm_nn_relu_mask(const void* dy, const void* y, void* g, long long count, void* stream);
+
+/* y[parent] = scale * sum of the 8 children of x; (d, h, w) are x's sizes
+ * (even).  scale 1/8 is 2x2x2 average pooling, 1 the backward of upsampling. */
+lbm_status lbm_nn_pool2(const void* x, void* y, int c, int n, int d, int h, int w, float scale,
+                        void* stream);
+
+/* y[child] = scale * x[parent]; (d, h, w) are y's sizes (even).  scale 1 is
+ * nearest upsampling, 1/8 the backward of average pooling. */
+lbm_status lbm_nn_upsample2(const void* x, void* y, int c, int n, int d, int h, int w, float scale,
+                            void* stream);
+
+/* y[v] = [a[v] (ca channels), b[v] (cb channels)]. */
+lbm_status lbm_nn_concat(const void* a, int ca, const void* b, int cb, void* y, long long nvox,
+                         void* stream);
+
+/* dst[v][0:c] = src[v][coff:coff+c] (+ dst if accumulate); src has csrc channels. */
+lbm_status lbm_nn_slice(const void* src, int csrc, int coff, void* dst, int c, long long nvox,
+                        int accumulate, void* stream);
+
+/* Output head: pred[v] = t_lin[v] + b + w . h[v] (h: 32 BF16 channels, w, b
+ * FP32).  With target != NULL also the squared-error loss and its gradients:
+ * loss += sum_v (pred - target)^2, dT = 2 (pred - target) / nvox,
+ * dh = dT w (BF16), dw += sum dT h, db += sum dT. */
+lbm_status lbm_nn_head(const void* h, const float* w, const float* b, const float* t_lin,
+                       const float* target, float* pred, void* dh, float* dw, float* db,
+                       double* loss, long long nvox, void* stream);
+
+/* Network input x [V][16] BF16: channels 0..5 = table[phase[v]] (six tensor
+ * components per phase, FP32), channel 6 = t_lin_z[z], 7..15 = 0. */
+lbm_status lbm_nn_input(const uint8_t* phase, const float* table, const float* t_lin_z, void* x,
+                        int n, int d, int h, int w, void* stream);
+
+/* One Adam step on FP32 master weights p with gradient g and moments m, v
+ * (step counts from 1); p_bf16 (nullable) receives the BF16 copy. */
+lbm_status lbm_nn_adam(float* p, const float* g, float* m, float* v, void* p_bf16, long long count,
+                       float lr, float beta1, float beta2, float eps, int step, void* stream);
+
 /* Largest n_max accepted by lbm_braid_voxelize_noalloc. */
 #define LBM_NOALLOC_MAX_YARNS 1024
 

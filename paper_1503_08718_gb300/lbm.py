@@ -113,6 +113,18 @@ _PROTOS = {
                                                  ctypes.POINTER(ctypes.c_float)]),
     "lbm_batch_last_error": (ctypes.c_char_p, [_ctx_p]),
     "lbm_batch_destroy": (None, [_ctx_p]),
+    "lbm_nn_conv3d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "lbm_nn_conv3d_wgrad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "lbm_nn_flip_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "lbm_nn_bias_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]),
+    "lbm_nn_relu_mask": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p]),
+    "lbm_nn_pool2": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_void_p]),
+    "lbm_nn_upsample2": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_void_p]),
+    "lbm_nn_concat": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p]),
+    "lbm_nn_slice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_int, ctypes.c_void_p]),
+    "lbm_nn_head": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p]),
+    "lbm_nn_input": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "lbm_nn_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_int, ctypes.c_void_p]),
     "lbm_last_error": (ctypes.c_char_p, [_ctx_p]),
     "lbm_destroy": (None, [_ctx_p]),
 }
@@ -304,6 +316,30 @@ def lbm_batch_last_error(b) -> str:
 
 def lbm_batch_destroy(b) -> None:
     load().lbm_batch_destroy(b)
+
+
+# ---- network layers (device pointers as ints, cudaStream_t as int) -------
+
+def _nn(name):
+    def call(*args):
+        return getattr(load(), name)(*args)
+    call.__name__ = name
+    call.__doc__ = f"{name}: see include/lbm.h; arguments are device addresses and sizes."
+    return call
+
+
+lbm_nn_conv3d = _nn("lbm_nn_conv3d")
+lbm_nn_conv3d_wgrad = _nn("lbm_nn_conv3d_wgrad")
+lbm_nn_flip_weights = _nn("lbm_nn_flip_weights")
+lbm_nn_bias_grad = _nn("lbm_nn_bias_grad")
+lbm_nn_relu_mask = _nn("lbm_nn_relu_mask")
+lbm_nn_pool2 = _nn("lbm_nn_pool2")
+lbm_nn_upsample2 = _nn("lbm_nn_upsample2")
+lbm_nn_concat = _nn("lbm_nn_concat")
+lbm_nn_slice = _nn("lbm_nn_slice")
+lbm_nn_head = _nn("lbm_nn_head")
+lbm_nn_input = _nn("lbm_nn_input")
+lbm_nn_adam = _nn("lbm_nn_adam")
 
 
 # ---- convenience object ---------------------------------------------------

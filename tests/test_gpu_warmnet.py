@@ -1,0 +1,176 @@
+"""The learned warm start: the network's CUDA layers against the FP64 CPU
+reference (oracle/warmnet_ref.py), gradients of the whole network, training,
+and the iterations the trained network saves the solver.
+
+BF16 activations and weights carry a relative rounding of 2^-8; layer
+outputs are compared with FP32 output (accumulation error only) at 1e-3 of
+the output scale, whole-network gradients by direction (cosine >= 0.99) and
+relative norm (<= 5 %), the usual bar for BF16 training.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import warmnet_ref as R
+from paper_1503_08718_gb300 import inputs as I
+from paper_1503_08718_gb300 import lbm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1503_08718_gb300 import build
+    build.build()
+    lbm.load()
+    return t
+
+
+def _bf16_round(a):
+    import torch as T
+    return T.from_numpy(np.asarray(a, np.float32)).to(T.bfloat16).to(T.float64).numpy()
+
+
+@pytest.mark.parametrize("cin,cout,ksize", [(16, 32, 3), (32, 64, 3), (96, 32, 3), (192, 64, 3),
+                                            (64, 128, 3), (32, 32, 1)])
+def test_conv_forward_matches_reference(torch, cin, cout, ksize):
+    rng = np.random.default_rng(cin + cout)
+    n, d, h, w = 2, 4, 6, 8
+    x = _bf16_round(rng.standard_normal((n, d, h, w, cin)))
+    wt = _bf16_round(rng.standard_normal((cout, cin, ksize, ksize, ksize)) / math.sqrt(cin * ksize ** 3))
+    b = rng.standard_normal(cout)
+    if ksize == 3:
+        ref = R.conv3_np(x, wt, b)
+    else:
+        ref = np.einsum("ndhwc,oc->ndhwo", x, wt[:, :, 0, 0, 0]) + b
+    dev = torch.device("cuda")
+    xg = torch.from_numpy(x.reshape(-1, cin)).to(torch.bfloat16).to(dev)
+    wg = torch.from_numpy(np.transpose(wt.reshape(cout, cin, -1), (2, 1, 0)).copy()).to(torch.bfloat16).to(dev)
+    bg = torch.from_numpy(b.astype(np.float32)).to(dev)
+    y = torch.empty((n * d * h * w, cout), dtype=torch.float32, device=dev)
+    st = lbm.lbm_nn_conv3d(xg.data_ptr(), cin, wg.data_ptr(), bg.data_ptr(), y.data_ptr(), cout,
+                           n, d, h, w, ksize, 0, 1, None)
+    assert st == lbm.LBM_OK
+    got = y.cpu().numpy().reshape(ref.shape)
+    assert np.max(np.abs(got - ref)) <= 1e-3 * np.max(np.abs(ref))
+    # fused ReLU with BF16 output
+    yb = torch.empty((n * d * h * w, cout), dtype=torch.bfloat16, device=dev)
+    lbm.lbm_nn_conv3d(xg.data_ptr(), cin, wg.data_ptr(), bg.data_ptr(), yb.data_ptr(), cout,
+                      n, d, h, w, ksize, 1, 0, None)
+    gotb = yb.float().cpu().numpy().reshape(ref.shape)
+    assert np.max(np.abs(gotb - np.maximum(ref, 0))) <= 1e-2 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 32), (96, 64), (128, 128)])
+def test_conv_weight_gradient_matches_reference(torch, cin, cout):
+    rng = np.random.default_rng(7 * cin + cout)
+    n, d, h, w = 1, 4, 8, 8
+    x = _bf16_round(rng.standard_normal((n, d, h, w, cin)))
+    g = _bf16_round(rng.standard_normal((n, d, h, w, cout)))
+    # reference: d/dW of sum(g * conv(x, W)) by reverse mode in FP64
+    import torch as T
+    W = T.zeros((cout, cin, 3, 3, 3), dtype=T.float64, requires_grad=True)
+    y = R.conv3(T.from_numpy(np.moveaxis(x, -1, 1)), W, None)
+    (y * T.from_numpy(np.moveaxis(g, -1, 1))).sum().backward()
+    ref = np.transpose(W.grad.numpy().reshape(cout, cin, 27), (2, 1, 0))
+    dev = torch.device("cuda")
+    xg = torch.from_numpy(x.reshape(-1, cin)).to(torch.bfloat16).to(dev)
+    gg = torch.from_numpy(g.reshape(-1, cout)).to(torch.bfloat16).to(dev)
+    dw = torch.zeros((27, cin, cout), dtype=torch.float32, device=dev)
+    assert lbm.lbm_nn_conv3d_wgrad(xg.data_ptr(), cin, gg.data_ptr(), cout, dw.data_ptr(),
+                                   n, d, h, w, 3, None) == lbm.LBM_OK
+    assert np.max(np.abs(dw.cpu().numpy() - ref)) <= 1e-4 * np.max(np.abs(ref))
+
+
+def _tiny_case(seed=3, n=1, d=8, h=8, w=8):
+    rng = np.random.default_rng(seed)
+    lam = np.stack([I.random_spd(rng) for _ in range(3)])
+    phase = rng.integers(0, 3, size=(n, d, h, w), dtype=np.uint8)
+    target = rng.uniform(0, 1, size=(n, d, h, w))
+    return phase, [lam] * n, target
+
+
+def _ref_input(phase, lams, d):
+    from paper_1503_08718_gb300.warmstart import linear_profile, material_table
+    n = phase.shape[0]
+    x = np.zeros((n, 7) + phase.shape[1:])
+    for i in range(n):
+        tab = _bf16_round(material_table(lams[i]))
+        x[i, :6] = np.moveaxis(tab[phase[i]], -1, 0)
+    prof = linear_profile(d)
+    x[:, 6] = _bf16_round(prof)[None, :, None, None]
+    t_lin = np.broadcast_to(prof.astype(np.float64)[None, None, :, None, None], (n, 1) + phase.shape[1:])
+    return x, t_lin
+
+
+def test_network_loss_and_gradients_match_reference(torch):
+    from paper_1503_08718_gb300.warmstart import WarmNet
+    phase, lams, target = _tiny_case()
+    n, d, h, w = phase.shape
+    params = R.init_params(seed=5)
+    # a nonzero head so every layer receives gradient
+    params[-1] = (params[-1][0] * 0 + 0.3 * np.random.default_rng(1).standard_normal((1, 32, 1, 1, 1)),
+                  np.zeros(1))
+    params = [(_bf16_round(wt), b) for wt, b in params[:-1]] + [params[-1]]
+    net = WarmNet(seed=0)
+    net.set_reference_params(params)
+    x0, tl = net.make_input(phase, lams)
+    tgt = torch.from_numpy(target.reshape(-1).astype(np.float32)).to(net.dev)
+    pred, loss = net.forward(x0, (n, d, h, w), tl, tgt)
+    net.backward()
+    x, t_lin = _ref_input(phase, lams, d)
+    ref_loss, ref_grads = R.loss_and_grads(params, x, t_lin, target[:, None])
+    V = n * d * h * w
+    assert float(loss.item()) / V == pytest.approx(ref_loss, rel=2e-2)
+    for l in range(len(R.CONV3)):
+        gw = net.gW[l].cpu().numpy()[:, : R.CONV3[l][0], :]
+        rw = np.transpose(ref_grads[l][0].reshape(R.CONV3[l][1], R.CONV3[l][0], 27), (2, 1, 0))
+        cos = np.sum(gw * rw) / (np.linalg.norm(gw) * np.linalg.norm(rw))
+        assert cos >= 0.99, (l, cos)
+        assert np.linalg.norm(gw - rw) <= 0.05 * np.linalg.norm(rw), l
+        gb, rb = net.gb[l].cpu().numpy(), ref_grads[l][1]
+        assert np.linalg.norm(gb - rb) <= 0.05 * np.linalg.norm(rb) + 1e-7, l
+    hw = net.g_hw.cpu().numpy()
+    rhw = ref_grads[-1][0].reshape(-1)
+    assert np.linalg.norm(hw - rhw) <= 0.05 * np.linalg.norm(rhw)
+
+
+def test_training_reduces_the_loss(torch):
+    from paper_1503_08718_gb300.warmstart import WarmNet, train
+    rng = np.random.default_rng(0)
+    phases = rng.integers(0, 2, size=(8, 16, 16, 16), dtype=np.uint8)
+    lams = [np.stack([I.isotropic(0.5), I.isotropic(2.0)])] * 8
+    # a smooth target the inputs determine: linear profile plus a phase bump
+    prof = np.linspace(1, 0, 16)[None, :, None, None]
+    temps = prof + 0.05 * (phases - 0.5)
+    net = WarmNet(seed=1)
+    hist = train(net, phases, lams, temps, epochs=15, batch=4, lr=2e-3)
+    assert hist[-1] < 0.5 * hist[0]
+
+
+def test_warm_start_saves_iterations(torch):
+    """Trained on solver outputs of seeded 64^3 braided cells, the network's
+    prediction starts held-out cells closer to their steady state: fewer
+    iterations to R_T <= 1e-8, the same converged k_eff."""
+    from paper_1503_08718_gb300.warmstart import WarmNet, generate_cells, train
+    ph, lams, temps, _ = generate_cells(range(40), n=64)
+    net = WarmNet(seed=2)
+    train(net, ph, lams, temps, epochs=12, batch=4, lr=1e-3)
+    ph_t, lams_t, _, _ = generate_cells(range(900, 903), n=64)
+    saved = []
+    for i in range(3):
+        S = lbm.Solver(64, 64, 64)
+        S.set_geometry(ph_t[i], 5)
+        S.set_tensors(lams_t[i])
+        base = S.solve(2, 0, S.opts(tol=1e-8, max_iters=2_000_000), allow=())
+        T0 = np.ascontiguousarray(net.predict(ph_t[i], lams_t[i]), dtype=np.float32)
+        o = S.opts(tol=1e-8, max_iters=2_000_000)
+        o.t_init = T0.ctypes.data_as(lbm.ctypes.POINTER(lbm.ctypes.c_float))
+        warm = S.solve(2, 0, o, allow=())
+        assert warm.k_eff == pytest.approx(base.k_eff, rel=2e-4)
+        saved.append(1.0 - warm.iters / base.iters)
+    assert np.mean(saved) > 0.1, saved
