@@ -9,11 +9,11 @@ path only through this docstring:
 
   input  x: 7 channels = 6 tensor components (xx, yy, zz, yz, xz, xy) divided
             by the largest diagonal entry, and the linear profile T_lin(z)
-  conv3(7->32) relu, conv3(32->32) relu                      -> s1   (full)
-  avgpool2, conv3(32->64) relu, conv3(64->64) relu            -> s2   (1/2)
-  avgpool2, conv3(64->128) relu, conv3(128->128) relu               (1/4)
-  upsample2, concat[up, s2], conv3(192->64) relu, conv3(64->64) relu (1/2)
-  upsample2, concat[up, s1], conv3(96->32) relu                     (full)
+  channels per level c_0 = 32, c_1, ..., c_L (default 32, 64, 128)
+  encoder level i: [avgpool2 if i > 0], conv3(. -> c_i) relu, conv3(c_i -> c_i)
+            relu -> s_i
+  decoder level i = L-1 .. 0: upsample2, concat[up, s_i],
+            conv3(c_(i+1) + c_i -> c_i) relu, conv3(c_i -> c_i) relu
   conv1(32->1)                                          -> dT, T = T_lin + dT
 
 conv3: 3x3x3 cross-correlation with bias, periodic (circular) padding in x
@@ -29,16 +29,30 @@ import numpy as np
 import torch
 import torch.nn.functional as F
 
-CONV3 = [(7, 32), (32, 32), (32, 64), (64, 64), (64, 128), (128, 128),
-         (192, 64), (64, 64), (96, 32)]
+CHANS = (32, 64, 128)
+
+
+def conv_layers(chans=CHANS, cin=7):
+    """(cin, cout) of the 3x3x3 convolutions in order: two per encoder level,
+    two per decoder level."""
+    L = len(chans) - 1
+    layers = [(cin, chans[0]), (chans[0], chans[0])]
+    for i in range(1, L + 1):
+        layers += [(chans[i - 1], chans[i]), (chans[i], chans[i])]
+    for i in range(L - 1, -1, -1):
+        layers += [(chans[i + 1] + chans[i], chans[i]), (chans[i], chans[i])]
+    return layers
+
+
+CONV3 = conv_layers()
 HEAD = (32, 1)
 
 
-def init_params(seed: int = 0):
+def init_params(seed: int = 0, chans=CHANS):
     """He-normal weights (torch layout [Cout, Cin, 3, 3, 3]) and zero biases."""
     g = np.random.default_rng(seed)
     params = []
-    for ci, co in CONV3:
+    for ci, co in conv_layers(chans):
         w = g.standard_normal((co, ci, 3, 3, 3)) * np.sqrt(2.0 / (27 * ci))
         params.append((w, np.zeros(co)))
     ci, co = HEAD
@@ -53,36 +67,36 @@ def conv3(x, w, b):
     return F.conv3d(xp, w, b)
 
 
-def forward(params, x):
+def forward(params, x, chans=CHANS):
     """x: torch float64 [N, 7, D, H, W] -> dT [N, 1, D, H, W]."""
     p = [(torch.as_tensor(w), torch.as_tensor(b)) for w, b in params]
-    h = F.relu(conv3(x, *p[0]))
-    s1 = F.relu(conv3(h, *p[1]))
-    h = F.avg_pool3d(s1, 2)
-    h = F.relu(conv3(h, *p[2]))
-    s2 = F.relu(conv3(h, *p[3]))
-    h = F.avg_pool3d(s2, 2)
-    h = F.relu(conv3(h, *p[4]))
-    h = F.relu(conv3(h, *p[5]))
-    h = F.interpolate(h, scale_factor=2, mode="nearest")
-    h = torch.cat([h, s2], dim=1)
-    h = F.relu(conv3(h, *p[6]))
-    h = F.relu(conv3(h, *p[7]))
-    h = F.interpolate(h, scale_factor=2, mode="nearest")
-    h = torch.cat([h, s1], dim=1)
-    h = F.relu(conv3(h, *p[8]))
-    return F.conv3d(h, *p[9])
+    L = len(chans) - 1
+    k = 0
+    h = x
+    skips = []
+    for i in range(L + 1):
+        if i > 0:
+            h = F.avg_pool3d(h, 2)
+        h = F.relu(conv3(h, *p[k])); k += 1
+        h = F.relu(conv3(h, *p[k])); k += 1
+        skips.append(h)
+    for i in range(L - 1, -1, -1):
+        h = F.interpolate(h, scale_factor=2, mode="nearest")
+        h = torch.cat([h, skips[i]], dim=1)
+        h = F.relu(conv3(h, *p[k])); k += 1
+        h = F.relu(conv3(h, *p[k])); k += 1
+    return F.conv3d(h, *p[k])
 
 
-def loss_and_grads(params, x, t_lin, target):
+def loss_and_grads(params, x, t_lin, target, chans=CHANS):
     """MSE of T = T_lin + dT against target; returns (loss, [(dW, db), ...])."""
     p = [(torch.tensor(w, requires_grad=True), torch.tensor(b, requires_grad=True))
          for w, b in params]
-    dT = forward([(w, b) for w, b in p], torch.as_tensor(x))
-    T = torch.as_tensor(t_lin) + dT
+    dT = forward([(w, b) for w, b in p], torch.as_tensor(x), chans)
+    T = torch.as_tensor(np.array(t_lin)) + dT
     loss = ((T - torch.as_tensor(target)) ** 2).mean()
     loss.backward()
-    return float(loss), [(w.grad.numpy(), b.grad.numpy()) for w, b in p]
+    return float(loss.detach()), [(w.grad.numpy(), b.grad.numpy()) for w, b in p]
 
 
 def conv3_np(x_ndhwc, w_t, b):

@@ -12,10 +12,12 @@ convolutions on the tensor cores, FP32 accumulation); this module only
 allocates buffers (torch), sequences the layer calls and keeps the optimiser
 state.  Training targets come from the library's own solver.
 
-Architecture (weights [taps][cin][cout], activations channels-last):
-  conv3 16(7)->32, conv3 32->32 = s1 | pool | conv3 32->64, conv3 64->64 = s2 |
-  pool | conv3 64->128, conv3 128->128 | up, cat s2 | conv3 192->64,
-  conv3 64->64 | up, cat s1 | conv3 96->32 | conv1 32->1 head: T = T_lin + out
+Architecture (weights [taps][cin][cout], activations channels-last), with
+channels c_0 = 32, c_1, ..., c_L per level:
+  encoder level i: [2x2x2 average pool if i > 0], conv3 -> c_i, conv3 c_i -> c_i
+  decoder level i = L-1..0: nearest upsample, concat with encoder level i,
+          conv3 (c_(i+1) + c_i) -> c_i, conv3 c_i -> c_i
+  head: conv1 32 -> 1, T = T_lin + out.   (All convs but the head use ReLU.)
 """
 from __future__ import annotations
 
@@ -26,10 +28,20 @@ import numpy as np
 from . import inputs as I
 from . import lbm
 
-CONV3 = [(16, 32), (32, 32), (32, 64), (64, 64), (64, 128), (128, 128), (192, 64), (64, 64),
-         (96, 32)]
 IN_CHANNELS = 7           # 6 tensor components + linear profile (padded to 16)
 HEAD_C = 32
+CHANS = (32, 64, 128)
+
+
+def conv_layers(chans=CHANS):
+    """(cin, cout) of the 3x3x3 convolutions in order (input padded to 16)."""
+    L = len(chans) - 1
+    layers = [(16, chans[0]), (chans[0], chans[0])]
+    for i in range(1, L + 1):
+        layers += [(chans[i - 1], chans[i]), (chans[i], chans[i])]
+    for i in range(L - 1, -1, -1):
+        layers += [(chans[i + 1] + chans[i], chans[i]), (chans[i], chans[i])]
+    return layers
 
 
 def _torch():
@@ -53,13 +65,19 @@ class WarmNet:
     """Parameters and optimiser state on the GPU; forward and backward passes
     over a batch of n cells of d x h x w (all multiples of 4)."""
 
-    def __init__(self, seed: int = 0, device: int = 0):
+    def __init__(self, seed: int = 0, device: int = 0, chans=CHANS, train_height: int = 64):
         torch = _torch()
         self.torch = torch
+        # cell height (along z) of the training cells: the correction to the
+        # linear profile scales with the wall-to-wall gradient, so predictions
+        # for a cell of height d are rescaled by train_height / d
+        self.train_height = int(train_height)
         self.dev = torch.device("cuda", device)
+        self.chans = tuple(chans)
+        self.layers = conv_layers(self.chans)
         g = np.random.default_rng(seed)
         self.W, self.Wb, self.b = [], [], []
-        for cin, cout in CONV3:
+        for cin, cout in self.layers:
             fan_in = 27 * (IN_CHANNELS if cin == 16 else cin)
             w = np.zeros((27, cin, cout), np.float32)
             live = IN_CHANNELS if cin == 16 else cin
@@ -83,8 +101,8 @@ class WarmNet:
     def set_reference_params(self, params):
         """Loads weights given as [(w [cout, cin, 3, 3, 3], b), ..., head]."""
         torch = self.torch
-        for l, (w, b) in enumerate(params[: len(CONV3)]):
-            cin_pad, cout = CONV3[l]
+        for l, (w, b) in enumerate(params[: len(self.layers)]):
+            cin_pad, cout = self.layers[l]
             wt = np.zeros((27, cin_pad, cout), np.float32)
             wt[:, : w.shape[1], :] = np.transpose(np.asarray(w).reshape(cout, w.shape[1], 27), (2, 1, 0))
             self.W[l].copy_(torch.from_numpy(wt))
@@ -96,6 +114,8 @@ class WarmNet:
 
     def save(self, path: str):
         arrs = {f"W{l}": w.cpu().numpy() for l, w in enumerate(self.W)}
+        arrs["chans"] = np.array(self.chans)
+        arrs["train_height"] = np.array(self.train_height)
         arrs.update({f"b{l}": b.cpu().numpy() for l, b in enumerate(self.b)})
         arrs["hw"] = self.hw.cpu().numpy()
         arrs["hb"] = self.hb.cpu().numpy()
@@ -104,7 +124,11 @@ class WarmNet:
     def load(self, path: str):
         torch = self.torch
         z = np.load(path)
-        for l in range(len(CONV3)):
+        if "chans" in z and tuple(int(c) for c in z["chans"]) != self.chans:
+            raise ValueError(f"weights are for channels {tuple(z['chans'])}, not {self.chans}")
+        if "train_height" in z:
+            self.train_height = int(z["train_height"])
+        for l in range(len(self.layers)):
             self.W[l].copy_(torch.from_numpy(z[f"W{l}"]))
             self.b[l].copy_(torch.from_numpy(z[f"b{l}"]))
         self.hw.copy_(torch.from_numpy(z["hw"]))
@@ -123,7 +147,7 @@ class WarmNet:
     def _conv(self, l, x, vol, relu=True):
         torch = self.torch
         n, d, h, w = vol
-        cin, cout = CONV3[l]
+        cin, cout = self.layers[l]
         y = torch.empty((n * d * h * w, cout), dtype=torch.bfloat16, device=self.dev)
         self._ok(lbm.lbm_nn_conv3d(x.data_ptr(), cin, self.Wb[l].data_ptr(), self.b[l].data_ptr(),
                                    y.data_ptr(), cout, n, d, h, w, 3, int(relu), 0, self._stream()),
@@ -153,35 +177,43 @@ class WarmNet:
                                    self._stream()), "concat")
         return y
 
+    def _vols(self, vol):
+        n, d, h, w = vol
+        return [(n, d >> i, h >> i, w >> i) for i in range(len(self.chans))]
+
     def forward(self, x0, vol, t_lin, target=None):
         """x0 [V, 16] BF16 input, t_lin [V] FP32; returns pred [V] FP32 (and
         keeps the activations for backward).  With a target, also the loss
         and the head's gradients."""
         torch = self.torch
         n, d, h, w = vol
-        v2 = (n, d // 2, h // 2, w // 2)
-        v4 = (n, d // 4, h // 4, w // 4)
+        L = len(self.chans) - 1
+        if d % (1 << L) or h % (1 << L) or w % (1 << L):
+            raise ValueError(f"cell sizes must be multiples of {1 << L}")
+        vols = self._vols(vol)
         A = {"x0": x0}
-        A["a1"] = self._conv(0, x0, vol)
-        A["s1"] = self._conv(1, A["a1"], vol)
-        A["p1"] = self._pool(A["s1"], 32, vol)
-        A["a3"] = self._conv(2, A["p1"], v2)
-        A["s2"] = self._conv(3, A["a3"], v2)
-        A["p2"] = self._pool(A["s2"], 64, v2)
-        A["a5"] = self._conv(4, A["p2"], v4)
-        A["a6"] = self._conv(5, A["a5"], v4)
-        A["u1"] = self._up(A["a6"], 128, v2)
-        A["c1"] = self._cat(A["u1"], 128, A["s2"], 64)
-        A["a7"] = self._conv(6, A["c1"], v2)
-        A["a8"] = self._conv(7, A["a7"], v2)
-        A["u2"] = self._up(A["a8"], 64, vol)
-        A["c2"] = self._cat(A["u2"], 64, A["s1"], 32)
-        A["a9"] = self._conv(8, A["c2"], vol)
+        k = 0
+        hcur = x0
+        for i in range(L + 1):
+            if i > 0:
+                hcur = self._pool(hcur, self.chans[i - 1], vols[i - 1])
+                A[f"p{i}"] = hcur
+            A[f"e{i}a"] = self._conv(k, hcur, vols[i]); k += 1
+            A[f"e{i}b"] = self._conv(k, A[f"e{i}a"], vols[i]); k += 1
+            hcur = A[f"e{i}b"]
+        for i in range(L - 1, -1, -1):
+            up = self._up(hcur, self.chans[i + 1], vols[i])
+            A[f"c{i}"] = self._cat(up, self.chans[i + 1], A[f"e{i}b"], self.chans[i])
+            A[f"d{i}a"] = self._conv(k, A[f"c{i}"], vols[i]); k += 1
+            A[f"d{i}b"] = self._conv(k, A[f"d{i}a"], vols[i]); k += 1
+            hcur = A[f"d{i}b"]
+        A["last"] = hcur
+        n, d, h, w = vol
         V = n * d * h * w
         pred = torch.empty(V, dtype=torch.float32, device=self.dev)
         self.vol, self.A = vol, A
         if target is None:
-            self._ok(lbm.lbm_nn_head(A["a9"].data_ptr(), self.hw.data_ptr(), self.hb.data_ptr(),
+            self._ok(lbm.lbm_nn_head(A["last"].data_ptr(), self.hw.data_ptr(), self.hb.data_ptr(),
                                      t_lin.data_ptr(), None, pred.data_ptr(), None, None, None,
                                      None, V, self._stream()), "head")
             return pred, None
@@ -189,7 +221,7 @@ class WarmNet:
         self.g_hb = torch.zeros_like(self.hb)
         loss = torch.zeros(1, dtype=torch.float64, device=self.dev)
         self.dh9 = torch.empty((V, HEAD_C), dtype=torch.bfloat16, device=self.dev)
-        self._ok(lbm.lbm_nn_head(A["a9"].data_ptr(), self.hw.data_ptr(), self.hb.data_ptr(),
+        self._ok(lbm.lbm_nn_head(A["last"].data_ptr(), self.hw.data_ptr(), self.hb.data_ptr(),
                                  t_lin.data_ptr(), target.data_ptr(), pred.data_ptr(),
                                  self.dh9.data_ptr(), self.g_hw.data_ptr(), self.g_hb.data_ptr(),
                                  loss.data_ptr(), V, self._stream()), "head")
@@ -199,7 +231,7 @@ class WarmNet:
         """Weight, bias and (optionally) input gradients of conv layer l."""
         torch = self.torch
         n, d, h, w = vol
-        cin, cout = CONV3[l]
+        cin, cout = self.layers[l]
         V = n * d * h * w
         self.gW[l].zero_()
         self.gb[l].zero_()
@@ -235,50 +267,51 @@ class WarmNet:
         """Gradients of the loss of the last forward into gW, gb, g_hw, g_hb."""
         torch = self.torch
         A, vol = self.A, self.vol
-        n, d, h, w = vol
-        v2 = (n, d // 2, h // 2, w // 2)
-        v4 = (n, d // 4, h // 4, w // 4)
-        if not hasattr(self, "gW"):
+        L = len(self.chans) - 1
+        vols = self._vols(vol)
+        C = self.chans
+        if not hasattr(self, "gW") or len(self.gW) != len(self.W):
             self.gW = [torch.zeros_like(x) for x in self.W]
             self.gb = [torch.zeros_like(x) for x in self.b]
-        g9 = self._mask(self.dh9, A["a9"])
-        dc2 = self._back_conv(8, g9, A["c2"], vol)
-        du2 = self._slice(dc2, 96, 0, 64)
-        ds1_cat = self._slice(dc2, 96, 64, 32)
         s = self._stream()
-        da8 = torch.empty((A["a8"].shape[0], 64), dtype=torch.bfloat16, device=self.dev)
-        self._ok(lbm.lbm_nn_pool2(du2.data_ptr(), da8.data_ptr(), 64, n, d, h, w, 1.0, s), "up bwd")
-        g8 = self._mask(da8, A["a8"])
-        da7 = self._back_conv(7, g8, A["a7"], v2)
-        g7 = self._mask(da7, A["a7"])
-        dc1 = self._back_conv(6, g7, A["c1"], v2)
-        du1 = self._slice(dc1, 192, 0, 128)
-        ds2 = self._slice(dc1, 192, 128, 64)
-        da6 = torch.empty((A["a6"].shape[0], 128), dtype=torch.bfloat16, device=self.dev)
-        self._ok(lbm.lbm_nn_pool2(du1.data_ptr(), da6.data_ptr(), 128, *v2, 1.0, s), "up bwd")
-        g6 = self._mask(da6, A["a6"])
-        da5 = self._back_conv(5, g6, A["a5"], v4)
-        g5 = self._mask(da5, A["a5"])
-        dp2 = self._back_conv(4, g5, A["p2"], v4)
-        dp2u = self._up(dp2, 64, v2, 0.125)
-        self._slice(dp2u, 64, 0, 64, dst=ds2)
-        g4 = self._mask(ds2, A["s2"])
-        da3 = self._back_conv(3, g4, A["a3"], v2)
-        g3 = self._mask(da3, A["a3"])
-        dp1 = self._back_conv(2, g3, A["p1"], v2)
-        dp1u = self._up(dp1, 32, vol, 0.125)
-        self._slice(dp1u, 32, 0, 32, dst=ds1_cat)
-        g2 = self._mask(ds1_cat, A["s1"])
-        da1 = self._back_conv(1, g2, A["a1"], vol)
-        g1 = self._mask(da1, A["a1"])
-        self._back_conv(0, g1, A["x0"], vol, need_dx=False)
+        k = len(self.layers) - 1
+        skip_grad = [None] * (L + 1)
+        dy = self.dh9                  # gradient of the last decoder output
+        # decoder levels in reverse forward order: 0, 1, ..., L-1
+        for i in range(0, L):
+            g = self._mask(dy, A[f"d{i}b"])
+            dx = self._back_conv(k, g, A[f"d{i}a"], vols[i]); k -= 1
+            g = self._mask(dx, A[f"d{i}a"])
+            dc = self._back_conv(k, g, A[f"c{i}"], vols[i]); k -= 1
+            cu, cs = C[i + 1], C[i]
+            du = self._slice(dc, cu + cs, 0, cu)
+            skip_grad[i] = self._slice(dc, cu + cs, cu, cs)
+            n, d, h, w = vols[i]
+            dy = torch.empty((du.shape[0] // 8, cu), dtype=torch.bfloat16, device=self.dev)
+            self._ok(lbm.lbm_nn_pool2(du.data_ptr(), dy.data_ptr(), cu, n, d, h, w, 1.0, s),
+                     "upsample backward")
+            # dy is now the gradient of the decoder level i+1 output, or of
+            # the bottom encoder output when i + 1 == L
+        # encoder levels from the bottom up
+        for i in range(L, -1, -1):
+            if skip_grad[i] is not None:
+                self._slice(dy, C[i], 0, C[i], dst=skip_grad[i])   # skip_grad += dy
+                dy = skip_grad[i]
+            g = self._mask(dy, A[f"e{i}b"])
+            dx = self._back_conv(k, g, A[f"e{i}a"], vols[i]); k -= 1
+            g = self._mask(dx, A[f"e{i}a"])
+            x_in = A["x0"] if i == 0 else A[f"p{i}"]
+            dx = self._back_conv(k, g, x_in, vols[i], need_dx=i > 0); k -= 1
+            if i > 0:
+                # backward of the average pool: spread / 8 to the children
+                dy = self._up(dx, C[i - 1], vols[i - 1], 0.125)
 
     def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
         self.t += 1
         grads = self.gW + self.gb + [self.g_hw, self.g_hb]
         s = self._stream()
         for i, (p, g) in enumerate(zip(self.params, grads)):
-            pb = self.Wb[i].data_ptr() if i < len(CONV3) else None
+            pb = self.Wb[i].data_ptr() if i < len(self.layers) else None
             self._ok(lbm.lbm_nn_adam(p.data_ptr(), g.data_ptr(), self.m[i].data_ptr(),
                                      self.v[i].data_ptr(), pb, p.numel(), lr, beta1, beta2, eps,
                                      self.t, s), "adam")
@@ -304,12 +337,15 @@ class WarmNet:
                                       1, d, h, w, self._stream()), "input")
         return x0, tl
 
-    def predict(self, phase, lam, t_hot=1.0, t_cold=0.0) -> np.ndarray:
+    def predict(self, phase, lam, t_hot=1.0, t_cold=0.0, as_tensor=False):
         """Predicted temperature [d, h, w] of one cell (z = temperature axis)."""
         d, h, w = phase.shape
         x0, tl = self.make_input(phase[None], [lam], t_hot, t_cold)
         pred, _ = self.forward(x0, (1, d, h, w), tl)
-        return pred.view(d, h, w).cpu().numpy()
+        if d != self.train_height:
+            pred = tl + (pred - tl) * (self.train_height / d)
+        pred = pred.view(d, h, w)
+        return pred if as_tensor else pred.cpu().numpy()
 
 
 def generate_cells(seeds, n=64, g_range=(20.0, 45.0), phi_range=(0.30, 0.60), A=10.0, B=6.0,
@@ -357,3 +393,111 @@ def train(net: WarmNet, phases, lams, temps, epochs=10, batch=4, lr=1e-3, seed=0
         if log:
             log(f"epoch {ep}: mse {history[-1]:.3e}")
     return history
+
+
+def time_to_keff(history, k_ref, ms_per_iter, rel=1e-4):
+    """First iteration after which every later k_eff stays within rel of
+    k_ref, and its device time."""
+    err = np.abs(history[:, 1] / k_ref - 1.0)
+    bad = np.nonzero(err > rel)[0]
+    first = 0 if bad.size == 0 else int(bad[-1]) + 1
+    if first >= len(history):
+        return None, None
+    it = int(history[first, 0])
+    return it, it * ms_per_iter
+
+
+def evaluate(net, seeds, shape=(128, 128, 256), tol=1e-8, rel=1e-4, max_iters=3_000_000,
+             device=0):
+    """Held-out braided cells: plain FP32 from the linear profile against
+    the warm start (FP32 and BF16 storage).  Per cell: iterations and device
+    time to R_T <= tol and to k_eff within rel of the FP32 converged value,
+    and the inference time."""
+    import json
+    import time
+
+    torch = net.torch
+    nx, ny, nz = shape
+    rows = []
+    for s in seeds:
+        r = I.SplitMix64(10_000 + int(s))
+        g = 20.0 + 25.0 * r.uniform()
+        phi = 0.30 + 0.30 * r.uniform()
+        lam = I.braid_tensors(g)
+        S = lbm.Solver(nx, ny, nz, device)
+        S.set_geometry_braid(math.radians(g), I.braid_anchors(nx, ny, int(s), n_max=512), phi)
+        S.set_tensors(lam)
+        ph = S.geometry()
+        out = {"seed": int(s), "g_deg": g, "phi": phi}
+        base = S.solve(2, 0, S.opts(tol=tol, max_iters=max_iters))
+        hb = S.history()
+        k_ref = base.k_eff
+        ms_it = base.elapsed_ms / base.iters
+        out["linear_f32"] = {"iters": int(base.iters), "ms": base.elapsed_ms,
+                             "keff_iters": time_to_keff(hb, k_ref, ms_it, rel)[0],
+                             "keff_ms": time_to_keff(hb, k_ref, ms_it, rel)[1], "k_eff": k_ref}
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        T0 = net.predict(ph, lam, as_tensor=True)
+        e1.record()
+        torch.cuda.synchronize()
+        out["inference_ms"] = e0.elapsed_time(e1)
+        T0h = np.ascontiguousarray(T0.cpu().numpy(), dtype=np.float32)
+        for name, storage in (("warm_f32", lbm.LBM_STORE_F32), ("warm_bf16", lbm.LBM_STORE_BF16)):
+            o = S.opts(tol=tol if storage == lbm.LBM_STORE_F32 else 0.0,
+                       max_iters=max_iters if storage == lbm.LBM_STORE_F32 else base.iters,
+                       storage=storage)
+            o.t_init = T0h.ctypes.data_as(lbm.ctypes.POINTER(lbm.ctypes.c_float))
+            info = S.solve(2, 0, o)
+            h = S.history()
+            ms = info.elapsed_ms / info.iters
+            ki, kms = time_to_keff(h, k_ref, ms, rel)
+            out[name] = {"iters": int(info.iters), "ms": info.elapsed_ms, "keff_iters": ki,
+                         "keff_ms": kms, "k_eff": info.k_eff,
+                         "k_rel_vs_linear": info.k_eff / k_ref - 1.0}
+        S.close()
+        rows.append(out)
+        print(json.dumps(out), flush=True)
+    return rows
+
+
+def main(argv=None):
+    import argparse
+    import json
+    import time
+
+    ap = argparse.ArgumentParser(description="train / evaluate the learned warm start")
+    ap.add_argument("--train-cells", type=int, default=2000)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--chans", default="32,64,128")
+    ap.add_argument("--eval-cells", type=int, default=10)
+    ap.add_argument("--eval-shape", default="128,128,256")
+    ap.add_argument("--weights", default=None, help="load instead of training")
+    ap.add_argument("--out", default=None, help="save the trained weights here")
+    a = ap.parse_args(argv)
+    chans = tuple(int(c) for c in a.chans.split(","))
+    net = WarmNet(seed=0, chans=chans)
+    summary = {"chans": chans}
+    if a.weights:
+        net.load(a.weights)
+    else:
+        t0 = time.time()
+        ph, lams, temps, _ = generate_cells(range(a.train_cells), n=64)
+        t1 = time.time()
+        hist = train(net, ph, lams, temps, epochs=a.epochs, lr=a.lr,
+                     log=lambda m: print(m, flush=True))
+        t2 = time.time()
+        summary.update(train_cells=a.train_cells, epochs=a.epochs, data_s=t1 - t0,
+                       train_s=t2 - t1, mse_first=hist[0], mse_last=hist[-1])
+        if a.out:
+            net.save(a.out)
+    shape = tuple(int(c) for c in a.eval_shape.split(","))
+    rows = evaluate(net, range(5000, 5000 + a.eval_cells), shape=shape)
+    summary["eval"] = rows
+    print(json.dumps(summary))
+
+
+if __name__ == "__main__":
+    main()
