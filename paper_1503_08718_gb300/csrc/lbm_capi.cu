@@ -259,6 +259,44 @@ cudaError_t launch_step(const lbm_ctx* c, int src, bool check, Frame fr, cudaStr
     return cudaGetLastError();
 }
 
+// Two plain FP32 steps in one launch (temporal blocking), when the layout
+// allows it.
+bool fusable(const lbm_ctx* c) {
+    return c->opts.fuse && c->fmt == LBM_STORE_F32 && c->L.NX % lbm::FX == 0 &&
+           c->L.NY % lbm::FY == 0;
+}
+
+cudaError_t launch_pair(const lbm_ctx* c, int src, Frame fr, cudaStream_t st) {
+    const lbm::StepArgs a = step_args(c, src, fr);
+    const int bxy = (c->L.NX / lbm::FX) * (c->L.NY / lbm::FY);
+    int nzc = (152 * 8 + bxy - 1) / bxy;                 // ~8 blocks per SM in flight
+    if (nzc > c->L.NZ) nzc = c->L.NZ;
+    int zchunk = (c->L.NZ + nzc - 1) / nzc;
+    if (zchunk < 4) zchunk = 4;
+    const dim3 grid(c->L.NX / lbm::FX, c->L.NY / lbm::FY, (c->L.NZ + zchunk - 1) / zchunk);
+    const size_t smem = sizeof(float4) * 2 * c->n_phases;
+    if (c->lateral == LBM_LATERAL_PERIODIC)
+        lbm::fused2_kernel<true><<<grid, lbm::FX * lbm::FY, smem, st>>>(a, zchunk);
+    else
+        lbm::fused2_kernel<false><<<grid, lbm::FX * lbm::FY, smem, st>>>(a, zchunk);
+    return cudaGetLastError();
+}
+
+// The launches of one check interval of K steps: a single step moving the
+// state to frame R_b, plain steps (fused in an even number of pairs, so
+// the interval ends in the buffer it started from), and the check step.
+struct Plan {
+    int pairs, singles;                  // plain steps after the first one
+};
+
+Plan interval_plan(const lbm_ctx* c) {
+    const int R = c->opts.check_every - 2;
+    Plan p;
+    p.pairs = fusable(c) ? 2 * (R / 4) : 0;
+    p.singles = R - 2 * p.pairs;
+    return p;
+}
+
 // The closing of a graph or host-loop interval: the first step moved the
 // state to frame R_b, and the check closes K iterations.
 Closing interval_closing(const lbm_ctx* c) {
@@ -313,7 +351,7 @@ std::vector<char> graph_signature(const lbm_ctx* c, int parity) {
     const lbm::StepArgs a = step_args(c, parity, kAB, interval_closing(c));
     std::vector<char> sig(sizeof a + 3 * sizeof(int));
     std::memcpy(sig.data(), &a, sizeof a);
-    const int extra[3] = {c->lateral, c->opts.check_every, c->fmt};
+    const int extra[3] = {c->lateral, c->opts.check_every, c->fmt * 2 + (fusable(c) ? 1 : 0)};
     std::memcpy(sig.data() + sizeof a, extra, sizeof extra);
     return sig;
 }
@@ -351,9 +389,23 @@ lbm_status build_graph(lbm_ctx* c, int parity) {
         Closing cl = interval_closing(c);
         cl.handle = h;
         cl.use_handle = 1;
-        for (int k = 0; k < K && e == cudaSuccess; ++k) {
+        const Plan pl = interval_plan(c);
+        int k = 0;
+        cl.rseed = (unsigned)k++;
+        e = launch_step(c, src, false, kAB, c->cap_stream, cl);
+        src ^= 1;
+        for (int i = 0; i < pl.pairs && e == cudaSuccess; ++i, k += 2) {
+            e = launch_pair(c, src, kBB, c->cap_stream);
+            src ^= 1;
+        }
+        for (int i = 0; i < pl.singles && e == cudaSuccess; ++i) {
+            cl.rseed = (unsigned)k++;
+            e = launch_step(c, src, false, kBB, c->cap_stream, cl);
+            src ^= 1;
+        }
+        if (e == cudaSuccess) {
             cl.rseed = (unsigned)k;
-            e = launch_step(c, src, k == K - 1, k == 0 ? kAB : kBB, c->cap_stream, cl);
+            e = launch_step(c, src, true, kBB, c->cap_stream, cl);
             src ^= 1;
         }
         cudaGraph_t captured = nullptr;
@@ -389,6 +441,7 @@ void lbm_default_opts(lbm_solve_opts* o) {
     o->check_every = 100;
     o->stall_checks = 0;
     o->storage = LBM_STORE_F32;
+    o->fuse = 1;
     o->t_init = nullptr;
     o->stream = nullptr;
 }
@@ -636,7 +689,14 @@ lbm_status lbm_advance(lbm_ctx* c, int64_t n_steps) {
     if (n_steps < 0) return fail(c, LBM_ERR_INVALID_ARG, "n_steps must be >= 0");
     if (n_steps == 0) return LBM_OK;
     CUDA_TRY(c, cudaSetDevice(c->device));
-    for (int64_t k = 0; k < n_steps; ++k) {
+    int64_t k = 0;
+    if (fusable(c)) {
+        for (; k + 2 <= n_steps; k += 2) {
+            CUDA_TRY(c, launch_pair(c, c->cur, kAA, c->stream));
+            c->cur ^= 1;
+        }
+    }
+    for (; k < n_steps; ++k) {
         Closing cl;
         cl.rseed = 0x10000u + (unsigned)k;
         CUDA_TRY(c, launch_step(c, c->cur, false, kAA, c->stream, cl));
@@ -683,12 +743,24 @@ lbm_status lbm_run(lbm_ctx* c, lbm_solve_info* info) {
         // the same interval, launched kernel by kernel; the stop flag is read
         // back after every interval
         do {
-            for (int k = 0; k < K; ++k) {
-                Closing cl = interval_closing(c);
-                cl.rseed = (unsigned)k;
-                CUDA_TRY(c, launch_step(c, c->cur, k == K - 1, k == 0 ? kAB : kBB, c->stream, cl));
+            const Plan pl = interval_plan(c);
+            Closing cl = interval_closing(c);
+            int k = 0;
+            cl.rseed = (unsigned)k++;
+            CUDA_TRY(c, launch_step(c, c->cur, false, kAB, c->stream, cl));
+            c->cur ^= 1;
+            for (int i = 0; i < pl.pairs; ++i, k += 2) {
+                CUDA_TRY(c, launch_pair(c, c->cur, kBB, c->stream));
                 c->cur ^= 1;
             }
+            for (int i = 0; i < pl.singles; ++i) {
+                cl.rseed = (unsigned)k++;
+                CUDA_TRY(c, launch_step(c, c->cur, false, kBB, c->stream, cl));
+                c->cur ^= 1;
+            }
+            cl.rseed = (unsigned)k;
+            CUDA_TRY(c, launch_step(c, c->cur, true, kBB, c->stream, cl));
+            c->cur ^= 1;
             CUDA_TRY(c, cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost,
                                         c->stream));
             CUDA_TRY(c, cudaStreamSynchronize(c->stream));

@@ -236,6 +236,62 @@ __device__ void close_plane(const StepArgs& a, int z) {
     }
 }
 
+// The collision of one node (Eq. 5, 8-13 in the reduced form above) from its
+// seven pulled values relative to R_src, with the frame constants kT, kJ;
+// returns the seven post-collision values relative to R_dst, and th = T - R_dst,
+// j_z and sigma_z for the flux.  Every step kernel uses this one function.
+struct Collided {
+    float o[7];
+    float th, jz, sz;
+};
+
+__device__ __forceinline__ Collided collide_node(float g0, float g1, float g2, float g3, float g4,
+                                                 float g5, float g6, float4 sa, float4 sc, float kT,
+                                                 float kJ) {
+    Collided c;
+    // T - R_dst(z) (Eq. 14) and the flux moment j, with the frame constants
+    c.th = (((g0 + g1) + (g2 + g3)) + ((g4 + g5) + g6)) + kT;
+    const float jx = g1 - g2, jy = g3 - g4, jz = (g5 - g6) + kJ;
+    // sigma = S_b j with S_b symmetric: (xx, yy, zz, yz) = sa, (xz, xy) = sc.xy
+    const float sx = fmaf(sa.x, jx, fmaf(sc.y, jy, sc.x * jz));
+    const float sy = fmaf(sc.y, jx, fmaf(sa.y, jy, sa.w * jz));
+    const float sz = fmaf(sc.x, jx, fmaf(sa.w, jy, sa.z * jz));
+    const float hx = jx - sx, hy = jy - sy, hz = jz - sz;
+    const float t8 = 0.125f * c.th;
+    c.o[0] = 0.25f * c.th;
+    c.o[1] = fmaf(0.5f, hx, t8);
+    c.o[2] = fmaf(-0.5f, hx, t8);
+    c.o[3] = fmaf(0.5f, hy, t8);
+    c.o[4] = fmaf(-0.5f, hy, t8);
+    c.o[5] = fmaf(0.5f, hz, t8);
+    c.o[6] = fmaf(-0.5f, hz, t8);
+    c.jz = jz;
+    c.sz = sz;
+    return c;
+}
+
+// Frame constants of plane z for a step from frame R_src to R_dst (see the
+// step kernel): kT is added to the sum of the pulled values, kJ to j_z.
+struct PlaneK {
+    float kT, kJ;
+};
+
+__device__ __forceinline__ PlaneK plane_consts(const float* rsrc, const float* rdst, int z, int nz,
+                                               float eps_hot, float eps_cold) {
+    const float w = 0.125f;
+    const bool zlo = z == 0, zhi = z == nz - 1;
+    const float r0 = rsrc[z], rd = rdst[z];
+    const float rm = zlo ? r0 : rsrc[z - 1];
+    const float rp = zhi ? r0 : rsrc[z + 1];
+    const float k_in = w * (r0 - rd);
+    const float k5 = zlo ? (eps_hot - w * r0) - w * rd : w * (rm - rd);
+    const float k6 = zhi ? (eps_cold - w * r0) - w * rd : w * (rp - rd);
+    PlaneK k;
+    k.kT = (2.f * k_in + 4.f * k_in) + (k5 + k6);
+    k.kJ = k5 - k6;
+    return k;
+}
+
 // Storage policies.  FP32 moves 4 voxels per thread as one float4 per
 // population; BF16 and FP16 move 8 voxels per thread as one uint4 (eight
 // 16-bit values) per population, converted to FP32 for the collision and
@@ -370,16 +426,9 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
     }
     // Frame changes (all exact): a population pulled from plane z' carries
     // w_i R_src(z'); it is re-expressed relative to R_dst(z) of this node.
-    const float w = 0.125f;
-    const float r0 = a.rsrc[z], rd = a.rdst[z];
-    const float rm = zlo ? r0 : a.rsrc[z - 1];
-    const float rp = zhi ? r0 : a.rsrc[z + 1];
-    const float k_in = w * (r0 - rd);
-    // walls (Eq. 23): f_in = -fhat_out(x) + eps T_wall, fhat_out = g + w R_src(z)
-    const float k5 = zlo ? (a.eps_hot - w * r0) - w * rd : w * (rm - rd);
-    const float k6 = zhi ? (a.eps_cold - w * r0) - w * rd : w * (rp - rd);
-    const float kT = (2.f * k_in + 4.f * k_in) + (k5 + k6);   // sum of w_i (...) with w_0 = 2w
-    const float kJ = k5 - k6;
+    const PlaneK pk = plane_consts(a.rsrc, a.rdst, z, a.nz, a.eps_hot, a.eps_cold);
+    const float kT = pk.kT, kJ = pk.kJ;
+    const float rd = a.rdst[z];
     if (zlo) c5 = S::neg(c5);
     if (zhi) c6 = S::neg(c6);
     // x-neighbours: f1 comes from x - 1, f2 from x + 1.
@@ -428,23 +477,11 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
         const int p = (k < 4 ? (ph.x >> (8 * k)) : (ph.y >> (8 * (k - 4)))) & 0xff;
         const float4 sa = s_sb[2 * p];
         const float4 sc = s_sb[2 * p + 1];
-        // T - R_dst(z) (Eq. 14) and the flux moment j, with the frame constants
-        const float th = (((g0 + g1) + (g2 + g3)) + ((g4 + g5) + g6)) + kT;
-        const float jx = g1 - g2, jy = g3 - g4, jz = (g5 - g6) + kJ;
-        // sigma = S_b j with S_b symmetric: (xx, yy, zz, yz) = sa, (xz, xy) = sc.xy
-        const float sx = fmaf(sa.x, jx, fmaf(sc.y, jy, sc.x * jz));
-        const float sy = fmaf(sc.y, jx, fmaf(sa.y, jy, sa.w * jz));
-        const float sz = fmaf(sc.x, jx, fmaf(sa.w, jy, sa.z * jz));
-        const float hx = jx - sx, hy = jy - sy, hz = jz - sz;
-        const float t8 = 0.125f * th;
+        const Collided cc = collide_node(g0, g1, g2, g3, g4, g5, g6, sa, sc, kT, kJ);
+        const float th = cc.th, jz = cc.jz, sz = cc.sz;
         const bool real = RAGGED ? k < n_real : active;   // n_real is 0 for inactive threads
-        o[0][k] = 0.25f * th;
-        o[1][k] = fmaf(0.5f, hx, t8);
-        o[2][k] = fmaf(-0.5f, hx, t8);
-        o[3][k] = fmaf(0.5f, hy, t8);
-        o[4][k] = fmaf(-0.5f, hy, t8);
-        o[5][k] = fmaf(0.5f, hz, t8);
-        o[6][k] = fmaf(-0.5f, hz, t8);
+#pragma unroll
+        for (int i = 0; i < 7; ++i) o[i][k] = cc.o[i];
         if (CHECK) {
             const float tdev = th + dref;                    // T - T_ref
             thv[k] = tdev;
@@ -522,6 +559,102 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
         }
         __syncthreads();
         if (s_last) close_plane<THREADS>(a, z);
+    }
+}
+
+// Two fused steps (temporal blocking) in FP32: step n for a tile of
+// FX x FY nodes plus a one-node x/y halo, kept in a ring of three planes in
+// shared memory, then step n+1 for the tile from that ring.  The block
+// marches up a chunk of planes; each iteration computes step n for the plane
+// above and step n+1 for the current plane.  Each node's arithmetic is the
+// single step's (collide_node), so two fused steps equal two single steps
+// bit for bit; only the intermediate state never reaches global memory
+// (DRAM traffic per pair of steps: one read and one write of the state).
+// Requires FP32 storage, nx % FX == 0 and ny % FY == 0.  Step n runs from
+// frame rsrc to rdst, step n+1 within rdst.
+constexpr int FX = 32, FY = 8;
+constexpr int FR = (FX + 2) * (FY + 2);     // halo'd tile
+
+template <bool PERIODIC>
+__global__ void __launch_bounds__(FX * FY) fused2_kernel(const StepArgs a, int zchunk) {
+    extern __shared__ float4 s_sb[];
+    __shared__ float ring[3][7][FR];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 2 * a.n_phases; i += FX * FY) s_sb[i] = a.sb[i];
+
+    const int x0 = blockIdx.x * FX, y0 = blockIdx.y * FY;
+    const int z0 = blockIdx.z * zchunk;
+    const int z1 = min(z0 + zchunk, a.nz);
+    const long long P = a.pstride;
+    const float* __restrict__ src = reinterpret_cast<const float*>(a.src);
+    float* __restrict__ dst = reinterpret_cast<float*>(a.dst);
+    const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch;
+    __syncthreads();
+
+    // step n of one node of the halo'd tile (entry e) at plane p, into the ring
+    auto first_step = [&](int e, int p) {
+        const int lx = e % (FX + 2), ly = e / (FX + 2);
+        int x = x0 - 1 + lx, y = y0 - 1 + ly;
+        if (PERIODIC) {
+            x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+            y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+        } else if (x < 0 || x >= nx || y < 0 || y >= ny) {
+            return;                         // outside an adiabatic cell: never read
+        }
+        const long long row = ((long long)p * ny + y) * pitch;
+        const long long v = row + x;
+        const float g0 = src[v];
+        float g1, g2, g3, g4, g5, g6;
+        if (x > 0) g1 = src[P + v - 1];
+        else g1 = PERIODIC ? src[P + row + nx - 1] : src[2 * P + v];
+        if (x < nx - 1) g2 = src[2 * P + v + 1];
+        else g2 = PERIODIC ? src[2 * P + row] : src[P + v];
+        if (y > 0) g3 = src[3 * P + v - pitch];
+        else g3 = PERIODIC ? src[3 * P + v + (long long)(ny - 1) * pitch] : src[4 * P + v];
+        if (y < ny - 1) g4 = src[4 * P + v + pitch];
+        else g4 = PERIODIC ? src[4 * P + v - (long long)(ny - 1) * pitch] : src[3 * P + v];
+        const long long plane = (long long)ny * pitch;
+        g5 = p > 0 ? src[5 * P + v - plane] : -src[6 * P + v];
+        g6 = p < nz - 1 ? src[6 * P + v + plane] : -src[5 * P + v];
+        const PlaneK pk = plane_consts(a.rsrc, a.rdst, p, nz, a.eps_hot, a.eps_cold);
+        const int ph = a.phase[v];
+        const Collided c = collide_node(g0, g1, g2, g3, g4, g5, g6, s_sb[2 * ph], s_sb[2 * ph + 1],
+                                        pk.kT, pk.kJ);
+        float(*slot)[FR] = ring[p % 3];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) slot[i][e] = c.o[i];
+    };
+    auto first_plane = [&](int p) {
+        if (p < 0 || p >= nz) return;
+        for (int e = tid; e < FR; e += FX * FY) first_step(e, p);
+    };
+
+    first_plane(z0 - 1);
+    first_plane(z0);
+    const int tx = tid % FX, ty = tid / FX;
+    const int x = x0 + tx, y = y0 + ty;
+    const int e = (ty + 1) * (FX + 2) + (tx + 1);      // this node in the halo'd tile
+    for (int z = z0; z < z1; ++z) {
+        first_plane(z + 1);
+        __syncthreads();
+        // step n+1 at (x, y, z) from the ring (frame rdst -> rdst)
+        const float(*cur)[FR] = ring[z % 3];
+        const float g0 = cur[0][e];
+        float g1, g2, g3, g4, g5, g6;
+        g1 = (PERIODIC || x > 0) ? cur[1][e - 1] : cur[2][e];
+        g2 = (PERIODIC || x < nx - 1) ? cur[2][e + 1] : cur[1][e];
+        g3 = (PERIODIC || y > 0) ? cur[3][e - (FX + 2)] : cur[4][e];
+        g4 = (PERIODIC || y < ny - 1) ? cur[4][e + (FX + 2)] : cur[3][e];
+        g5 = z > 0 ? ring[(z + 2) % 3][5][e] : -cur[6][e];
+        g6 = z < nz - 1 ? ring[(z + 1) % 3][6][e] : -cur[5][e];
+        const PlaneK pk = plane_consts(a.rdst, a.rdst, z, nz, a.eps_hot, a.eps_cold);
+        const long long v = ((long long)z * ny + y) * pitch + x;
+        const int ph = a.phase[v];
+        const Collided c = collide_node(g0, g1, g2, g3, g4, g5, g6, s_sb[2 * ph], s_sb[2 * ph + 1],
+                                        pk.kT, pk.kJ);
+#pragma unroll
+        for (int i = 0; i < 7; ++i) dst[i * P + v] = c.o[i];
+        __syncthreads();                    // the ring slot of plane z-1 is reused next
     }
 }
 

@@ -42,6 +42,7 @@ class lbm_solve_opts(ctypes.Structure):
                 ("tol", ctypes.c_double), ("max_iters", ctypes.c_int64),
                 ("check_every", ctypes.c_int32), ("stall_checks", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("host_loop", ctypes.c_int32),
+                ("fuse", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("t_init", ctypes.POINTER(ctypes.c_float)), ("stream", ctypes.c_void_p)]
 
 

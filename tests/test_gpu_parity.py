@@ -322,3 +322,32 @@ def test_history_records_every_check():
     for row in h[:4]:
         ref.step(int(row[0]) - ref.iter)
         assert row[1] == pytest.approx(ref.k_eff()[0], rel=K_TOL)
+
+
+@pytest.mark.parametrize("lateral", [0, 1])
+@pytest.mark.parametrize("axis", [2, 0])
+def test_fused_pairs_equal_single_steps_bit_for_bit(lateral, axis):
+    """Two steps fused in one kernel (temporal blocking) do each node's
+    arithmetic exactly as two single steps: identical fields and k_eff,
+    through the graph loop and through lbm_advance."""
+    rng = np.random.default_rng(31 + lateral + axis)
+    lam = np.stack([I.random_spd(rng) for _ in range(3)])
+    shape = (64, 40, 24) if axis == 2 else (24, 64, 40)      # (nx, ny, nz) -> canonical 64 x 40
+    phase = I.random_phase(rng, *shape, 3)
+    out = []
+    for fuse in (1, 0):
+        S = lbm.Solver(*shape)
+        S.set_geometry(phase, 3)
+        S.set_tensors(lam)
+        info = S.solve(axis, lateral, S.opts(tol=0.0, max_iters=300, fuse=fuse))
+        T1 = S.temperature()
+        S.start(axis, lateral, S.opts(fuse=fuse))
+        S.advance(37)
+        T2 = S.temperature()
+        out.append((T1, info.k_eff, info.residual_T, T2))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1] and out[0][2] == out[1][2]
+    assert np.array_equal(out[0][3], out[1][3])
+    # and both follow the oracle
+    ref = _oracle(phase, lam, axis, lateral, info.lattice_scale, 300)
+    assert np.max(np.abs(out[0][0] - ref.temperature())) <= T_TOL
