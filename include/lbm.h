@@ -238,7 +238,8 @@ void lbm_batch_destroy(lbm_batch* b);
 /* y = act(bias + conv(x, w)): ksize 3 (27 taps, periodic in x and y, zero
  * outside in z) or 1.  x [V][cin] (cin a multiple of 16), w [taps][cin][cout]
  * (tap = (dz*3 + dy)*3 + dx), bias [cout] FP32 or NULL, y [V][cout] BF16, or
- * FP32 if out_f32 (cout a multiple of 32).  relu != 0 applies max(., 0).
+ * FP32 if out_f32 (cout a multiple of 32).  relu != 0 applies the leaky
+ * ReLU max(., 0) + 0.01 min(., 0).
  * Runs on the tensor cores (mma.sync m16n8k16, implicit GEMM). */
 lbm_status lbm_nn_conv3d(const void* x, int cin, const void* w, const float* bias, void* y, int cout,
                          int n, int d, int h, int wdt, int ksize, int relu, int out_f32,
@@ -256,7 +257,8 @@ lbm_status lbm_nn_flip_weights(const void* w, void* wf, int cin, int cout, int k
 /* db[c] += sum_v g[v][c] (c <= 1024). */
 lbm_status lbm_nn_bias_grad(const void* g, int c, long long nvox, float* db, void* stream);
 
-/* g = dy where y > 0, else 0 (backward of a fused ReLU whose output is y). */
+/* g = dy where y > 0, else 0.01 dy (backward of the fused leaky ReLU whose
+ * output is y). */
 lbm_status lbm_nn_relu_mask(const void* dy, const void* y, void* g, long long count, void* stream);
 
 /* y[parent] = scale * sum of the 8 children of x; (d, h, w) are x's sizes

@@ -17,7 +17,7 @@ path only through this docstring:
   conv1(32->1)                                          -> dT, T = T_lin + dT
 
 conv3: 3x3x3 cross-correlation with bias, periodic (circular) padding in x
-and y, zero padding in z.  avgpool2: mean of 2x2x2 blocks.  upsample2:
+and y, zero padding in z.  relu: leaky, slope 0.01 below zero.  avgpool2: mean of 2x2x2 blocks.  upsample2:
 nearest neighbour.  Loss: mean squared error of T over all voxels.
 
 Plain PyTorch CPU ops in float64; reverse-mode differentiation of those ops
@@ -77,14 +77,14 @@ def forward(params, x, chans=CHANS):
     for i in range(L + 1):
         if i > 0:
             h = F.avg_pool3d(h, 2)
-        h = F.relu(conv3(h, *p[k])); k += 1
-        h = F.relu(conv3(h, *p[k])); k += 1
+        h = F.leaky_relu(conv3(h, *p[k]), 0.01); k += 1
+        h = F.leaky_relu(conv3(h, *p[k]), 0.01); k += 1
         skips.append(h)
     for i in range(L - 1, -1, -1):
         h = F.interpolate(h, scale_factor=2, mode="nearest")
         h = torch.cat([h, skips[i]], dim=1)
-        h = F.relu(conv3(h, *p[k])); k += 1
-        h = F.relu(conv3(h, *p[k])); k += 1
+        h = F.leaky_relu(conv3(h, *p[k]), 0.01); k += 1
+        h = F.leaky_relu(conv3(h, *p[k]), 0.01); k += 1
     return F.conv3d(h, *p[k])
 
 

@@ -10,7 +10,8 @@
 //   conv: 3x3x3 (or 1x1x1) cross-correlation as an implicit GEMM
 //         M = voxels, N = output channels, K = taps x input channels, on the
 //         tensor cores with mma.sync m16n8k16 (BF16 in, FP32 accumulate);
-//         periodic padding in x and y, zero padding in z; bias and ReLU fused
+//         periodic padding in x and y, zero padding in z; bias and leaky ReLU
+//         (slope 0.01 below zero) fused
 //   wgrad: dW[tap][ci][co] = sum_v X[v + tap][ci] dY[v][co], the same tensor
 //         core tiles with the voxel axis as the reduction
 //   data gradient: the forward conv with flipped taps and swapped channels
@@ -71,6 +72,8 @@ __device__ __forceinline__ long long tap_src(const Vol& v, int n, int z, int y, 
 }
 
 constexpr int BM = 128;     // voxels per block (4 warps x 32)
+// leaky ReLU slope for negative inputs (a plain ReLU can die under Adam)
+constexpr float kLeak = 0.01f;
 constexpr int NT = 128;     // threads
 
 // Y[v][co] = act(bias[co] + sum_tap sum_ci X[src(v, tap)][ci] W[tap][ci][co])
@@ -157,8 +160,8 @@ __global__ void __launch_bounds__(NT) conv_fwd_kernel(const bf16* __restrict__ X
                 float y0 = acc[mt][nt][2 * half] + (bias ? bias[co] : 0.f);
                 float y1 = acc[mt][nt][2 * half + 1] + (bias ? bias[co + 1] : 0.f);
                 if (RELU) {
-                    y0 = fmaxf(y0, 0.f);
-                    y1 = fmaxf(y1, 0.f);
+                    y0 = y0 > 0.f ? y0 : kLeak * y0;
+                    y1 = y1 > 0.f ? y1 : kLeak * y1;
                 }
                 if (OUT_F32) {
                     float* Y = reinterpret_cast<float*>(Yv);
@@ -281,7 +284,7 @@ __global__ void relu_mask_kernel(const bf16* __restrict__ dY, const bf16* __rest
                                  bf16* __restrict__ G, long long count) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
          i += (long long)gridDim.x * blockDim.x)
-        G[i] = __bfloat162float(Y[i]) > 0.f ? dY[i] : __float2bfloat16(0.f);
+        G[i] = __bfloat162float(Y[i]) > 0.f ? dY[i] : __float2bfloat16(kLeak * __bfloat162float(dY[i]));
 }
 
 // out[parent][c] = scale * sum of the 8 children (input dims are the children's)

@@ -17,7 +17,8 @@ channels c_0 = 32, c_1, ..., c_L per level:
   encoder level i: [2x2x2 average pool if i > 0], conv3 -> c_i, conv3 c_i -> c_i
   decoder level i = L-1..0: nearest upsample, concat with encoder level i,
           conv3 (c_(i+1) + c_i) -> c_i, conv3 c_i -> c_i
-  head: conv1 32 -> 1, T = T_lin + out.   (All convs but the head use ReLU.)
+  head: conv1 32 -> 1, T = T_lin + out.   (All convs but the head use a
+  leaky ReLU, slope 0.01 below zero.)
 """
 from __future__ import annotations
 
@@ -371,8 +372,10 @@ def generate_cells(seeds, n=64, g_range=(20.0, 45.0), phi_range=(0.30, 0.60), A=
     return np.stack(phases), lams, temps, k
 
 
-def train(net: WarmNet, phases, lams, temps, epochs=10, batch=4, lr=1e-3, seed=0, log=None):
-    """Adam on the mean squared error of the predicted temperature."""
+def train(net: WarmNet, phases, lams, temps, epochs=10, batch=4, lr=5e-4, seed=0, log=None,
+          warmup=200):
+    """Adam on the mean squared error of the predicted temperature; the
+    learning rate ramps up linearly over the first `warmup` steps."""
     torch = net.torch
     rng = np.random.default_rng(seed)
     n = len(phases)
@@ -387,7 +390,7 @@ def train(net: WarmNet, phases, lams, temps, epochs=10, batch=4, lr=1e-3, seed=0
             tgt = torch.from_numpy(temps[idx].reshape(-1).astype(np.float32)).to(net.dev)
             _, loss = net.forward(x0, (len(idx), d, h, w), tl, tgt)
             net.backward()
-            net.adam_step(lr)
+            net.adam_step(lr * min(1.0, (net.t + 1) / warmup))
             tot += float(loss.item()) / (len(idx) * d * h * w)
         history.append(tot / max(1, n // batch))
         if log:
@@ -470,7 +473,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description="train / evaluate the learned warm start")
     ap.add_argument("--train-cells", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=30)
-    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr", type=float, default=5e-4)
     ap.add_argument("--chans", default="32,64,128")
     ap.add_argument("--eval-cells", type=int, default=10)
     ap.add_argument("--eval-shape", default="128,128,256")
