@@ -264,7 +264,7 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     iters = args.iters
     opts = S.opts(tol=0.0, max_iters=iters, check_every=K, host_loop=int(args.launch == "host"),
-                  storage=STORAGE[args.storage])
+                  storage=STORAGE[args.storage], fuse=int(args.fuse))
     opts.stream = int(stream.cuda_stream)
 
     def one_step():
@@ -299,7 +299,7 @@ def run_ours(args):
     # per check interval: the first step, fused pairs (FP32, the cell's 128 x
     # 128 rows allow them), the remaining single steps and the check step
     R = K - 2
-    pairs = 2 * (R // 4) if args.storage == "f32" else 0
+    pairs = 2 * (R // 4) if (args.storage == "f32" and args.fuse) else 0
     launches_per_interval = 2 + pairs + (R - 2 * pairs)
     launches_per_step = (iters // K) * launches_per_interval + 2   # + permute, init
     # roofline of the dominant kernel: the fused two-step kernel in FP32 (one
@@ -388,7 +388,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else f"f32 (storage {args.storage})",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "iters_per_step": iters, "check_every": K,
-                       "storage": args.storage,
+                       "storage": args.storage, "fuse": bool(args.fuse),
                        "launch": args.launch,
                        "yarns": used, "yarn_fraction": round(frac, 6),
                        "l2": "inputs larger than L2 (f buffers 2 x 117 MB)",
@@ -426,6 +426,8 @@ def main():
                          "host: the same kernels launched from the host (for profilers)")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
                     help="distribution storage (collision is FP32 in every mode)")
+    ap.add_argument("--fuse", action="store_true",
+                    help="run FP32 plain steps two at a time (temporal blocking)")
     ap.add_argument("--no-variants", action="store_true",
                     help="omit the BF16/FP16 storage variants of the step")
     ap.add_argument("--no-extras", action="store_true",

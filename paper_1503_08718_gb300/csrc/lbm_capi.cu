@@ -441,7 +441,7 @@ void lbm_default_opts(lbm_solve_opts* o) {
     o->check_every = 100;
     o->stall_checks = 0;
     o->storage = LBM_STORE_F32;
-    o->fuse = 1;
+    o->fuse = 0;
     o->t_init = nullptr;
     o->stream = nullptr;
 }
