@@ -269,16 +269,16 @@ bool fusable(const lbm_ctx* c) {
 cudaError_t launch_pair(const lbm_ctx* c, int src, Frame fr, cudaStream_t st) {
     const lbm::StepArgs a = step_args(c, src, fr);
     const int bxy = (c->L.NX / lbm::FX) * (c->L.NY / lbm::FY);
-    int nzc = (152 * 8 + bxy - 1) / bxy;                 // ~8 blocks per SM in flight
+    int nzc = (152 * 4 + bxy - 1) / bxy;                 // ~4 blocks per SM in flight
     if (nzc > c->L.NZ) nzc = c->L.NZ;
     int zchunk = (c->L.NZ + nzc - 1) / nzc;
     if (zchunk < 4) zchunk = 4;
     const dim3 grid(c->L.NX / lbm::FX, c->L.NY / lbm::FY, (c->L.NZ + zchunk - 1) / zchunk);
-    const size_t smem = sizeof(float4) * 2 * c->n_phases;
+    const size_t smem = lbm::fused2_smem_bytes(c->n_phases);
     if (c->lateral == LBM_LATERAL_PERIODIC)
-        lbm::fused2_kernel<true><<<grid, lbm::FX * lbm::FY, smem, st>>>(a, zchunk);
+        lbm::fused2_kernel<true><<<grid, lbm::FT, smem, st>>>(a, zchunk);
     else
-        lbm::fused2_kernel<false><<<grid, lbm::FX * lbm::FY, smem, st>>>(a, zchunk);
+        lbm::fused2_kernel<false><<<grid, lbm::FT, smem, st>>>(a, zchunk);
     return cudaGetLastError();
 }
 
@@ -472,7 +472,12 @@ lbm_status lbm_create(int nx, int ny, int nz, int cuda_device, lbm_ctx** out) {
               cudaMalloc((void**)&c->d_ctl, sizeof(Ctl)) == cudaSuccess &&
               cudaMalloc((void**)&c->d_hist, sizeof(double) * 4 * kHistCap) == cudaSuccess &&
               cudaMallocHost((void**)&c->h_ctl, sizeof(Ctl)) == cudaSuccess &&
-              cudaEventCreate(&c->ev0) == cudaSuccess && cudaEventCreate(&c->ev1) == cudaSuccess;
+              cudaEventCreate(&c->ev0) == cudaSuccess && cudaEventCreate(&c->ev1) == cudaSuccess &&
+              // the fused two-step kernel needs more than the default 48 KB
+              cudaFuncSetAttribute(lbm::fused2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)lbm::fused2_smem_bytes(255)) == cudaSuccess &&
+              cudaFuncSetAttribute(lbm::fused2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)lbm::fused2_smem_bytes(255)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         lbm_destroy(c);

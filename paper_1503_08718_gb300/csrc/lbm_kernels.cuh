@@ -562,25 +562,41 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
     }
 }
 
-// Two fused steps (temporal blocking) in FP32: step n for a tile of
-// FX x FY nodes plus a one-node x/y halo, kept in a ring of three planes in
-// shared memory, then step n+1 for the tile from that ring.  The block
-// marches up a chunk of planes; each iteration computes step n for the plane
-// above and step n+1 for the current plane.  Each node's arithmetic is the
-// single step's (collide_node), so two fused steps equal two single steps
-// bit for bit; only the intermediate state never reaches global memory
-// (DRAM traffic per pair of steps: one read and one write of the state).
-// Requires FP32 storage, nx % FX == 0 and ny % FY == 0.  Step n runs from
-// frame rsrc to rdst, step n+1 within rdst.
+// Two fused steps (temporal blocking) in FP32.  A block owns a tile of
+// FX x FY nodes and marches up a chunk of planes.  Per plane it keeps
+//   - the state of step n-1 (read from global memory) for the tile plus a
+//     halo of 2 rows and 4 columns (aligned float4 rows) in a ring of four
+//     planes; the next plane is prefetched into registers at the top of an
+//     iteration and stored at its end, so its global loads overlap the work;
+//   - the state after step n for the tile plus a one-node halo in a ring of
+//     three planes.
+// Each iteration computes step n for the plane above (tile + halo) and step
+// n+1 for the current plane (tile), which goes to global memory.  Each
+// node's arithmetic is the single step's (collide_node), so two fused steps
+// equal two single steps bit for bit; the intermediate state never reaches
+// global memory.  Requires FP32 storage, nx % FX == 0 and ny % FY == 0.
+// Step n runs from frame rsrc to rdst, step n+1 within rdst.
 constexpr int FX = 32, FY = 8;
-constexpr int FR = (FX + 2) * (FY + 2);     // halo'd tile
+constexpr int FT = FX * FY;                  // threads
+constexpr int RW = FX + 8, RH = FY + 4;      // raw plane: 4 + FX + 4 columns, 2 + FY + 2 rows
+constexpr int RP = RW * RH;                  // floats per population of a raw plane
+constexpr int NW = FX + 2, NH = FY + 2;      // step-n plane: tile + 1
+constexpr int NP = NW * NH;
+constexpr int RAW_ITEMS = 7 * RH * (RW / 4); // float4 per raw plane
+constexpr int RAW_PER_THREAD = (RAW_ITEMS + FT - 1) / FT;
+
+__host__ __device__ constexpr size_t fused2_smem_bytes(int n_phases) {
+    return sizeof(float) * (4 * 7 * RP + 3 * 7 * NP) + sizeof(float4) * 2 * n_phases;
+}
 
 template <bool PERIODIC>
-__global__ void __launch_bounds__(FX * FY) fused2_kernel(const StepArgs a, int zchunk) {
-    extern __shared__ float4 s_sb[];
-    __shared__ float ring[3][7][FR];
+__global__ void __launch_bounds__(FT, 2) fused2_kernel(const StepArgs a, int zchunk) {
+    extern __shared__ float4 smem4[];
+    float* raw = reinterpret_cast<float*>(smem4);              // [4][7][RH][RW]
+    float* fn = raw + 4 * 7 * RP;                              // [3][7][NH][NW]
+    float4* s_sb = reinterpret_cast<float4*>(fn + 3 * 7 * NP);
     const int tid = threadIdx.x;
-    for (int i = tid; i < 2 * a.n_phases; i += FX * FY) s_sb[i] = a.sb[i];
+    for (int i = tid; i < 2 * a.n_phases; i += FT) s_sb[i] = a.sb[i];
 
     const int x0 = blockIdx.x * FX, y0 = blockIdx.y * FY;
     const int z0 = blockIdx.z * zchunk;
@@ -589,64 +605,102 @@ __global__ void __launch_bounds__(FX * FY) fused2_kernel(const StepArgs a, int z
     const float* __restrict__ src = reinterpret_cast<const float*>(a.src);
     float* __restrict__ dst = reinterpret_cast<float*>(a.dst);
     const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch;
-    __syncthreads();
 
-    // step n of one node of the halo'd tile (entry e) at plane p, into the ring
-    auto first_step = [&](int e, int p) {
-        const int lx = e % (FX + 2), ly = e / (FX + 2);
-        int x = x0 - 1 + lx, y = y0 - 1 + ly;
-        if (PERIODIC) {
-            x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
-            y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-        } else if (x < 0 || x >= nx || y < 0 || y >= ny) {
-            return;                         // outside an adiabatic cell: never read
-        }
-        const long long row = ((long long)p * ny + y) * pitch;
-        const long long v = row + x;
-        const float g0 = src[v];
-        float g1, g2, g3, g4, g5, g6;
-        if (x > 0) g1 = src[P + v - 1];
-        else g1 = PERIODIC ? src[P + row + nx - 1] : src[2 * P + v];
-        if (x < nx - 1) g2 = src[2 * P + v + 1];
-        else g2 = PERIODIC ? src[2 * P + row] : src[P + v];
-        if (y > 0) g3 = src[3 * P + v - pitch];
-        else g3 = PERIODIC ? src[3 * P + v + (long long)(ny - 1) * pitch] : src[4 * P + v];
-        if (y < ny - 1) g4 = src[4 * P + v + pitch];
-        else g4 = PERIODIC ? src[4 * P + v - (long long)(ny - 1) * pitch] : src[3 * P + v];
-        const long long plane = (long long)ny * pitch;
-        g5 = p > 0 ? src[5 * P + v - plane] : -src[6 * P + v];
-        g6 = p < nz - 1 ? src[6 * P + v + plane] : -src[5 * P + v];
-        const PlaneK pk = plane_consts(a.rsrc, a.rdst, p, nz, a.eps_hot, a.eps_cold);
-        const int ph = a.phase[v];
-        const Collided c = collide_node(g0, g1, g2, g3, g4, g5, g6, s_sb[2 * ph], s_sb[2 * ph + 1],
-                                        pk.kT, pk.kJ);
-        float(*slot)[FR] = ring[p % 3];
+    // ---- raw plane staging: global -> registers -> shared ----
+    float4 pre[RAW_PER_THREAD];
+    auto fetch = [&](int p) {
 #pragma unroll
-        for (int i = 0; i < 7; ++i) slot[i][e] = c.o[i];
+        for (int k = 0; k < RAW_PER_THREAD; ++k) {
+            const int it = tid + k * FT;
+            pre[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (it >= RAW_ITEMS || p < 0 || p >= nz) continue;
+            const int q = it / (RH * (RW / 4));
+            const int rem = it - q * (RH * (RW / 4));
+            const int r = rem / (RW / 4), c = rem - r * (RW / 4);
+            int y = y0 - 2 + r, x = x0 - 4 + 4 * c;
+            if (PERIODIC) {
+                y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+                x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+            } else if (y < 0 || y >= ny || x < 0 || x >= nx) {
+                continue;                               // outside an adiabatic cell
+            }
+            pre[k] = __ldg(reinterpret_cast<const float4*>(src + q * P + ((long long)p * ny + y) * pitch + x));
+        }
     };
+    auto store = [&](int p) {
+        if (p < 0 || p >= nz) return;
+        float* slot = raw + (p & 3) * 7 * RP;
+#pragma unroll
+        for (int k = 0; k < RAW_PER_THREAD; ++k) {
+            const int it = tid + k * FT;
+            if (it >= RAW_ITEMS) continue;
+            const int q = it / (RH * (RW / 4));
+            const int rem = it - q * (RH * (RW / 4));
+            const int r = rem / (RW / 4), c = rem - r * (RW / 4);
+            *reinterpret_cast<float4*>(slot + q * RP + r * RW + 4 * c) = pre[k];
+        }
+    };
+    // ---- step n of the halo'd tile at plane p, from the raw ring ----
     auto first_plane = [&](int p) {
         if (p < 0 || p >= nz) return;
-        for (int e = tid; e < FR; e += FX * FY) first_step(e, p);
+        const float* R0 = raw + (p & 3) * 7 * RP;
+        const float* Rm = raw + ((p + 3) & 3) * 7 * RP;     // plane p-1
+        const float* Rp = raw + ((p + 1) & 3) * 7 * RP;     // plane p+1
+        const PlaneK pk = plane_consts(a.rsrc, a.rdst, p, nz, a.eps_hot, a.eps_cold);
+        float* out = fn + (p % 3) * 7 * NP;
+        for (int e = tid; e < NP; e += FT) {
+            const int lx = e % NW, ly = e / NW;
+            const int x = x0 - 1 + lx, y = y0 - 1 + ly;
+            if (!PERIODIC && (x < 0 || x >= nx || y < 0 || y >= ny)) continue;
+            const int o = (ly + 1) * RW + (lx + 3);          // this node in the raw plane
+            const float g0 = R0[o];
+            const float g1 = (PERIODIC || x > 0) ? R0[RP + o - 1] : R0[2 * RP + o];
+            const float g2 = (PERIODIC || x < nx - 1) ? R0[2 * RP + o + 1] : R0[RP + o];
+            const float g3 = (PERIODIC || y > 0) ? R0[3 * RP + o - RW] : R0[4 * RP + o];
+            const float g4 = (PERIODIC || y < ny - 1) ? R0[4 * RP + o + RW] : R0[3 * RP + o];
+            const float g5 = p > 0 ? Rm[5 * RP + o] : -R0[6 * RP + o];
+            const float g6 = p < nz - 1 ? Rp[6 * RP + o] : -R0[5 * RP + o];
+            const int xg = PERIODIC ? (x < 0 ? x + nx : (x >= nx ? x - nx : x)) : x;
+            const int yg = PERIODIC ? (y < 0 ? y + ny : (y >= ny ? y - ny : y)) : y;
+            const int ph = a.phase[((long long)p * ny + yg) * pitch + xg];
+            const Collided c = collide_node(g0, g1, g2, g3, g4, g5, g6, s_sb[2 * ph], s_sb[2 * ph + 1],
+                                            pk.kT, pk.kJ);
+#pragma unroll
+            for (int i = 0; i < 7; ++i) out[i * NP + e] = c.o[i];
+        }
     };
 
+    // prologue: raw planes z0-2 .. z0+1, step n at z0-1 and z0, raw z0+2
+    for (int p = z0 - 2; p <= z0 + 1; ++p) {
+        fetch(p);
+        store(p);
+    }
+    __syncthreads();
     first_plane(z0 - 1);
     first_plane(z0);
+    fetch(z0 + 2);
+    __syncthreads();                                    // raw slot of z0-2 is free
+    store(z0 + 2);
+    __syncthreads();
+
     const int tx = tid % FX, ty = tid / FX;
     const int x = x0 + tx, y = y0 + ty;
-    const int e = (ty + 1) * (FX + 2) + (tx + 1);      // this node in the halo'd tile
+    const int e = (ty + 1) * NW + (tx + 1);             // this node in the step-n plane
     for (int z = z0; z < z1; ++z) {
-        first_plane(z + 1);
+        fetch(z + 3);                                   // overlaps the rest of the iteration
+        first_plane(z + 1);                             // raw planes z .. z+2
         __syncthreads();
-        // step n+1 at (x, y, z) from the ring (frame rdst -> rdst)
-        const float(*cur)[FR] = ring[z % 3];
-        const float g0 = cur[0][e];
-        float g1, g2, g3, g4, g5, g6;
-        g1 = (PERIODIC || x > 0) ? cur[1][e - 1] : cur[2][e];
-        g2 = (PERIODIC || x < nx - 1) ? cur[2][e + 1] : cur[1][e];
-        g3 = (PERIODIC || y > 0) ? cur[3][e - (FX + 2)] : cur[4][e];
-        g4 = (PERIODIC || y < ny - 1) ? cur[4][e + (FX + 2)] : cur[3][e];
-        g5 = z > 0 ? ring[(z + 2) % 3][5][e] : -cur[6][e];
-        g6 = z < nz - 1 ? ring[(z + 1) % 3][6][e] : -cur[5][e];
+        // step n+1 at (x, y, z) from the step-n ring (frame rdst -> rdst)
+        const float* cur = fn + (z % 3) * 7 * NP;
+        const float* below = fn + ((z + 2) % 3) * 7 * NP;
+        const float* above = fn + ((z + 1) % 3) * 7 * NP;
+        const float g0 = cur[e];
+        const float g1 = (PERIODIC || x > 0) ? cur[NP + e - 1] : cur[2 * NP + e];
+        const float g2 = (PERIODIC || x < nx - 1) ? cur[2 * NP + e + 1] : cur[NP + e];
+        const float g3 = (PERIODIC || y > 0) ? cur[3 * NP + e - NW] : cur[4 * NP + e];
+        const float g4 = (PERIODIC || y < ny - 1) ? cur[4 * NP + e + NW] : cur[3 * NP + e];
+        const float g5 = z > 0 ? below[5 * NP + e] : -cur[6 * NP + e];
+        const float g6 = z < nz - 1 ? above[6 * NP + e] : -cur[5 * NP + e];
         const PlaneK pk = plane_consts(a.rdst, a.rdst, z, nz, a.eps_hot, a.eps_cold);
         const long long v = ((long long)z * ny + y) * pitch + x;
         const int ph = a.phase[v];
@@ -654,7 +708,8 @@ __global__ void __launch_bounds__(FX * FY) fused2_kernel(const StepArgs a, int z
                                         pk.kT, pk.kJ);
 #pragma unroll
         for (int i = 0; i < 7; ++i) dst[i * P + v] = c.o[i];
-        __syncthreads();                    // the ring slot of plane z-1 is reused next
+        store(z + 3);                                   // raw slot of plane z-1 is free
+        __syncthreads();
     }
 }
 
