@@ -80,9 +80,9 @@ typedef struct {
                                (same kernels and results; for tools that cannot trace
                                conditional graphs) */
     int32_t fuse;           /* 1: FP32 plain steps run two at a time in one kernel
-                               (temporal blocking; needs nx % 32 == 0 and ny % 8 == 0
-                               after the axis permutation, else single steps);
-                               identical results; 0 (default): single steps */
+                               (temporal blocking; needs rows of nx = 128 or 256 nodes
+                               and ny % 8 == 0 after the axis permutation, else single
+                               steps); identical results; 0 (default): single steps */
     int32_t reserved;
     const float* t_init;    /* host, nx*ny*nz initial T field in the original axis
                                order, or NULL for the linear profile between walls */

@@ -23,6 +23,7 @@ using lbm::Layout;
 struct lbm_ctx {
     int n[3] = {0, 0, 0};
     int device = 0;
+    int n_sm = 152;                        // multiprocessors of the device
     cudaStream_t own_stream = nullptr;     // context stream (non-blocking)
     cudaStream_t cap_stream = nullptr;     // private stream used only for graph capture
     bool poisoned = false;
@@ -260,25 +261,39 @@ cudaError_t launch_step(const lbm_ctx* c, int src, bool check, Frame fr, cudaStr
 }
 
 // Two plain FP32 steps in one launch (temporal blocking), when the layout
-// allows it.
+// allows it: rows of 128 or 256 nodes without padding, whole tiles of rows.
 bool fusable(const lbm_ctx* c) {
-    return c->opts.fuse && c->fmt == LBM_STORE_F32 && c->L.NX % lbm::FX == 0 &&
-           c->L.NY % lbm::FY == 0;
+    return c->opts.fuse && c->fmt == LBM_STORE_F32 && (c->L.NX == 128 || c->L.NX == 256) &&
+           c->L.pitch == c->L.NX && c->L.NY % lbm::F2_FY == 0;
 }
 
 cudaError_t launch_pair(const lbm_ctx* c, int src, Frame fr, cudaStream_t st) {
     const lbm::StepArgs a = step_args(c, src, fr);
-    const int bxy = (c->L.NX / lbm::FX) * (c->L.NY / lbm::FY);
-    int nzc = (152 * 4 + bxy - 1) / bxy;                 // ~4 blocks per SM in flight
-    if (nzc > c->L.NZ) nzc = c->L.NZ;
-    int zchunk = (c->L.NZ + nzc - 1) / nzc;
-    if (zchunk < 4) zchunk = 4;
-    const dim3 grid(c->L.NX / lbm::FX, c->L.NY / lbm::FY, (c->L.NZ + zchunk - 1) / zchunk);
-    const size_t smem = lbm::fused2_smem_bytes(c->n_phases);
-    if (c->lateral == LBM_LATERAL_PERIODIC)
-        lbm::fused2_kernel<true><<<grid, lbm::FT, smem, st>>>(a, zchunk);
-    else
-        lbm::fused2_kernel<false><<<grid, lbm::FT, smem, st>>>(a, zchunk);
+    const int kw = c->L.NX / 128;
+    const int bxy = c->L.NY / lbm::F2_FY;
+    // z chunks: balance the fill of the last wave against the two extra
+    // planes of the first step each chunk computes; chunks of >= 8 planes
+    const long long slots = (long long)(2 / kw) * c->n_sm;
+    int zchunk = c->L.NZ;
+    double best = -1.0;
+    for (int nzc = 1; nzc <= c->L.NZ / 8 || nzc == 1; ++nzc) {
+        const int zc = (c->L.NZ + nzc - 1) / nzc;
+        const long long blocks = (long long)bxy * ((c->L.NZ + zc - 1) / zc);
+        const double fill = (double)blocks / (double)(((blocks + slots - 1) / slots) * slots);
+        const double score = fill * zc / (zc + 2.0);
+        if (score > best + 1e-9) { best = score; zchunk = zc; }
+    }
+    const dim3 grid(bxy, (c->L.NZ + zchunk - 1) / zchunk);
+    const int threads = lbm::fused2_threads(kw);
+    const size_t smem = lbm::fused2_smem_bytes(kw, c->n_phases);
+    const bool per = c->lateral == LBM_LATERAL_PERIODIC;
+    if (kw == 1) {
+        if (per) lbm::fused2_kernel<true, 1><<<grid, threads, smem, st>>>(a, zchunk);
+        else lbm::fused2_kernel<false, 1><<<grid, threads, smem, st>>>(a, zchunk);
+    } else {
+        if (per) lbm::fused2_kernel<true, 2><<<grid, threads, smem, st>>>(a, zchunk);
+        else lbm::fused2_kernel<false, 2><<<grid, threads, smem, st>>>(a, zchunk);
+    }
     return cudaGetLastError();
 }
 
@@ -473,11 +488,16 @@ lbm_status lbm_create(int nx, int ny, int nz, int cuda_device, lbm_ctx** out) {
               cudaMalloc((void**)&c->d_hist, sizeof(double) * 4 * kHistCap) == cudaSuccess &&
               cudaMallocHost((void**)&c->h_ctl, sizeof(Ctl)) == cudaSuccess &&
               cudaEventCreate(&c->ev0) == cudaSuccess && cudaEventCreate(&c->ev1) == cudaSuccess &&
+              cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, cuda_device) == cudaSuccess &&
               // the fused two-step kernel needs more than the default 48 KB
-              cudaFuncSetAttribute(lbm::fused2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)lbm::fused2_smem_bytes(255)) == cudaSuccess &&
-              cudaFuncSetAttribute(lbm::fused2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)lbm::fused2_smem_bytes(255)) == cudaSuccess;
+              cudaFuncSetAttribute(lbm::fused2_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)lbm::fused2_smem_bytes(1, 255)) == cudaSuccess &&
+              cudaFuncSetAttribute(lbm::fused2_kernel<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)lbm::fused2_smem_bytes(1, 255)) == cudaSuccess &&
+              cudaFuncSetAttribute(lbm::fused2_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)lbm::fused2_smem_bytes(2, 255)) == cudaSuccess &&
+              cudaFuncSetAttribute(lbm::fused2_kernel<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)lbm::fused2_smem_bytes(2, 255)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         lbm_destroy(c);

@@ -562,153 +562,168 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
     }
 }
 
-// Two fused steps (temporal blocking) in FP32.  A block owns a tile of
-// FX x FY nodes and marches up a chunk of planes.  Per plane it keeps
-//   - the state of step n-1 (read from global memory) for the tile plus a
-//     halo of 2 rows and 4 columns (aligned float4 rows) in a ring of four
-//     planes; the next plane is prefetched into registers at the top of an
-//     iteration and stored at its end, so its global loads overlap the work;
-//   - the state after step n for the tile plus a one-node halo in a ring of
-//     three planes.
-// Each iteration computes step n for the plane above (tile + halo) and step
-// n+1 for the current plane (tile), which goes to global memory.  Each
-// node's arithmetic is the single step's (collide_node), so two fused steps
-// equal two single steps bit for bit; the intermediate state never reaches
-// global memory.  Requires FP32 storage, nx % FX == 0 and ny % FY == 0.
-// Step n runs from frame rsrc to rdst, step n+1 within rdst.
-constexpr int FX = 32, FY = 8;
-constexpr int FT = FX * FY;                  // threads
-constexpr int RW = FX + 8, RH = FY + 4;      // raw plane: 4 + FX + 4 columns, 2 + FY + 2 rows
-constexpr int RP = RW * RH;                  // floats per population of a raw plane
-constexpr int NW = FX + 2, NH = FY + 2;      // step-n plane: tile + 1
-constexpr int NP = NW * NH;
-constexpr int RAW_ITEMS = 7 * RH * (RW / 4); // float4 per raw plane
-constexpr int RAW_PER_THREAD = (RAW_ITEMS + FT - 1) / FT;
+// Two fused steps (temporal blocking) in FP32.  A block owns F2_FY rows of
+// the full x extent (nx = 128 KW: KW warps per row, each thread 4
+// consecutive nodes) and marches up a chunk of planes.  Block row r = 0 ..
+// F2_FY + 1 is grid row y0 - 1 + r: rows 1 .. F2_FY are the tile, rows 0 and
+// F2_FY + 1 the halo whose populations 3 and 4 the tile's second step pulls.
+// Iteration i computes step n at plane i for all rows (pulled from global
+// memory, written to a ring of three shared planes) and step n + 1 at plane
+// i - 2 for the tile rows (pulled from the ring, written to global memory).
+// The loads of plane i are issued before the second step's work, so they are
+// in flight while it runs.  Every node's arithmetic is the single step's
+// (collide_node), so two fused steps equal two single steps bit for bit.
+// Step n runs from frame rsrc to rdst, step n + 1 within rdst.
+constexpr int F2_FY = 8;
+constexpr int F2_ROWS = F2_FY + 2;
 
-__host__ __device__ constexpr size_t fused2_smem_bytes(int n_phases) {
-    return sizeof(float) * (4 * 7 * RP + 3 * 7 * NP) + sizeof(float4) * 2 * n_phases;
+__host__ __device__ constexpr int fused2_threads(int kw) { return 32 * kw * F2_ROWS; }
+__host__ __device__ constexpr size_t fused2_smem_bytes(int kw, int n_phases) {
+    return sizeof(float) * 3 * 7 * F2_ROWS * 128 * kw + sizeof(float4) * 2 * n_phases;
 }
 
-template <bool PERIODIC>
-__global__ void __launch_bounds__(FT, 2) fused2_kernel(const StepArgs a, int zchunk) {
-    extern __shared__ float4 smem4[];
-    float* raw = reinterpret_cast<float*>(smem4);              // [4][7][RH][RW]
-    float* fn = raw + 4 * 7 * RP;                              // [3][7][NH][NW]
-    float4* s_sb = reinterpret_cast<float4*>(fn + 3 * 7 * NP);
-    const int tid = threadIdx.x;
-    for (int i = tid; i < 2 * a.n_phases; i += FT) s_sb[i] = a.sb[i];
+__device__ __forceinline__ float4 f4neg(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
+__device__ __forceinline__ float f4get(const float4& v, int k) {
+    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
 
-    const int x0 = blockIdx.x * FX, y0 = blockIdx.y * FY;
-    const int z0 = blockIdx.z * zchunk;
-    const int z1 = min(z0 + zchunk, a.nz);
+// Step at 4 nodes from pulled values: g1 = (l1, c1.x, c1.y, c1.z) and
+// g2 = (c2.y, c2.z, c2.w, r2) are assembled by the caller.
+struct Quad7 {
+    float4 o[7];
+};
+__device__ __forceinline__ Quad7 collide_quad(const float4& g0, const float4& g1, const float4& g2,
+                                              const float4& g3, const float4& g4, const float4& g5,
+                                              const float4& g6, unsigned phw, const float4* s_sb,
+                                              float kT, float kJ) {
+    Quad7 q;
+    float* o = reinterpret_cast<float*>(q.o);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int ph = (phw >> (8 * k)) & 255u;
+        const Collided c = collide_node(f4get(g0, k), f4get(g1, k), f4get(g2, k), f4get(g3, k),
+                                        f4get(g4, k), f4get(g5, k), f4get(g6, k), s_sb[2 * ph],
+                                        s_sb[2 * ph + 1], kT, kJ);
+#pragma unroll
+        for (int i = 0; i < 7; ++i) o[4 * i + k] = c.o[i];
+    }
+    return q;
+}
+
+template <bool PERIODIC, int KW>
+__global__ void __launch_bounds__(32 * KW * F2_ROWS, 2 / KW) fused2_kernel(const StepArgs a, int zchunk) {
+    constexpr int NXB = 128 * KW;                  // nodes per row (= nx)
+    constexpr int RR = F2_ROWS * NXB;              // floats per population of a ring plane
+    constexpr int RS = 7 * RR;                     // floats per ring plane
+    extern __shared__ float4 smem4[];
+    float* fn = reinterpret_cast<float*>(smem4);   // [3][7][F2_ROWS][NXB]
+    float4* s_sb = reinterpret_cast<float4*>(fn + 3 * RS);
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 2 * a.n_phases; i += 32 * KW * F2_ROWS) s_sb[i] = a.sb[i];
+
+    const int lane = tid & 31;
+    const int r = tid / (32 * KW);                 // block row (warp-uniform)
+    const int x = 4 * (tid - r * 32 * KW);         // first of this thread's 4 nodes
+    const int ny = a.ny, nz = a.nz, pitch = a.pitch;
+    const int y0 = blockIdx.x * F2_FY;
+    int y = y0 - 1 + r;
+    bool row_in = true;
+    if (PERIODIC) y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+    else row_in = y >= 0 && y < ny;
+    const bool tile_row = r >= 1 && r <= F2_FY;
+    const bool ylo = y == 0, yhi = y == ny - 1;
+    const int xm = x == 0 ? NXB - 1 : x - 1;       // x - 1 of node x, wrapped
+    const int xp = x + 4 == NXB ? 0 : x + 4;       // x + 1 of node x + 3, wrapped
     const long long P = a.pstride;
+    const long long PL = (long long)ny * pitch;
+    const long long yrow = (long long)y * pitch;
+    // rows pulled for populations 3 and 4: the neighbour row, or the own
+    // node's opposite population at an adiabatic face (Eq. 24)
+    const long long o3 = PERIODIC ? 3 * P + (long long)(ylo ? ny - 1 : y - 1) * pitch
+                                  : (ylo ? 4 * P + yrow : 3 * P + yrow - pitch);
+    const long long o4 = PERIODIC ? 4 * P + (long long)(yhi ? 0 : y + 1) * pitch
+                                  : (yhi ? 3 * P + yrow : 4 * P + yrow + pitch);
     const float* __restrict__ src = reinterpret_cast<const float*>(a.src);
     float* __restrict__ dst = reinterpret_cast<float*>(a.dst);
-    const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch;
+    const int z0 = blockIdx.y * zchunk;
+    const int z1 = min(z0 + zchunk, nz);
+    __syncthreads();                               // s_sb is ready
 
-    // ---- raw plane staging: global -> registers -> shared ----
-    float4 pre[RAW_PER_THREAD];
-    auto fetch = [&](int p) {
+    unsigned phA = 0u, phB = 0u;                   // phase words of planes i - 2 and i - 1
+    for (int i = z0 - 1; i <= z1 + 1; ++i) {
+        // ---- loads of step n at plane i (warp-uniform condition) ----
+        const bool first = i <= z1 && i >= 0 && i < nz && row_in;
+        float4 q0, q1, q2, q3, q4, q5, q6;
+        unsigned phC = 0u;
+        if (first) {
+            const float* s = src + (long long)i * PL;
+            q0 = __ldg(reinterpret_cast<const float4*>(s + yrow + x));
+            q1 = __ldg(reinterpret_cast<const float4*>(s + P + yrow + x));
+            q2 = __ldg(reinterpret_cast<const float4*>(s + 2 * P + yrow + x));
+            q3 = __ldg(reinterpret_cast<const float4*>(s + o3 + x));
+            q4 = __ldg(reinterpret_cast<const float4*>(s + o4 + x));
+            // the walls (Eq. 23) read the own node's opposite population
+            q5 = __ldg(reinterpret_cast<const float4*>(s + (i > 0 ? 5 * P - PL : 6 * P) + yrow + x));
+            q6 = __ldg(reinterpret_cast<const float4*>(s + (i < nz - 1 ? 6 * P + PL : 5 * P) + yrow + x));
+            phC = __ldg(reinterpret_cast<const unsigned*>(a.phase + (long long)i * PL + yrow + x));
+        }
+        // ---- step n + 1 at plane j = i - 2, tile rows ----
+        const int j = i - 2;
+        if (tile_row && j >= z0 && j < z1) {
+            const float* fs = fn + (j % 3) * RS + r * NXB + x;
+            const float* fb = fn + ((j + 2) % 3) * RS + r * NXB + x;   // plane j - 1
+            const float* fa = fn + ((j + 1) % 3) * RS + r * NXB + x;   // plane j + 1
+            const float4 g0 = *reinterpret_cast<const float4*>(fs);
+            const float4 c1 = *reinterpret_cast<const float4*>(fs + RR);
+            const float4 c2 = *reinterpret_cast<const float4*>(fs + 2 * RR);
+            const float4 g3 = (PERIODIC || !ylo) ? *reinterpret_cast<const float4*>(fs + 3 * RR - NXB)
+                                                 : *reinterpret_cast<const float4*>(fs + 4 * RR);
+            const float4 g4 = (PERIODIC || !yhi) ? *reinterpret_cast<const float4*>(fs + 4 * RR + NXB)
+                                                 : *reinterpret_cast<const float4*>(fs + 3 * RR);
+            const float4 g5 = j > 0 ? *reinterpret_cast<const float4*>(fb + 5 * RR)
+                                    : f4neg(*reinterpret_cast<const float4*>(fs + 6 * RR));
+            const float4 g6 = j < nz - 1 ? *reinterpret_cast<const float4*>(fa + 6 * RR)
+                                         : f4neg(*reinterpret_cast<const float4*>(fs + 5 * RR));
+            // x-neighbours within the ring row (the row holds the full x extent)
+            const float* row1 = fn + (j % 3) * RS + RR + r * NXB;
+            const float* row2 = row1 + RR;
+            float l1 = row1[xm], r2 = row2[xp];
+            if (!PERIODIC && x == 0) l1 = c2.x;                 // Eq. 24 at x = 0
+            if (!PERIODIC && x + 4 == NXB) r2 = c1.w;           // and at x = nx - 1
+            const float4 g1 = make_float4(l1, c1.x, c1.y, c1.z);
+            const float4 g2 = make_float4(c2.y, c2.z, c2.w, r2);
+            const PlaneK pk = plane_consts(a.rdst, a.rdst, j, nz, a.eps_hot, a.eps_cold);
+            const Quad7 o = collide_quad(g0, g1, g2, g3, g4, g5, g6, phA, s_sb, pk.kT, pk.kJ);
+            float* d = dst + (long long)j * PL + yrow + x;
 #pragma unroll
-        for (int k = 0; k < RAW_PER_THREAD; ++k) {
-            const int it = tid + k * FT;
-            pre[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (it >= RAW_ITEMS || p < 0 || p >= nz) continue;
-            const int q = it / (RH * (RW / 4));
-            const int rem = it - q * (RH * (RW / 4));
-            const int r = rem / (RW / 4), c = rem - r * (RW / 4);
-            int y = y0 - 2 + r, x = x0 - 4 + 4 * c;
-            if (PERIODIC) {
-                y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-                x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
-            } else if (y < 0 || y >= ny || x < 0 || x >= nx) {
-                continue;                               // outside an adiabatic cell
+            for (int p = 0; p < 7; ++p) *reinterpret_cast<float4*>(d + p * P) = o.o[p];
+        }
+        // ---- step n at plane i into the ring ----
+        if (first) {
+            if (i == 0) q5 = f4neg(q5);
+            if (i == nz - 1) q6 = f4neg(q6);
+            float l1 = __shfl_sync(kFull, q1.w, (lane + 31) & 31);
+            float r2 = __shfl_sync(kFull, q2.x, (lane + 1) & 31);
+            if (KW > 1 && lane == 0) l1 = __ldg(src + (long long)i * PL + P + yrow + xm);
+            if (KW > 1 && lane == 31) r2 = __ldg(src + (long long)i * PL + 2 * P + yrow + xp);
+            if (!PERIODIC && x == 0) l1 = q2.x;
+            if (!PERIODIC && x + 4 == NXB) r2 = q1.w;
+            const float4 g1 = make_float4(l1, q1.x, q1.y, q1.z);
+            const float4 g2 = make_float4(q2.y, q2.z, q2.w, r2);
+            const PlaneK pk = plane_consts(a.rsrc, a.rdst, i, nz, a.eps_hot, a.eps_cold);
+            const Quad7 o = collide_quad(q0, g1, g2, q3, q4, q5, q6, phC, s_sb, pk.kT, pk.kJ);
+            float* w = fn + (i % 3) * RS + r * NXB + x;
+            if (tile_row) {
+#pragma unroll
+                for (int p = 0; p < 7; ++p) *reinterpret_cast<float4*>(w + p * RR) = o.o[p];
+            } else if (r == 0) {
+                *reinterpret_cast<float4*>(w + 3 * RR) = o.o[3];
+            } else {
+                *reinterpret_cast<float4*>(w + 4 * RR) = o.o[4];
             }
-            pre[k] = __ldg(reinterpret_cast<const float4*>(src + q * P + ((long long)p * ny + y) * pitch + x));
         }
-    };
-    auto store = [&](int p) {
-        if (p < 0 || p >= nz) return;
-        float* slot = raw + (p & 3) * 7 * RP;
-#pragma unroll
-        for (int k = 0; k < RAW_PER_THREAD; ++k) {
-            const int it = tid + k * FT;
-            if (it >= RAW_ITEMS) continue;
-            const int q = it / (RH * (RW / 4));
-            const int rem = it - q * (RH * (RW / 4));
-            const int r = rem / (RW / 4), c = rem - r * (RW / 4);
-            *reinterpret_cast<float4*>(slot + q * RP + r * RW + 4 * c) = pre[k];
-        }
-    };
-    // ---- step n of the halo'd tile at plane p, from the raw ring ----
-    auto first_plane = [&](int p) {
-        if (p < 0 || p >= nz) return;
-        const float* R0 = raw + (p & 3) * 7 * RP;
-        const float* Rm = raw + ((p + 3) & 3) * 7 * RP;     // plane p-1
-        const float* Rp = raw + ((p + 1) & 3) * 7 * RP;     // plane p+1
-        const PlaneK pk = plane_consts(a.rsrc, a.rdst, p, nz, a.eps_hot, a.eps_cold);
-        float* out = fn + (p % 3) * 7 * NP;
-        for (int e = tid; e < NP; e += FT) {
-            const int lx = e % NW, ly = e / NW;
-            const int x = x0 - 1 + lx, y = y0 - 1 + ly;
-            if (!PERIODIC && (x < 0 || x >= nx || y < 0 || y >= ny)) continue;
-            const int o = (ly + 1) * RW + (lx + 3);          // this node in the raw plane
-            const float g0 = R0[o];
-            const float g1 = (PERIODIC || x > 0) ? R0[RP + o - 1] : R0[2 * RP + o];
-            const float g2 = (PERIODIC || x < nx - 1) ? R0[2 * RP + o + 1] : R0[RP + o];
-            const float g3 = (PERIODIC || y > 0) ? R0[3 * RP + o - RW] : R0[4 * RP + o];
-            const float g4 = (PERIODIC || y < ny - 1) ? R0[4 * RP + o + RW] : R0[3 * RP + o];
-            const float g5 = p > 0 ? Rm[5 * RP + o] : -R0[6 * RP + o];
-            const float g6 = p < nz - 1 ? Rp[6 * RP + o] : -R0[5 * RP + o];
-            const int xg = PERIODIC ? (x < 0 ? x + nx : (x >= nx ? x - nx : x)) : x;
-            const int yg = PERIODIC ? (y < 0 ? y + ny : (y >= ny ? y - ny : y)) : y;
-            const int ph = a.phase[((long long)p * ny + yg) * pitch + xg];
-            const Collided c = collide_node(g0, g1, g2, g3, g4, g5, g6, s_sb[2 * ph], s_sb[2 * ph + 1],
-                                            pk.kT, pk.kJ);
-#pragma unroll
-            for (int i = 0; i < 7; ++i) out[i * NP + e] = c.o[i];
-        }
-    };
-
-    // prologue: raw planes z0-2 .. z0+1, step n at z0-1 and z0, raw z0+2
-    for (int p = z0 - 2; p <= z0 + 1; ++p) {
-        fetch(p);
-        store(p);
-    }
-    __syncthreads();
-    first_plane(z0 - 1);
-    first_plane(z0);
-    fetch(z0 + 2);
-    __syncthreads();                                    // raw slot of z0-2 is free
-    store(z0 + 2);
-    __syncthreads();
-
-    const int tx = tid % FX, ty = tid / FX;
-    const int x = x0 + tx, y = y0 + ty;
-    const int e = (ty + 1) * NW + (tx + 1);             // this node in the step-n plane
-    for (int z = z0; z < z1; ++z) {
-        fetch(z + 3);                                   // overlaps the rest of the iteration
-        first_plane(z + 1);                             // raw planes z .. z+2
-        __syncthreads();
-        // step n+1 at (x, y, z) from the step-n ring (frame rdst -> rdst)
-        const float* cur = fn + (z % 3) * 7 * NP;
-        const float* below = fn + ((z + 2) % 3) * 7 * NP;
-        const float* above = fn + ((z + 1) % 3) * 7 * NP;
-        const float g0 = cur[e];
-        const float g1 = (PERIODIC || x > 0) ? cur[NP + e - 1] : cur[2 * NP + e];
-        const float g2 = (PERIODIC || x < nx - 1) ? cur[2 * NP + e + 1] : cur[NP + e];
-        const float g3 = (PERIODIC || y > 0) ? cur[3 * NP + e - NW] : cur[4 * NP + e];
-        const float g4 = (PERIODIC || y < ny - 1) ? cur[4 * NP + e + NW] : cur[3 * NP + e];
-        const float g5 = z > 0 ? below[5 * NP + e] : -cur[6 * NP + e];
-        const float g6 = z < nz - 1 ? above[6 * NP + e] : -cur[5 * NP + e];
-        const PlaneK pk = plane_consts(a.rdst, a.rdst, z, nz, a.eps_hot, a.eps_cold);
-        const long long v = ((long long)z * ny + y) * pitch + x;
-        const int ph = a.phase[v];
-        const Collided c = collide_node(g0, g1, g2, g3, g4, g5, g6, s_sb[2 * ph], s_sb[2 * ph + 1],
-                                        pk.kT, pk.kJ);
-#pragma unroll
-        for (int i = 0; i < 7; ++i) dst[i * P + v] = c.o[i];
-        store(z + 3);                                   // raw slot of plane z-1 is free
+        phA = phB;
+        phB = phC;
         __syncthreads();
     }
 }

@@ -325,14 +325,17 @@ def test_history_records_every_check():
 
 
 @pytest.mark.parametrize("lateral", [0, 1])
-@pytest.mark.parametrize("axis", [2, 0])
-def test_fused_pairs_equal_single_steps_bit_for_bit(lateral, axis):
+@pytest.mark.parametrize("axis,shape", [(2, (128, 16, 24)), (0, (24, 128, 16)), (2, (128, 16, 80)),
+                                        (2, (256, 8, 40))])
+def test_fused_pairs_equal_single_steps_bit_for_bit(lateral, axis, shape):
     """Two steps fused in one kernel (temporal blocking) do each node's
     arithmetic exactly as two single steps: identical fields and k_eff,
-    through the graph loop and through lbm_advance."""
-    rng = np.random.default_rng(31 + lateral + axis)
+    through the graph loop and through lbm_advance.  Shapes (canonical rows
+    of 128 or 256 nodes, the layouts the fused kernel takes): one z chunk
+    along z and from x, several z chunks (128 x 16 x 80), and rows of two
+    warps (256 x 8 x 40)."""
+    rng = np.random.default_rng(31 + lateral + axis + shape[2])
     lam = np.stack([I.random_spd(rng) for _ in range(3)])
-    shape = (64, 40, 24) if axis == 2 else (24, 64, 40)      # (nx, ny, nz) -> canonical 64 x 40
     phase = I.random_phase(rng, *shape, 3)
     out = []
     for fuse in (1, 0):
