@@ -8,8 +8,9 @@ difference along z, periodic laterals, FP32 distributions.
 One bench step = one pass of the hot path over the cell: ITERS fused
 collide-stream iterations in check intervals of K = 100 (each interval ends
 with an FP64 plane-flux / residual check and the k_eff finalize), launched as
-one CUDA graph with a device-side while condition.  Metric: GLUPS (giga
-lattice updates per second).  The f buffers (2 x 117 MB) exceed the 129 MB
+one CUDA graph with a device-side while condition.  FP32 plain iterations run
+two per launch (temporal blocking, identical results; --no-fuse: one).
+Metric: GLUPS (giga lattice updates per second).  The f buffers (2 x 117 MB) exceed the 129 MB
 L2, so no flush is needed between steps.
 
 `value`: device time (CUDA events on the solver's stream) with the state
@@ -426,8 +427,8 @@ def main():
                          "host: the same kernels launched from the host (for profilers)")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
                     help="distribution storage (collision is FP32 in every mode)")
-    ap.add_argument("--fuse", action="store_true",
-                    help="run FP32 plain steps two at a time (temporal blocking)")
+    ap.add_argument("--no-fuse", action="store_true",
+                    help="run FP32 plain steps one per launch (default: two, temporal blocking)")
     ap.add_argument("--no-variants", action="store_true",
                     help="omit the BF16/FP16 storage variants of the step")
     ap.add_argument("--no-extras", action="store_true",
@@ -437,6 +438,7 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per fused-step launch from an ncu capture")
     args = ap.parse_args()
+    args.fuse = not args.no_fuse
     if args.iters % K:
         ap.error("--iters must be a multiple of 100")
     if args.impl == "reference":

@@ -81,8 +81,9 @@ typedef struct {
                                conditional graphs) */
     int32_t fuse;           /* 1: FP32 plain steps run two at a time in one kernel
                                (temporal blocking; needs rows of nx = 128 or 256 nodes
-                               and ny % 8 == 0 after the axis permutation, else single
-                               steps); identical results; 0 (default): single steps */
+                               and ny a multiple of 4 or 8 respectively, after the axis
+                               permutation, else single steps); identical results;
+                               the default; 0: single steps only */
     int32_t reserved;
     const float* t_init;    /* host, nx*ny*nz initial T field in the original axis
                                order, or NULL for the linear profile between walls */

@@ -24,6 +24,7 @@ struct lbm_ctx {
     int n[3] = {0, 0, 0};
     int device = 0;
     int n_sm = 152;                        // multiprocessors of the device
+    bool fuse_ok[2] = {false, false};      // fused kernel usable for rows of 128, 256 nodes
     cudaStream_t own_stream = nullptr;     // context stream (non-blocking)
     cudaStream_t cap_stream = nullptr;     // private stream used only for graph capture
     bool poisoned = false;
@@ -264,16 +265,16 @@ cudaError_t launch_step(const lbm_ctx* c, int src, bool check, Frame fr, cudaStr
 // allows it: rows of 128 or 256 nodes without padding, whole tiles of rows.
 bool fusable(const lbm_ctx* c) {
     return c->opts.fuse && c->fmt == LBM_STORE_F32 && (c->L.NX == 128 || c->L.NX == 256) &&
-           c->L.pitch == c->L.NX && c->L.NY % lbm::F2_FY == 0;
+           c->fuse_ok[c->L.NX / 128 - 1] && c->L.pitch == c->L.NX && c->L.NY % lbm::f2_fy(c->L.NX / 128) == 0;
 }
 
 cudaError_t launch_pair(const lbm_ctx* c, int src, Frame fr, cudaStream_t st) {
     const lbm::StepArgs a = step_args(c, src, fr);
     const int kw = c->L.NX / 128;
-    const int bxy = c->L.NY / lbm::F2_FY;
+    const int bxy = c->L.NY / lbm::f2_fy(kw);
     // z chunks: balance the fill of the last wave against the two extra
     // planes of the first step each chunk computes; chunks of >= 8 planes
-    const long long slots = (long long)(2 / kw) * c->n_sm;
+    const long long slots = (long long)lbm::f2_minb(kw) * c->n_sm;
     int zchunk = c->L.NZ;
     double best = -1.0;
     for (int nzc = 1; nzc <= c->L.NZ / 8 || nzc == 1; ++nzc) {
@@ -456,7 +457,7 @@ void lbm_default_opts(lbm_solve_opts* o) {
     o->check_every = 100;
     o->stall_checks = 0;
     o->storage = LBM_STORE_F32;
-    o->fuse = 0;
+    o->fuse = 1;
     o->t_init = nullptr;
     o->stream = nullptr;
 }
@@ -488,16 +489,22 @@ lbm_status lbm_create(int nx, int ny, int nz, int cuda_device, lbm_ctx** out) {
               cudaMalloc((void**)&c->d_hist, sizeof(double) * 4 * kHistCap) == cudaSuccess &&
               cudaMallocHost((void**)&c->h_ctl, sizeof(Ctl)) == cudaSuccess &&
               cudaEventCreate(&c->ev0) == cudaSuccess && cudaEventCreate(&c->ev1) == cudaSuccess &&
-              cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, cuda_device) == cudaSuccess &&
-              // the fused two-step kernel needs more than the default 48 KB
-              cudaFuncSetAttribute(lbm::fused2_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)lbm::fused2_smem_bytes(1, 255)) == cudaSuccess &&
-              cudaFuncSetAttribute(lbm::fused2_kernel<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)lbm::fused2_smem_bytes(1, 255)) == cudaSuccess &&
-              cudaFuncSetAttribute(lbm::fused2_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)lbm::fused2_smem_bytes(2, 255)) == cudaSuccess &&
-              cudaFuncSetAttribute(lbm::fused2_kernel<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)lbm::fused2_smem_bytes(2, 255)) == cudaSuccess;
+              cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, cuda_device) == cudaSuccess;
+    // the fused two-step kernel needs more than the default 48 KB of shared
+    // memory; a row width whose kernel cannot get it runs single steps
+    if (ok) {
+        c->fuse_ok[0] =
+            cudaFuncSetAttribute(lbm::fused2_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)lbm::fused2_smem_bytes(1, 255)) == cudaSuccess &&
+            cudaFuncSetAttribute(lbm::fused2_kernel<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)lbm::fused2_smem_bytes(1, 255)) == cudaSuccess;
+        c->fuse_ok[1] =
+            cudaFuncSetAttribute(lbm::fused2_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)lbm::fused2_smem_bytes(2, 255)) == cudaSuccess &&
+            cudaFuncSetAttribute(lbm::fused2_kernel<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)lbm::fused2_smem_bytes(2, 255)) == cudaSuccess;
+        cudaGetLastError();
+    }
     if (!ok) {
         cudaGetLastError();
         lbm_destroy(c);

@@ -562,11 +562,11 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
     }
 }
 
-// Two fused steps (temporal blocking) in FP32.  A block owns F2_FY rows of
-// the full x extent (nx = 128 KW: KW warps per row, each thread 4
-// consecutive nodes) and marches up a chunk of planes.  Block row r = 0 ..
-// F2_FY + 1 is grid row y0 - 1 + r: rows 1 .. F2_FY are the tile, rows 0 and
-// F2_FY + 1 the halo whose populations 3 and 4 the tile's second step pulls.
+// Two fused steps (temporal blocking) in FP32.  A block owns FY rows of the
+// full x extent (nx = 128 KW: KW warps per row, each thread 4 consecutive
+// nodes) and marches through a chunk of planes.  Block row r = 0 .. FY + 1
+// is grid row y0 - 1 + r: rows 1 .. FY are the tile, rows 0 and FY + 1 the
+// halo whose populations 3 and 4 the tile's second step pulls.
 // Iteration i computes step n at plane i for all rows (pulled from global
 // memory, written to a ring of three shared planes) and step n + 1 at plane
 // i - 2 for the tile rows (pulled from the ring, written to global memory).
@@ -574,12 +574,16 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
 // in flight while it runs.  Every node's arithmetic is the single step's
 // (collide_node), so two fused steps equal two single steps bit for bit.
 // Step n runs from frame rsrc to rdst, step n + 1 within rdst.
-constexpr int F2_FY = 8;
-constexpr int F2_ROWS = F2_FY + 2;
+// Tile rows and resident blocks per SM by row width (measured on the
+// 128 x 128 x 256 cell: 4 rows at 3 blocks per SM beat 8 at 2 and 16 at 1).
+__host__ __device__ constexpr int f2_fy(int kw) { return kw == 1 ? 4 : 8; }
+__host__ __device__ constexpr int f2_minb(int kw) { return kw == 1 ? 3 : 1; }
+__host__ __device__ constexpr int f2_rows(int kw) { return f2_fy(kw) + 2; }
+constexpr int F2_PF = 1;                           // L2 prefetch distance in planes
 
-__host__ __device__ constexpr int fused2_threads(int kw) { return 32 * kw * F2_ROWS; }
+__host__ __device__ constexpr int fused2_threads(int kw) { return 32 * kw * f2_rows(kw); }
 __host__ __device__ constexpr size_t fused2_smem_bytes(int kw, int n_phases) {
-    return sizeof(float) * 3 * 7 * F2_ROWS * 128 * kw + sizeof(float4) * 2 * n_phases;
+    return sizeof(float) * 3 * 7 * f2_rows(kw) * 128 * kw + (sizeof(float4) + sizeof(float2)) * n_phases;
 }
 
 __device__ __forceinline__ float4 f4neg(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
@@ -594,16 +598,17 @@ struct Quad7 {
 };
 __device__ __forceinline__ Quad7 collide_quad(const float4& g0, const float4& g1, const float4& g2,
                                               const float4& g3, const float4& g4, const float4& g5,
-                                              const float4& g6, unsigned phw, const float4* s_sb,
-                                              float kT, float kJ) {
+                                              const float4& g6, unsigned phw, const float4* s_sa,
+                                              const float2* s_sc, float kT, float kJ) {
     Quad7 q;
     float* o = reinterpret_cast<float*>(q.o);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int ph = (phw >> (8 * k)) & 255u;
+        const float2 sc = s_sc[ph];
         const Collided c = collide_node(f4get(g0, k), f4get(g1, k), f4get(g2, k), f4get(g3, k),
-                                        f4get(g4, k), f4get(g5, k), f4get(g6, k), s_sb[2 * ph],
-                                        s_sb[2 * ph + 1], kT, kJ);
+                                        f4get(g4, k), f4get(g5, k), f4get(g6, k), s_sa[ph],
+                                        make_float4(sc.x, sc.y, 0.f, 0.f), kT, kJ);
 #pragma unroll
         for (int i = 0; i < 7; ++i) o[4 * i + k] = c.o[i];
     }
@@ -611,26 +616,33 @@ __device__ __forceinline__ Quad7 collide_quad(const float4& g0, const float4& g1
 }
 
 template <bool PERIODIC, int KW>
-__global__ void __launch_bounds__(32 * KW * F2_ROWS, 2 / KW) fused2_kernel(const StepArgs a, int zchunk) {
+__global__ void __launch_bounds__(fused2_threads(KW), f2_minb(KW)) fused2_kernel(const StepArgs a, int zchunk) {
+    constexpr int FY = f2_fy(KW), F2_ROWS = f2_rows(KW);
     constexpr int NXB = 128 * KW;                  // nodes per row (= nx)
     constexpr int RR = F2_ROWS * NXB;              // floats per population of a ring plane
     constexpr int RS = 7 * RR;                     // floats per ring plane
     extern __shared__ float4 smem4[];
     float* fn = reinterpret_cast<float*>(smem4);   // [3][7][F2_ROWS][NXB]
-    float4* s_sb = reinterpret_cast<float4*>(fn + 3 * RS);
+    // S_b per phase split into (xx, yy, zz, yz) and (xz, xy) tables: up to
+    // 8 (16) distinct phases in a warp read one 128-byte wavefront
+    float4* s_sa = reinterpret_cast<float4*>(fn + 3 * RS);
+    float2* s_sc = reinterpret_cast<float2*>(s_sa + a.n_phases);
     const int tid = threadIdx.x;
-    for (int i = tid; i < 2 * a.n_phases; i += 32 * KW * F2_ROWS) s_sb[i] = a.sb[i];
+    for (int i = tid; i < a.n_phases; i += 32 * KW * F2_ROWS) {
+        s_sa[i] = a.sb[2 * i];
+        s_sc[i] = make_float2(a.sb[2 * i + 1].x, a.sb[2 * i + 1].y);
+    }
 
     const int lane = tid & 31;
     const int r = tid / (32 * KW);                 // block row (warp-uniform)
     const int x = 4 * (tid - r * 32 * KW);         // first of this thread's 4 nodes
     const int ny = a.ny, nz = a.nz, pitch = a.pitch;
-    const int y0 = blockIdx.x * F2_FY;
+    const int y0 = blockIdx.x * FY;
     int y = y0 - 1 + r;
     bool row_in = true;
     if (PERIODIC) y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
     else row_in = y >= 0 && y < ny;
-    const bool tile_row = r >= 1 && r <= F2_FY;
+    const bool tile_row = r >= 1 && r <= FY;
     const bool ylo = y == 0, yhi = y == ny - 1;
     const int xm = x == 0 ? NXB - 1 : x - 1;       // x - 1 of node x, wrapped
     const int xp = x + 4 == NXB ? 0 : x + 4;       // x + 1 of node x + 3, wrapped
@@ -647,12 +659,53 @@ __global__ void __launch_bounds__(32 * KW * F2_ROWS, 2 / KW) fused2_kernel(const
     float* __restrict__ dst = reinterpret_cast<float*>(a.dst);
     const int z0 = blockIdx.y * zchunk;
     const int z1 = min(z0 + zchunk, nz);
-    __syncthreads();                               // s_sb is ready
+    // chunks march alternately up and down, so that two neighbouring chunks
+    // read the planes at their common boundary at about the same time
+    const bool up = (blockIdx.y & 1) == 0;
+    const int dz = up ? 1 : -1;
+    __syncthreads();                               // the S_b tables are ready
 
-    unsigned phA = 0u, phB = 0u;                   // phase words of planes i - 2 and i - 1
-    for (int i = z0 - 1; i <= z1 + 1; ++i) {
+    // L2 prefetch, F2_PF planes ahead: lanes 0..7 of each warp each fetch one
+    // population's row segment (what the first step at that plane pulls) or
+    // the phase bytes, by one bulk prefetch
+    const char* pf_base = nullptr;
+    long long pf_plane = 4 * PL;                   // bytes per plane
+    unsigned pf_bytes = 512;
+    {
+        const long long xw = x - 4 * lane;         // this warp's first node
+        const long long off = lane == 0 ? yrow : lane == 1 ? P + yrow : lane == 2 ? 2 * P + yrow
+                            : lane == 3 ? o3 : lane == 4 ? o4 : lane == 5 ? 5 * P - PL + yrow
+                            : 6 * P + PL + yrow;
+        pf_base = reinterpret_cast<const char*>(src + off + xw);
+        if (lane == 7) {
+            pf_base = reinterpret_cast<const char*>(a.phase + yrow + xw);
+            pf_plane = PL;
+            pf_bytes = 128;
+        }
+    }
+    const bool pf_lane = row_in && lane < 8;
+    unsigned phA = 0u, phB = 0u;                   // phase words of planes i - 2dz and i - dz
+    // ring slot of plane p: p mod 3.  si tracks plane i; planes j, j - 1 and
+    // j + 1 then sit in slots si + 1, si, si + 2 (up) or si + 2, si + 1, si
+    // (down), mod 3.
+    int si = ((up ? z0 - 1 : z1) + 3) % 3;
+    for (int t = 0; t < z1 - z0 + 3; ++t) {
+        const int i = up ? z0 - 1 + t : z1 - t;    // step n at plane i
+        const int j = i - 2 * dz;                  // step n + 1 at plane j
+        const int s_inc = si == 2 ? 0 : si + 1, s_dec = si == 0 ? 2 : si - 1;
+        const int sj = up ? s_inc : s_dec;
+        const int sjm = up ? si : s_inc;           // plane j - 1
+        const int sjp = up ? s_dec : si;           // plane j + 1
+        {
+            const int ip = i + F2_PF * dz;
+            // the wall planes pull their own populations: nothing to prefetch there
+            if (pf_lane && ip >= z0 - 1 && ip <= z1 && ip >= 0 && ip < nz && (lane != 5 || ip > 0) &&
+                (lane != 6 || ip < nz - 1))
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(pf_base + ip * pf_plane),
+                             "r"(pf_bytes) : "memory");
+        }
         // ---- loads of step n at plane i (warp-uniform condition) ----
-        const bool first = i <= z1 && i >= 0 && i < nz && row_in;
+        const bool first = i >= z0 - 1 && i <= z1 && i >= 0 && i < nz && row_in;
         float4 q0, q1, q2, q3, q4, q5, q6;
         unsigned phC = 0u;
         if (first) {
@@ -667,12 +720,11 @@ __global__ void __launch_bounds__(32 * KW * F2_ROWS, 2 / KW) fused2_kernel(const
             q6 = __ldg(reinterpret_cast<const float4*>(s + (i < nz - 1 ? 6 * P + PL : 5 * P) + yrow + x));
             phC = __ldg(reinterpret_cast<const unsigned*>(a.phase + (long long)i * PL + yrow + x));
         }
-        // ---- step n + 1 at plane j = i - 2, tile rows ----
-        const int j = i - 2;
+        // ---- step n + 1 at plane j, tile rows ----
         if (tile_row && j >= z0 && j < z1) {
-            const float* fs = fn + (j % 3) * RS + r * NXB + x;
-            const float* fb = fn + ((j + 2) % 3) * RS + r * NXB + x;   // plane j - 1
-            const float* fa = fn + ((j + 1) % 3) * RS + r * NXB + x;   // plane j + 1
+            const float* fs = fn + sj * RS + r * NXB + x;
+            const float* fb = fn + sjm * RS + r * NXB + x;
+            const float* fa = fn + sjp * RS + r * NXB + x;
             const float4 g0 = *reinterpret_cast<const float4*>(fs);
             const float4 c1 = *reinterpret_cast<const float4*>(fs + RR);
             const float4 c2 = *reinterpret_cast<const float4*>(fs + 2 * RR);
@@ -684,16 +736,17 @@ __global__ void __launch_bounds__(32 * KW * F2_ROWS, 2 / KW) fused2_kernel(const
                                     : f4neg(*reinterpret_cast<const float4*>(fs + 6 * RR));
             const float4 g6 = j < nz - 1 ? *reinterpret_cast<const float4*>(fa + 6 * RR)
                                          : f4neg(*reinterpret_cast<const float4*>(fs + 5 * RR));
-            // x-neighbours within the ring row (the row holds the full x extent)
-            const float* row1 = fn + (j % 3) * RS + RR + r * NXB;
-            const float* row2 = row1 + RR;
-            float l1 = row1[xm], r2 = row2[xp];
+            // x-neighbours: from the next lane, across warps from the ring row
+            float l1 = __shfl_sync(kFull, c1.w, (lane + 31) & 31);
+            float r2 = __shfl_sync(kFull, c2.x, (lane + 1) & 31);
+            if (KW > 1 && lane == 0) l1 = fs[RR - x + xm];
+            if (KW > 1 && lane == 31) r2 = fs[2 * RR - x + xp];
             if (!PERIODIC && x == 0) l1 = c2.x;                 // Eq. 24 at x = 0
             if (!PERIODIC && x + 4 == NXB) r2 = c1.w;           // and at x = nx - 1
             const float4 g1 = make_float4(l1, c1.x, c1.y, c1.z);
             const float4 g2 = make_float4(c2.y, c2.z, c2.w, r2);
             const PlaneK pk = plane_consts(a.rdst, a.rdst, j, nz, a.eps_hot, a.eps_cold);
-            const Quad7 o = collide_quad(g0, g1, g2, g3, g4, g5, g6, phA, s_sb, pk.kT, pk.kJ);
+            const Quad7 o = collide_quad(g0, g1, g2, g3, g4, g5, g6, phA, s_sa, s_sc, pk.kT, pk.kJ);
             float* d = dst + (long long)j * PL + yrow + x;
 #pragma unroll
             for (int p = 0; p < 7; ++p) *reinterpret_cast<float4*>(d + p * P) = o.o[p];
@@ -711,8 +764,8 @@ __global__ void __launch_bounds__(32 * KW * F2_ROWS, 2 / KW) fused2_kernel(const
             const float4 g1 = make_float4(l1, q1.x, q1.y, q1.z);
             const float4 g2 = make_float4(q2.y, q2.z, q2.w, r2);
             const PlaneK pk = plane_consts(a.rsrc, a.rdst, i, nz, a.eps_hot, a.eps_cold);
-            const Quad7 o = collide_quad(q0, g1, g2, q3, q4, q5, q6, phC, s_sb, pk.kT, pk.kJ);
-            float* w = fn + (i % 3) * RS + r * NXB + x;
+            const Quad7 o = collide_quad(q0, g1, g2, q3, q4, q5, q6, phC, s_sa, s_sc, pk.kT, pk.kJ);
+            float* w = fn + si * RS + r * NXB + x;
             if (tile_row) {
 #pragma unroll
                 for (int p = 0; p < 7; ++p) *reinterpret_cast<float4*>(w + p * RR) = o.o[p];
@@ -724,6 +777,7 @@ __global__ void __launch_bounds__(32 * KW * F2_ROWS, 2 / KW) fused2_kernel(const
         }
         phA = phB;
         phB = phC;
+        si = up ? s_inc : s_dec;
         __syncthreads();
     }
 }
@@ -731,7 +785,7 @@ __global__ void __launch_bounds__(32 * KW * F2_ROWS, 2 / KW) fused2_kernel(const
 // The single-solve step: blockIdx.x is the block within the plane,
 // blockIdx.y the plane.
 template <int FMT, bool PERIODIC, bool CHECK, bool RAGGED>
-__global__ void __launch_bounds__(kThreads, CHECK ? 1 : 4) step_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) step_kernel(const StepArgs a) {
     step_body<FMT, PERIODIC, CHECK, RAGGED, kThreads>(a, blockIdx.x, blockIdx.y, a.rseed);
 }
 

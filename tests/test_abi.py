@@ -43,7 +43,7 @@ def test_default_opts(lib):
     assert (o.t_hot, o.t_cold, o.tau_max, o.tol) == (1.0, 0.0, 1.5, 1e-8)
     assert o.max_iters == 50_000_000 and o.check_every == 100
     assert o.storage == lbm.LBM_STORE_F32 and not o.t_init and not o.stream
-    assert o.fuse == 0 and o.host_loop == 0
+    assert o.fuse == 1 and o.host_loop == 0
     assert ctypes.sizeof(lbm.lbm_solve_opts) == 88
     assert ctypes.sizeof(lbm.lbm_solve_info) == 56
 
