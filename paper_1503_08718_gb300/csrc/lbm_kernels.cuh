@@ -575,15 +575,19 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
 // (collide_node), so two fused steps equal two single steps bit for bit.
 // Step n runs from frame rsrc to rdst, step n + 1 within rdst.
 // Tile rows and resident blocks per SM by row width (measured on the
-// 128 x 128 x 256 cell: 4 rows at 3 blocks per SM beat 8 at 2 and 16 at 1).
-__host__ __device__ constexpr int f2_fy(int kw) { return kw == 1 ? 4 : 8; }
-__host__ __device__ constexpr int f2_minb(int kw) { return kw == 1 ? 3 : 1; }
+// 128 x 128 x 256 cell: 8 rows at 2 blocks per SM beat 4 at 3 and 16 at 1).
+__host__ __device__ constexpr int f2_fy(int kw) { return kw == 1 ? 8 : 8; }
+__host__ __device__ constexpr int f2_minb(int kw) { return kw == 1 ? 2 : 1; }
 __host__ __device__ constexpr int f2_rows(int kw) { return f2_fy(kw) + 2; }
 constexpr int F2_PF = 1;                           // L2 prefetch distance in planes
 
 __host__ __device__ constexpr int fused2_threads(int kw) { return 32 * kw * f2_rows(kw); }
+// A ring plane keeps, per population, only the rows the second step reads:
+// the FY tile rows for 0, 1, 2, 5, 6; block rows 0 .. FY for 3 and 1 .. FY + 1
+// for 4 (the halo row and, at an adiabatic face, the own row's bounce-back).
+__host__ __device__ constexpr int f2_slot_rows(int kw) { return 7 * f2_fy(kw) + 2; }
 __host__ __device__ constexpr size_t fused2_smem_bytes(int kw, int n_phases) {
-    return sizeof(float) * 3 * 7 * f2_rows(kw) * 128 * kw + (sizeof(float4) + sizeof(float2)) * n_phases;
+    return sizeof(float) * 3 * f2_slot_rows(kw) * 128 * kw + (sizeof(float4) + sizeof(float2)) * n_phases;
 }
 
 __device__ __forceinline__ float4 f4neg(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
@@ -619,10 +623,13 @@ template <bool PERIODIC, int KW>
 __global__ void __launch_bounds__(fused2_threads(KW), f2_minb(KW)) fused2_kernel(const StepArgs a, int zchunk) {
     constexpr int FY = f2_fy(KW), F2_ROWS = f2_rows(KW);
     constexpr int NXB = 128 * KW;                  // nodes per row (= nx)
-    constexpr int RR = F2_ROWS * NXB;              // floats per population of a ring plane
-    constexpr int RS = 7 * RR;                     // floats per ring plane
+    constexpr int RS = f2_slot_rows(KW) * NXB;     // floats per ring plane
+    // population offsets within a ring plane, for block row r at row r - 1:
+    // population 3 keeps block rows 0 .. FY, population 4 rows 1 .. FY + 1
+    constexpr int Q1 = FY * NXB, Q2 = 2 * FY * NXB, Q5 = 3 * FY * NXB, Q6 = 4 * FY * NXB;
+    constexpr int Q3 = (5 * FY + 1) * NXB, Q4 = (6 * FY + 1) * NXB;
     extern __shared__ float4 smem4[];
-    float* fn = reinterpret_cast<float*>(smem4);   // [3][7][F2_ROWS][NXB]
+    float* fn = reinterpret_cast<float*>(smem4);   // [3][f2_slot_rows][NXB]
     // S_b per phase split into (xx, yy, zz, yz) and (xz, xy) tables: up to
     // 8 (16) distinct phases in a warp read one 128-byte wavefront
     float4* s_sa = reinterpret_cast<float4*>(fn + 3 * RS);
@@ -663,7 +670,17 @@ __global__ void __launch_bounds__(fused2_threads(KW), f2_minb(KW)) fused2_kernel
     // read the planes at their common boundary at about the same time
     const bool up = (blockIdx.y & 1) == 0;
     const int dz = up ? 1 : -1;
-    __syncthreads();                               // the S_b tables are ready
+    // frame constants of the two planes an iteration updates, computed one
+    // iteration ahead by thread 0 into a double buffer: [t & 1][step n, n + 1]
+    __shared__ PlaneK s_kc[2][2];
+    auto plane_pair = [&](int t, PlaneK* out) {
+        const int ii = up ? z0 - 1 + t : z1 - t;
+        const int jj = ii - 2 * dz;
+        out[0] = plane_consts(a.rsrc, a.rdst, min(max(ii, 0), nz - 1), nz, a.eps_hot, a.eps_cold);
+        out[1] = plane_consts(a.rdst, a.rdst, min(max(jj, 0), nz - 1), nz, a.eps_hot, a.eps_cold);
+    };
+    if (tid == 0) plane_pair(0, s_kc[0]);
+    __syncthreads();                               // the S_b tables and s_kc[0] are ready
 
     // L2 prefetch, F2_PF planes ahead: lanes 0..7 of each warp each fetch one
     // population's row segment (what the first step at that plane pulls) or
@@ -696,6 +713,8 @@ __global__ void __launch_bounds__(fused2_threads(KW), f2_minb(KW)) fused2_kernel
         const int sj = up ? s_inc : s_dec;
         const int sjm = up ? si : s_inc;           // plane j - 1
         const int sjp = up ? s_dec : si;           // plane j + 1
+        const PlaneK kn = s_kc[t & 1][0], kn1 = s_kc[t & 1][1];
+        if (tid == 0) plane_pair(t + 1, s_kc[(t + 1) & 1]);   // read after this iteration's barrier
         {
             const int ip = i + F2_PF * dz;
             // the wall planes pull their own populations: nothing to prefetch there
@@ -721,32 +740,32 @@ __global__ void __launch_bounds__(fused2_threads(KW), f2_minb(KW)) fused2_kernel
             phC = __ldg(reinterpret_cast<const unsigned*>(a.phase + (long long)i * PL + yrow + x));
         }
         // ---- step n + 1 at plane j, tile rows ----
+        const int own = (r - 1) * NXB + x;          // this thread's nodes in a ring plane
         if (tile_row && j >= z0 && j < z1) {
-            const float* fs = fn + sj * RS + r * NXB + x;
-            const float* fb = fn + sjm * RS + r * NXB + x;
-            const float* fa = fn + sjp * RS + r * NXB + x;
+            const float* fs = fn + sj * RS + own;
+            const float* fb = fn + sjm * RS + own;
+            const float* fa = fn + sjp * RS + own;
             const float4 g0 = *reinterpret_cast<const float4*>(fs);
-            const float4 c1 = *reinterpret_cast<const float4*>(fs + RR);
-            const float4 c2 = *reinterpret_cast<const float4*>(fs + 2 * RR);
-            const float4 g3 = (PERIODIC || !ylo) ? *reinterpret_cast<const float4*>(fs + 3 * RR - NXB)
-                                                 : *reinterpret_cast<const float4*>(fs + 4 * RR);
-            const float4 g4 = (PERIODIC || !yhi) ? *reinterpret_cast<const float4*>(fs + 4 * RR + NXB)
-                                                 : *reinterpret_cast<const float4*>(fs + 3 * RR);
-            const float4 g5 = j > 0 ? *reinterpret_cast<const float4*>(fb + 5 * RR)
-                                    : f4neg(*reinterpret_cast<const float4*>(fs + 6 * RR));
-            const float4 g6 = j < nz - 1 ? *reinterpret_cast<const float4*>(fa + 6 * RR)
-                                         : f4neg(*reinterpret_cast<const float4*>(fs + 5 * RR));
+            const float4 c1 = *reinterpret_cast<const float4*>(fs + Q1);
+            const float4 c2 = *reinterpret_cast<const float4*>(fs + Q2);
+            const float4 g3 = (PERIODIC || !ylo) ? *reinterpret_cast<const float4*>(fs + Q3 - NXB)
+                                                 : *reinterpret_cast<const float4*>(fs + Q4);
+            const float4 g4 = (PERIODIC || !yhi) ? *reinterpret_cast<const float4*>(fs + Q4 + NXB)
+                                                 : *reinterpret_cast<const float4*>(fs + Q3);
+            const float4 g5 = j > 0 ? *reinterpret_cast<const float4*>(fb + Q5)
+                                    : f4neg(*reinterpret_cast<const float4*>(fs + Q6));
+            const float4 g6 = j < nz - 1 ? *reinterpret_cast<const float4*>(fa + Q6)
+                                         : f4neg(*reinterpret_cast<const float4*>(fs + Q5));
             // x-neighbours: from the next lane, across warps from the ring row
             float l1 = __shfl_sync(kFull, c1.w, (lane + 31) & 31);
             float r2 = __shfl_sync(kFull, c2.x, (lane + 1) & 31);
-            if (KW > 1 && lane == 0) l1 = fs[RR - x + xm];
-            if (KW > 1 && lane == 31) r2 = fs[2 * RR - x + xp];
+            if (KW > 1 && lane == 0) l1 = fs[Q1 - x + xm];
+            if (KW > 1 && lane == 31) r2 = fs[Q2 - x + xp];
             if (!PERIODIC && x == 0) l1 = c2.x;                 // Eq. 24 at x = 0
             if (!PERIODIC && x + 4 == NXB) r2 = c1.w;           // and at x = nx - 1
             const float4 g1 = make_float4(l1, c1.x, c1.y, c1.z);
             const float4 g2 = make_float4(c2.y, c2.z, c2.w, r2);
-            const PlaneK pk = plane_consts(a.rdst, a.rdst, j, nz, a.eps_hot, a.eps_cold);
-            const Quad7 o = collide_quad(g0, g1, g2, g3, g4, g5, g6, phA, s_sa, s_sc, pk.kT, pk.kJ);
+            const Quad7 o = collide_quad(g0, g1, g2, g3, g4, g5, g6, phA, s_sa, s_sc, kn1.kT, kn1.kJ);
             float* d = dst + (long long)j * PL + yrow + x;
 #pragma unroll
             for (int p = 0; p < 7; ++p) *reinterpret_cast<float4*>(d + p * P) = o.o[p];
@@ -763,16 +782,20 @@ __global__ void __launch_bounds__(fused2_threads(KW), f2_minb(KW)) fused2_kernel
             if (!PERIODIC && x + 4 == NXB) r2 = q1.w;
             const float4 g1 = make_float4(l1, q1.x, q1.y, q1.z);
             const float4 g2 = make_float4(q2.y, q2.z, q2.w, r2);
-            const PlaneK pk = plane_consts(a.rsrc, a.rdst, i, nz, a.eps_hot, a.eps_cold);
-            const Quad7 o = collide_quad(q0, g1, g2, q3, q4, q5, q6, phC, s_sa, s_sc, pk.kT, pk.kJ);
-            float* w = fn + si * RS + r * NXB + x;
+            const Quad7 o = collide_quad(q0, g1, g2, q3, q4, q5, q6, phC, s_sa, s_sc, kn.kT, kn.kJ);
+            float* w = fn + si * RS + own;           // block row 0 only writes population 3
             if (tile_row) {
-#pragma unroll
-                for (int p = 0; p < 7; ++p) *reinterpret_cast<float4*>(w + p * RR) = o.o[p];
+                *reinterpret_cast<float4*>(w) = o.o[0];
+                *reinterpret_cast<float4*>(w + Q1) = o.o[1];
+                *reinterpret_cast<float4*>(w + Q2) = o.o[2];
+                *reinterpret_cast<float4*>(w + Q3) = o.o[3];
+                *reinterpret_cast<float4*>(w + Q4) = o.o[4];
+                *reinterpret_cast<float4*>(w + Q5) = o.o[5];
+                *reinterpret_cast<float4*>(w + Q6) = o.o[6];
             } else if (r == 0) {
-                *reinterpret_cast<float4*>(w + 3 * RR) = o.o[3];
+                *reinterpret_cast<float4*>(w + Q3) = o.o[3];
             } else {
-                *reinterpret_cast<float4*>(w + 4 * RR) = o.o[4];
+                *reinterpret_cast<float4*>(w + Q4) = o.o[4];
             }
         }
         phA = phB;
