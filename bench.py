@@ -42,6 +42,10 @@ G_DEG, PHI, SEED, NMAX = 30.0, 0.45, 42, 128
 K = 100
 ITERS = 1000
 BYTES_PER_LUP = {"f32": 57, "bf16": 29, "f16": 29}   # 7 values read + 7 written + 1 B phase id
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture of this workload (profiles/fused2_kernel_braid128x128x256.md and
+# profiles/step_kernel_braid128x128x256.md); set to None when the kernel changes
+TRAFFIC = {("fused2", "f32"): 188.26e6, ("step", "f32"): 185.6e6, ("step", "bf16"): 74.5e6}
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 WORKLOAD = (f"braid {NX}x{NY}x{NZ} g=30deg phi=0.45 seed=42, dT along z, periodic laterals, "
             f"FP32 D3Q7 MRT")
@@ -121,6 +125,22 @@ def make_cell(lbm, I, device):
     lam = I.braid_tensors(G_DEG)
     S.set_tensors(lam)
     return S, lam, used, frac
+
+
+def kernel_launch_us(S, opts, stream, steps_per_launch, n=200, warm=20):
+    """Average device time of one launch of the plain step kernel (two steps
+    per launch when fused): CUDA events on the solver's stream around n
+    launches issued by lbm_advance (plus its one-thread iteration counter)."""
+    import torch
+    S.start(2, 0, opts)
+    S.advance(warm * steps_per_launch)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    S.advance(n * steps_per_launch)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1000.0 / n, n
 
 
 def time_to_keff(lbm, S, stream, iters_ref=250_000, rel=1e-4):
@@ -305,19 +325,26 @@ def run_ours(args):
     launches_per_step = (iters // K) * launches_per_interval + 2   # + permute, init
     # roofline of the dominant kernel: the fused two-step kernel in FP32 (one
     # read and one write of the state per launch: 57 B per voxel for two
-    # updates), else the single step (57 or 29 B per update).  Every launch's
-    # time in the timed region is charged to it (a lower bound).
+    # updates), else the single step (57 or 29 B per update).  Its average
+    # launch time is measured with CUDA events on the solver's stream over a
+    # run of its launches alone (lbm_advance); frac_whole_step charges every
+    # launch of the timed bench step to it instead (a lower bound).
     if pairs:
         dom_launches = args.steps * (iters // K) * pairs
         dom_bytes = BYTES_PER_LUP["f32"] * n_vox
         dominant = "fused2_kernel (2 updates per launch)"
+        dom_key = ("fused2", "f32")
     else:
         dom_launches = args.steps * iters
         dom_bytes = BYTES_PER_LUP[args.storage] * n_vox
         dominant = "step_kernel"
+        dom_key = ("step", args.storage)
     per_launch_s = (ms / 1000.0) / dom_launches
-    achieved = dom_bytes / per_launch_s / 1e9
+    achieved_step = dom_bytes / per_launch_s / 1e9
+    launch_us, n_timed = kernel_launch_us(S, opts, stream, 2 if pairs else 1)
+    achieved = dom_bytes / (launch_us * 1e-6) / 1e9
     peak, peak_kind = peaks()
+    traffic = args.traffic if args.traffic is not None else TRAFFIC.get(dom_key)
 
     # the same step with 16-bit distribution storage (FP32 collision,
     # stochastic rounding): GLUPS and the roofline at 29 B/LUP
@@ -342,10 +369,11 @@ def run_ours(args):
             torch.cuda.synchronize()
             ms16 = e0.elapsed_time(e1)
             g16 = n_vox * iters * n16 / (ms16 / 1000.0) / 1e9
-            a16 = BYTES_PER_LUP[name] * n_vox / ((ms16 / 1000.0) / (n16 * iters)) / 1e9
+            us16, _ = kernel_launch_us(S, o16, stream, 1)
+            a16 = BYTES_PER_LUP[name] * n_vox / (us16 * 1e-6) / 1e9
             variants[name] = {"value": g16, "unit": "GLUPS", "steps": n16,
                               "ms_per_step": ms16 / n16, "bytes_per_lup": BYTES_PER_LUP[name],
-                              "roofline_frac": a16 / peak,
+                              "step_kernel_us": us16, "roofline_frac": a16 / peak,
                               "k_eff_after_step": i16.k_eff,
                               "k_eff_rel_vs_f32": (i16.k_eff - info.k_eff) / info.k_eff}
 
@@ -395,9 +423,10 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (f buffers 2 x 117 MB)",
                        "parallelism": f"replicas{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": args.traffic,
+                         "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_kind, "kernel": dominant,
-                         "bytes_per_launch": dom_bytes},
+                         "bytes_per_launch": dom_bytes, "launch_us": launch_us,
+                         "launches_timed": n_timed, "frac_whole_step": achieved_step / peak},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_glups, "unit": "GLUPS",
                     "h2d_bytes_per_step": n_vox + lam.nbytes,

@@ -263,9 +263,12 @@ cudaError_t launch_step(const lbm_ctx* c, int src, bool check, Frame fr, cudaStr
 
 // Two plain FP32 steps in one launch (temporal blocking), when the layout
 // allows it: rows of 128 or 256 nodes without padding, whole tiles of rows.
+bool fused_rows(const lbm_ctx* c, int nx, int ny) {
+    return (nx == 128 || nx == 256) && c->fuse_ok[nx / 128 - 1] && ny % lbm::f2_fy(nx / 128) == 0;
+}
+
 bool fusable(const lbm_ctx* c) {
-    return c->opts.fuse && c->fmt == LBM_STORE_F32 && (c->L.NX == 128 || c->L.NX == 256) &&
-           c->fuse_ok[c->L.NX / 128 - 1] && c->L.pitch == c->L.NX && c->L.NY % lbm::f2_fy(c->L.NX / 128) == 0;
+    return c->opts.fuse && c->fmt == LBM_STORE_F32 && c->L.pitch == c->L.NX && fused_rows(c, c->L.NX, c->L.NY);
 }
 
 cudaError_t launch_pair(const lbm_ctx* c, int src, Frame fr, cudaStream_t st) {
@@ -583,12 +586,20 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
             for (int k = 0; k < 3; ++k) m = std::fmax(m, c->lambda[6 * p + k]);
         s = eps * (op.tau_max - 0.5) / m;
     }
-    // canonical layout: new axis i is old axis perm[i], Dirichlet axis last
+    // canonical layout: new axis i is old axis perm[i], Dirichlet axis last.
+    // Either order of the two lateral axes is valid (the tensors are permuted
+    // with the map); take the one whose rows the two-step kernel accepts.
     static const int perms[3][3] = {{1, 2, 0}, {2, 0, 1}, {0, 1, 2}};
     Layout L;
     for (int i = 0; i < 3; ++i) {
         L.n[i] = c->n[i];
         L.perm[i] = perms[axis][i];
+    }
+    if (op.fuse && op.storage == LBM_STORE_F32 && !fused_rows(c, c->n[L.perm[0]], c->n[L.perm[1]]) &&
+        fused_rows(c, c->n[L.perm[1]], c->n[L.perm[0]])) {
+        const int t = L.perm[0];
+        L.perm[0] = L.perm[1];
+        L.perm[1] = t;
     }
     L.NX = c->n[L.perm[0]];
     L.NY = c->n[L.perm[1]];

@@ -354,3 +354,27 @@ def test_fused_pairs_equal_single_steps_bit_for_bit(lateral, axis, shape):
     # and both follow the oracle
     ref = _oracle(phase, lam, axis, lateral, info.lattice_scale, 300)
     assert np.max(np.abs(out[0][0] - ref.temperature())) <= T_TOL
+
+
+@pytest.mark.parametrize("lateral", [0, 1])
+def test_lateral_order_chosen_for_fused_pairs(lateral):
+    """Along y the canonical rows would hold nz = 24 nodes; with fused pairs on,
+    lbm_start orders the lateral axes the other way (rows of nx = 128).  The
+    relabelling is exact in arithmetic, so both runs follow the oracle; they
+    differ from each other only by FP32 summation order."""
+    rng = np.random.default_rng(77 + lateral)
+    lam = np.stack([I.random_spd(rng) for _ in range(3)])
+    shape = (128, 20, 24)
+    phase = I.random_phase(rng, *shape, 3)
+    res = []
+    for fuse in (1, 0):
+        S = lbm.Solver(*shape)
+        S.set_geometry(phase, 3)
+        S.set_tensors(lam)
+        info = S.solve(1, lateral, S.opts(tol=0.0, max_iters=300, fuse=fuse))
+        res.append((S.temperature(), info.k_eff, info.lattice_scale))
+    ref = _oracle(phase, lam, 1, lateral, res[0][2], 300)
+    for T, k, _ in res:
+        assert np.max(np.abs(T - ref.temperature())) <= T_TOL
+        assert k == pytest.approx(ref.k_eff()[0], rel=K_TOL)
+    assert np.max(np.abs(res[0][0] - res[1][0])) <= 1e-6
