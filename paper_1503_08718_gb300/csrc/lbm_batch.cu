@@ -53,7 +53,7 @@ struct BatchCtl {
 // argument block per (buffer parity, reference frame), so a block only
 // searches the prefix and then reads its arguments through the cache.
 template <int FMT, bool PERIODIC, bool CHECK, int THREADS>
-__global__ void __launch_bounds__(THREADS, CHECK ? 1 : 1024 / THREADS)
+__global__ void __launch_bounds__(THREADS, (CHECK && FMT != 0) ? 512 / THREADS : 1024 / THREADS)
 batch_step_kernel(const StepArgs* __restrict__ args, const int* __restrict__ prefix,
                   const int* __restrict__ order, const BatchCtl* __restrict__ bctl, int variant,
                   unsigned rseed) {

@@ -808,7 +808,7 @@ __global__ void __launch_bounds__(fused2_threads(KW), f2_minb(KW)) fused2_kernel
 // The single-solve step: blockIdx.x is the block within the plane,
 // blockIdx.y the plane.
 template <int FMT, bool PERIODIC, bool CHECK, bool RAGGED>
-__global__ void __launch_bounds__(kThreads, 4) step_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(kThreads, (CHECK && FMT != 0) ? 2 : 4) step_kernel(const StepArgs a) {
     step_body<FMT, PERIODIC, CHECK, RAGGED, kThreads>(a, blockIdx.x, blockIdx.y, a.rseed);
 }
 
