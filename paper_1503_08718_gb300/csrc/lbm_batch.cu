@@ -69,7 +69,11 @@ batch_step_kernel(const StepArgs* __restrict__ args, const int* __restrict__ pre
     const StepArgs& a = args[order[lo] * kVariants + variant];
     const int local = b - prefix[lo];
     const int z = local / a.blocks_per_plane;
-    lbm::step_body<FMT, PERIODIC, CHECK, true, THREADS>(a, local - z * a.blocks_per_plane, z, rseed);
+    // rows without padding skip the ragged-row handling (block-uniform branch)
+    if (a.nx == a.pitch)
+        lbm::step_body<FMT, PERIODIC, CHECK, false, THREADS>(a, local - z * a.blocks_per_plane, z, rseed);
+    else
+        lbm::step_body<FMT, PERIODIC, CHECK, true, THREADS>(a, local - z * a.blocks_per_plane, z, rseed);
 }
 
 // After a check: keep the solves that are not done, rebuild the prefix and
