@@ -25,6 +25,7 @@ struct lbm_ctx {
     int device = 0;
     int n_sm = 152;                        // multiprocessors of the device
     bool fuse_ok[2] = {false, false};      // fused kernel usable for rows of 128, 256 nodes
+    int pair_flip = 0;                     // chunk direction of the next lbm_advance pair
     cudaStream_t own_stream = nullptr;     // context stream (non-blocking)
     cudaStream_t cap_stream = nullptr;     // private stream used only for graph capture
     bool poisoned = false;
@@ -271,7 +272,9 @@ bool fusable(const lbm_ctx* c) {
     return c->opts.fuse && c->fmt == LBM_STORE_F32 && c->L.pitch == c->L.NX && fused_rows(c, c->L.NX, c->L.NY);
 }
 
-cudaError_t launch_pair(const lbm_ctx* c, int src, Frame fr, cudaStream_t st) {
+// flip: 1 reverses every chunk's marching direction; alternate launches
+// flip, so that each chunk starts on the planes it wrote last (still in L2).
+cudaError_t launch_pair(const lbm_ctx* c, int src, Frame fr, int flip, cudaStream_t st) {
     const lbm::StepArgs a = step_args(c, src, fr);
     const int kw = c->L.NX / 128;
     const int bxy = c->L.NY / lbm::f2_fy(kw);
@@ -292,11 +295,11 @@ cudaError_t launch_pair(const lbm_ctx* c, int src, Frame fr, cudaStream_t st) {
     const size_t smem = lbm::fused2_smem_bytes(kw, c->n_phases);
     const bool per = c->lateral == LBM_LATERAL_PERIODIC;
     if (kw == 1) {
-        if (per) lbm::fused2_kernel<true, 1><<<grid, threads, smem, st>>>(a, zchunk);
-        else lbm::fused2_kernel<false, 1><<<grid, threads, smem, st>>>(a, zchunk);
+        if (per) lbm::fused2_kernel<true, 1><<<grid, threads, smem, st>>>(a, zchunk, flip);
+        else lbm::fused2_kernel<false, 1><<<grid, threads, smem, st>>>(a, zchunk, flip);
     } else {
-        if (per) lbm::fused2_kernel<true, 2><<<grid, threads, smem, st>>>(a, zchunk);
-        else lbm::fused2_kernel<false, 2><<<grid, threads, smem, st>>>(a, zchunk);
+        if (per) lbm::fused2_kernel<true, 2><<<grid, threads, smem, st>>>(a, zchunk, flip);
+        else lbm::fused2_kernel<false, 2><<<grid, threads, smem, st>>>(a, zchunk, flip);
     }
     return cudaGetLastError();
 }
@@ -414,7 +417,7 @@ lbm_status build_graph(lbm_ctx* c, int parity) {
         e = launch_step(c, src, false, kAB, c->cap_stream, cl);
         src ^= 1;
         for (int i = 0; i < pl.pairs && e == cudaSuccess; ++i, k += 2) {
-            e = launch_pair(c, src, kBB, c->cap_stream);
+            e = launch_pair(c, src, kBB, i & 1, c->cap_stream);
             src ^= 1;
         }
         for (int i = 0; i < pl.singles && e == cudaSuccess; ++i) {
@@ -735,7 +738,8 @@ lbm_status lbm_advance(lbm_ctx* c, int64_t n_steps) {
     int64_t k = 0;
     if (fusable(c)) {
         for (; k + 2 <= n_steps; k += 2) {
-            CUDA_TRY(c, launch_pair(c, c->cur, kAA, c->stream));
+            CUDA_TRY(c, launch_pair(c, c->cur, kAA, c->pair_flip, c->stream));
+            c->pair_flip ^= 1;
             c->cur ^= 1;
         }
     }
@@ -793,7 +797,7 @@ lbm_status lbm_run(lbm_ctx* c, lbm_solve_info* info) {
             CUDA_TRY(c, launch_step(c, c->cur, false, kAB, c->stream, cl));
             c->cur ^= 1;
             for (int i = 0; i < pl.pairs; ++i, k += 2) {
-                CUDA_TRY(c, launch_pair(c, c->cur, kBB, c->stream));
+                CUDA_TRY(c, launch_pair(c, c->cur, kBB, i & 1, c->stream));
                 c->cur ^= 1;
             }
             for (int i = 0; i < pl.singles; ++i) {

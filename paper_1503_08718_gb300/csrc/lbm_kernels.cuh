@@ -620,7 +620,7 @@ __device__ __forceinline__ Quad7 collide_quad(const float4& g0, const float4& g1
 }
 
 template <bool PERIODIC, int KW>
-__global__ void __launch_bounds__(fused2_threads(KW), f2_minb(KW)) fused2_kernel(const StepArgs a, int zchunk) {
+__global__ void __launch_bounds__(fused2_threads(KW), f2_minb(KW)) fused2_kernel(const StepArgs a, int zchunk, int flip) {
     constexpr int FY = f2_fy(KW), F2_ROWS = f2_rows(KW);
     constexpr int NXB = 128 * KW;                  // nodes per row (= nx)
     constexpr int RS = f2_slot_rows(KW) * NXB;     // floats per ring plane
@@ -667,8 +667,10 @@ __global__ void __launch_bounds__(fused2_threads(KW), f2_minb(KW)) fused2_kernel
     const int z0 = blockIdx.y * zchunk;
     const int z1 = min(z0 + zchunk, nz);
     // chunks march alternately up and down, so that two neighbouring chunks
-    // read the planes at their common boundary at about the same time
-    const bool up = (blockIdx.y & 1) == 0;
+    // read the planes at their common boundary at about the same time; flip
+    // reverses all of them (consecutive launches alternate, so a chunk starts
+    // on the planes it wrote last)
+    const bool up = ((blockIdx.y & 1) == 0) == (flip == 0);
     const int dz = up ? 1 : -1;
     // frame constants of the two planes an iteration updates, computed one
     // iteration ahead by thread 0 into a double buffer: [t & 1][step n, n + 1]
