@@ -109,6 +109,28 @@ void lbm_default_opts(lbm_solve_opts* o);
  * Sizes must be >= 2 and nx*ny*nz < 2^31.  *out receives the context. */
 lbm_status lbm_create(int nx, int ny, int nz, int cuda_device, lbm_ctx** out);
 
+/* Device bytes a context for an nx*ny*nz cell needs when all of its device
+ * memory comes from the caller (lbm_create_with_workspace): the cell's
+ * buffers, one solve along any axis with the given storage (lbm_storage) and
+ * up to 255 phases, and the voxeliser's scratch.  0 for invalid sizes or
+ * storage.  Host-only: needs no GPU. */
+size_t lbm_workspace_bytes(int nx, int ny, int nz, int storage);
+
+/* Like lbm_create, but every device buffer of the context is carved from the
+ * caller's block dev_ptr[0 .. bytes): for callers whose device memory belongs
+ * to another allocator (a framework's caching pool, e.g. a torch tensor) or
+ * to a fixed budget.  dev_ptr must be device memory of cuda_device, 256-byte
+ * aligned, and stay valid and untouched by the caller until lbm_destroy,
+ * which does not free it.  bytes >= lbm_workspace_bytes(nx, ny, nz, storage)
+ * holds every solve with that storage; a smaller block fails at lbm_start of
+ * a solve that does not fit (LBM_ERR_OUT_OF_MEMORY).  lbm_set_geometry_braid
+ * then keeps its scratch in the block too (n_max <= 4096).  The context still
+ * creates its streams, events and CUDA graphs and a small pinned host block.
+ * Errors: LBM_ERR_INVALID_ARG for bad sizes, a null, misaligned or non-device
+ * pointer, or bytes below what the cell's own buffers need. */
+lbm_status lbm_create_with_workspace(int nx, int ny, int nz, int cuda_device, void* dev_ptr, size_t bytes,
+                                     lbm_ctx** out);
+
 /* Voxel phase map (step-wise material description, Sections 3.2 and 5).
  * phase: host, nx*ny*nz uint8 phase ids, each < n_phases; 1 <= n_phases <= 255.
  * Copied to the device.  Invalidates any solve state. */

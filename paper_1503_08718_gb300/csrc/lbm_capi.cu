@@ -7,7 +7,9 @@
 // per-voxel work runs in the kernels of lbm_kernels.cuh.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -26,6 +28,11 @@ struct lbm_ctx {
     int n_sm = 152;                        // multiprocessors of the device
     bool fuse_ok[2] = {false, false};      // fused kernel usable for rows of 128, 256 nodes
     int pair_flip = 0;                     // chunk direction of the next lbm_advance pair
+    char* ws = nullptr;                    // caller's device workspace (nullptr: own allocations)
+    size_t ws_bytes = 0;
+    size_t ws_static = 0;                  // end of the part carved at creation
+    double2* d_vox_anchor = nullptr;       // voxeliser scratch inside the workspace
+    unsigned long long* d_vox_hist = nullptr;
     cudaStream_t own_stream = nullptr;     // context stream (non-blocking)
     cudaStream_t cap_stream = nullptr;     // private stream used only for graph capture
     bool poisoned = false;
@@ -328,6 +335,33 @@ Closing interval_closing(const lbm_ctx* c) {
     return cl;
 }
 
+// ---- workspace layout (lbm_create_with_workspace) ----
+// Every device buffer of such a context is carved, 256-byte aligned and in a
+// fixed order, from the caller's block: the creation-time part first, then,
+// at each lbm_start, the buffers of that solve.  lbm_workspace_bytes adds
+// up the same sizes.
+constexpr size_t kWsAlign = 256;
+constexpr int kWsYarns = 4096;             // voxeliser scratch for up to this many yarns
+size_t ws_round(size_t x) { return (x + kWsAlign - 1) & ~(kWsAlign - 1); }
+
+size_t ws_static_bytes(long long N) {
+    return ws_round((size_t)N) + ws_round(sizeof(float) * (size_t)N) + ws_round(sizeof(Ctl)) +
+           ws_round(sizeof(double) * 4 * kHistCap) + ws_round(sizeof(double2) * kWsYarns) +
+           ws_round(sizeof(unsigned long long) * (kWsYarns + 1));
+}
+
+// the buffers lbm_start carves for a canonical NX x NY x NZ solve
+size_t ws_solve_bytes(int NX, int NY, int NZ, int storage) {
+    const int V = storage == LBM_STORE_F32 ? 4 : 8;
+    const size_t esize = storage == LBM_STORE_F32 ? 4 : 2;
+    const size_t pitch = (size_t)((NX + V - 1) / V * V);
+    const size_t cells = pitch * NY * NZ;
+    const size_t bpp = ((pitch / V) * NY + lbm::kThreads - 1) / lbm::kThreads;
+    return 2 * ws_round(7 * cells * esize) + ws_round(cells) + ws_round(sizeof(float) * cells) +
+           ws_round(sizeof(float) * 5 * NZ) + ws_round(sizeof(int) * NZ) + ws_round(sizeof(float4) * 2 * 255) +
+           ws_round(sizeof(double) * 4 * NZ * bpp) + ws_round(sizeof(double) * 3 * NZ);
+}
+
 template <typename T>
 lbm_status ensure(lbm_ctx* c, T** p, size_t count, size_t* cap) {
     if (*p && *cap >= count) return LBM_OK;
@@ -342,6 +376,22 @@ lbm_status ensure(lbm_ctx* c, T** p, size_t count, size_t* cap) {
                     sizeof(T) * count, cudaGetErrorString(e));
     }
     *cap = count;
+    return LBM_OK;
+}
+
+// A solve's buffer: the context's own allocation, or the next piece of the
+// caller's workspace (*cursor advances; a solve that does not fit fails).
+template <typename T>
+lbm_status solve_buf(lbm_ctx* c, size_t* cursor, T** p, size_t count, size_t* cap) {
+    if (!c->ws) return ensure(c, p, count, cap);
+    const size_t off = ws_round(*cursor);
+    if (off + sizeof(T) * count > c->ws_bytes)
+        return fail(c, LBM_ERR_OUT_OF_MEMORY,
+                    "the workspace (%zu bytes) is too small for this solve; lbm_workspace_bytes gives "
+                    "the size for this cell and storage", c->ws_bytes);
+    *p = reinterpret_cast<T*>(c->ws + off);
+    *cap = count;
+    *cursor = off + sizeof(T) * count;
     return LBM_OK;
 }
 
@@ -468,7 +518,11 @@ void lbm_default_opts(lbm_solve_opts* o) {
     o->stream = nullptr;
 }
 
-lbm_status lbm_create(int nx, int ny, int nz, int cuda_device, lbm_ctx** out) {
+namespace {
+
+// Creation shared by lbm_create (ws == nullptr: own allocations) and
+// lbm_create_with_workspace (every device buffer carved from ws).
+lbm_status create_ctx(int nx, int ny, int nz, int cuda_device, char* ws, size_t ws_bytes, lbm_ctx** out) {
     if (!out) return LBM_ERR_INVALID_ARG;
     *out = nullptr;
     if (nx < 2 || ny < 2 || nz < 2) return LBM_ERR_INVALID_ARG;
@@ -486,13 +540,31 @@ lbm_status lbm_create(int nx, int ny, int nz, int cuda_device, lbm_ctx** out) {
     c->n[2] = nz;
     c->device = cuda_device;
     lbm_default_opts(&c->opts);
-    bool ok = cudaSetDevice(cuda_device) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) == cudaSuccess &&
+    bool ok = cudaSetDevice(cuda_device) == cudaSuccess;
+    if (ok && ws) {
+        size_t off = 0;
+        auto carve = [&](size_t bytes) {
+            char* p = ws + off;
+            off = ws_round(off + bytes);
+            return p;
+        };
+        c->ws = ws;
+        c->ws_bytes = ws_bytes;
+        c->d_phase = reinterpret_cast<uint8_t*>(carve((size_t)N));
+        c->d_T = reinterpret_cast<float*>(carve(sizeof(float) * (size_t)N));
+        c->d_ctl = reinterpret_cast<Ctl*>(carve(sizeof(Ctl)));
+        c->d_hist = reinterpret_cast<double*>(carve(sizeof(double) * 4 * kHistCap));
+        c->d_vox_anchor = reinterpret_cast<double2*>(carve(sizeof(double2) * kWsYarns));
+        c->d_vox_hist = reinterpret_cast<unsigned long long*>(carve(sizeof(unsigned long long) * (kWsYarns + 1)));
+        c->ws_static = off;
+    } else if (ok) {
+        ok = cudaMalloc((void**)&c->d_phase, (size_t)N) == cudaSuccess &&
+             cudaMalloc((void**)&c->d_T, sizeof(float) * (size_t)N) == cudaSuccess &&
+             cudaMalloc((void**)&c->d_ctl, sizeof(Ctl)) == cudaSuccess &&
+             cudaMalloc((void**)&c->d_hist, sizeof(double) * 4 * kHistCap) == cudaSuccess;
+    }
+    ok = ok && cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaMalloc((void**)&c->d_phase, (size_t)N) == cudaSuccess &&
-              cudaMalloc((void**)&c->d_T, sizeof(float) * (size_t)N) == cudaSuccess &&
-              cudaMalloc((void**)&c->d_ctl, sizeof(Ctl)) == cudaSuccess &&
-              cudaMalloc((void**)&c->d_hist, sizeof(double) * 4 * kHistCap) == cudaSuccess &&
               cudaMallocHost((void**)&c->h_ctl, sizeof(Ctl)) == cudaSuccess &&
               cudaEventCreate(&c->ev0) == cudaSuccess && cudaEventCreate(&c->ev1) == cudaSuccess &&
               cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, cuda_device) == cudaSuccess;
@@ -519,6 +591,42 @@ lbm_status lbm_create(int nx, int ny, int nz, int cuda_device, lbm_ctx** out) {
     std::memset(c->h_ctl, 0, sizeof(Ctl));
     *out = c;
     return LBM_OK;
+}
+
+}  // namespace
+
+lbm_status lbm_create(int nx, int ny, int nz, int cuda_device, lbm_ctx** out) {
+    return create_ctx(nx, ny, nz, cuda_device, nullptr, 0, out);
+}
+
+size_t lbm_workspace_bytes(int nx, int ny, int nz, int storage) {
+    if (nx < 2 || ny < 2 || nz < 2 || (long long)nx * ny * nz >= (1LL << 31)) return 0;
+    if (storage != LBM_STORE_F32 && storage != LBM_STORE_BF16 && storage != LBM_STORE_F16) return 0;
+    const int n[3] = {nx, ny, nz};
+    size_t most = 0;
+    // any Dirichlet axis, either order of the two lateral axes
+    for (int a = 0; a < 3; ++a)
+        for (int o = 0; o < 2; ++o) {
+            const int b = (a + 1 + o) % 3, d = (a + 2 - o) % 3;
+            most = std::max(most, ws_solve_bytes(n[b], n[d], n[a], storage));
+        }
+    return ws_static_bytes((long long)nx * ny * nz) + most;
+}
+
+lbm_status lbm_create_with_workspace(int nx, int ny, int nz, int cuda_device, void* dev_ptr, size_t bytes,
+                                     lbm_ctx** out) {
+    if (!out) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!dev_ptr || (reinterpret_cast<uintptr_t>(dev_ptr) & (kWsAlign - 1)) != 0) return LBM_ERR_INVALID_ARG;
+    if (nx < 2 || ny < 2 || nz < 2 || (long long)nx * ny * nz >= (1LL << 31)) return LBM_ERR_INVALID_ARG;
+    if (bytes < ws_static_bytes((long long)nx * ny * nz)) return LBM_ERR_INVALID_ARG;
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, dev_ptr) != cudaSuccess || pa.type != cudaMemoryTypeDevice ||
+        pa.device != cuda_device) {
+        cudaGetLastError();
+        return LBM_ERR_INVALID_ARG;
+    }
+    return create_ctx(nx, ny, nz, cuda_device, static_cast<char*>(dev_ptr), bytes, out);
 }
 
 lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* phase, int n_phases) {
@@ -631,21 +739,22 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
     // buffers
     const long long cells = (long long)L.pitch * L.NY * L.NZ;
     lbm_status st;
-    if ((st = ensure(c, &c->d_f[0], (size_t)(7 * cells) * esize, &c->cap_f[0])) != LBM_OK) return st;
-    if ((st = ensure(c, &c->d_f[1], (size_t)(7 * cells) * esize, &c->cap_f[1])) != LBM_OK) return st;
-    if ((st = ensure(c, &c->d_phase_c, (size_t)cells, &c->cap_phase_c)) != LBM_OK) return st;
-    if ((st = ensure(c, &c->d_tsnap, (size_t)cells, &c->cap_tsnap)) != LBM_OK) return st;
-    if ((st = ensure(c, &c->d_ref, (size_t)5 * L.NZ, &c->cap_ref)) != LBM_OK) return st;
-    if ((st = ensure(c, &c->d_plane_cnt, (size_t)L.NZ, &c->cap_cnt)) != LBM_OK) return st;
+    size_t cur = c->ws_static;              // workspace cursor (unused without a workspace)
+    if ((st = solve_buf(c, &cur, &c->d_f[0], (size_t)(7 * cells) * esize, &c->cap_f[0])) != LBM_OK) return st;
+    if ((st = solve_buf(c, &cur, &c->d_f[1], (size_t)(7 * cells) * esize, &c->cap_f[1])) != LBM_OK) return st;
+    if ((st = solve_buf(c, &cur, &c->d_phase_c, (size_t)cells, &c->cap_phase_c)) != LBM_OK) return st;
+    if ((st = solve_buf(c, &cur, &c->d_tsnap, (size_t)cells, &c->cap_tsnap)) != LBM_OK) return st;
+    if ((st = solve_buf(c, &cur, &c->d_ref, (size_t)5 * L.NZ, &c->cap_ref)) != LBM_OK) return st;
+    if ((st = solve_buf(c, &cur, &c->d_plane_cnt, (size_t)L.NZ, &c->cap_cnt)) != LBM_OK) return st;
     size_t cap_sb = (size_t)c->cap_sb;
-    if ((st = ensure(c, &c->d_sb, sb.size(), &cap_sb)) != LBM_OK) return st;
+    if ((st = solve_buf(c, &cur, &c->d_sb, c->ws ? (size_t)2 * 255 : sb.size(), &cap_sb)) != LBM_OK) return st;
     c->cap_sb = (int)cap_sb;
     const int quads = (L.pitch / V) * L.NY;
     c->blocks_per_plane = (quads + lbm::kThreads - 1) / lbm::kThreads;
-    if ((st = ensure(c, &c->d_part, (size_t)4 * L.NZ * c->blocks_per_plane, &c->cap_part)) != LBM_OK)
+    if ((st = solve_buf(c, &cur, &c->d_part, (size_t)4 * L.NZ * c->blocks_per_plane, &c->cap_part)) != LBM_OK)
         return st;
     size_t capQ = (size_t)c->cap_Q;
-    if ((st = ensure(c, &c->d_Q, (size_t)3 * L.NZ, &capQ)) != LBM_OK) return st;
+    if ((st = solve_buf(c, &cur, &c->d_Q, (size_t)3 * L.NZ, &capQ)) != LBM_OK) return st;
     c->cap_Q = (int)capQ;
     c->Q_host.assign(L.NZ, 0.0);
 
@@ -953,19 +1062,21 @@ void lbm_destroy(lbm_ctx* c) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_graphs(c);
-    cudaFree(c->d_f[0]);
-    cudaFree(c->d_f[1]);
-    cudaFree(c->d_phase_c);
-    cudaFree(c->d_tsnap);
-    cudaFree(c->d_ref);
-    cudaFree(c->d_sb);
-    cudaFree(c->d_part);
-    cudaFree(c->d_Q);
-    cudaFree(c->d_plane_cnt);
-    cudaFree(c->d_T);
-    cudaFree(c->d_phase);
-    cudaFree(c->d_ctl);
-    cudaFree(c->d_hist);
+    if (!c->ws) {                           // a workspace stays the caller's
+        cudaFree(c->d_f[0]);
+        cudaFree(c->d_f[1]);
+        cudaFree(c->d_phase_c);
+        cudaFree(c->d_tsnap);
+        cudaFree(c->d_ref);
+        cudaFree(c->d_sb);
+        cudaFree(c->d_part);
+        cudaFree(c->d_Q);
+        cudaFree(c->d_plane_cnt);
+        cudaFree(c->d_T);
+        cudaFree(c->d_phase);
+        cudaFree(c->d_ctl);
+        cudaFree(c->d_hist);
+    }
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
@@ -992,5 +1103,12 @@ LBM_HIDDEN void lbm__set_phase_count(lbm_ctx* c, int n_phases) {
 LBM_HIDDEN void lbm__set_error(lbm_ctx* c, const char* msg) { if (c) c->err = msg; }
 LBM_HIDDEN int lbm__poisoned(const lbm_ctx* c) { return c ? (c->poisoned ? 1 : 0) : 1; }
 LBM_HIDDEN void lbm__poison(lbm_ctx* c) { if (c) c->poisoned = true; }
+// Voxeliser scratch inside a workspace (returns 0 for a context without one).
+LBM_HIDDEN int lbm__voxel_scratch(lbm_ctx* c, int n_max, double2** anchors, unsigned long long** hist) {
+    if (!c || !c->ws || n_max > kWsYarns) return 0;
+    *anchors = c->d_vox_anchor;
+    *hist = c->d_vox_hist;
+    return 1;
+}
 
 }  // extern "C"

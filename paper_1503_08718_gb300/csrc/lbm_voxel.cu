@@ -24,6 +24,7 @@ void lbm__set_phase_count(lbm_ctx* c, int n_phases);
 void lbm__set_error(lbm_ctx* c, const char* msg);
 int lbm__poisoned(const lbm_ctx* c);
 void lbm__poison(lbm_ctx* c);
+int lbm__voxel_scratch(lbm_ctx* c, int n_max, double2** anchors, unsigned long long** hist);
 }
 
 namespace {
@@ -146,8 +147,10 @@ extern "C" lbm_status lbm_set_geometry_braid(lbm_ctx* c, double g_rad, double A,
     unsigned long long* d_hist = nullptr;
     std::vector<unsigned long long> hist((size_t)n_max + 1, 0ull);
     cudaError_t e = cudaSetDevice(dev);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_anchor, sizeof(double2) * n_max);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_hist, sizeof(unsigned long long) * (n_max + 1));
+    // a context on a caller's workspace keeps this scratch inside it
+    const bool own = !lbm__voxel_scratch(c, n_max, &d_anchor, &d_hist);
+    if (e == cudaSuccess && own) e = cudaMalloc((void**)&d_anchor, sizeof(double2) * n_max);
+    if (e == cudaSuccess && own) e = cudaMalloc((void**)&d_hist, sizeof(unsigned long long) * (n_max + 1));
     if (e == cudaSuccess) e = cudaMemcpy(d_anchor, anchors, sizeof(double2) * n_max, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(d_hist, 0, sizeof(unsigned long long) * (n_max + 1));
     long long blocks = (N + 255) / 256;
@@ -175,8 +178,10 @@ extern "C" lbm_status lbm_set_geometry_braid(lbm_ctx* c, double g_rad, double A,
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
-    cudaFree(d_anchor);
-    cudaFree(d_hist);
+    if (own) {
+        cudaFree(d_anchor);
+        cudaFree(d_hist);
+    }
     if (e != cudaSuccess) {
         lbm__poison(c);
         lbm__set_error(c, cudaGetErrorString(e));

@@ -126,6 +126,9 @@ _PROTOS = {
     "lbm_nn_head": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p]),
     "lbm_nn_input": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "lbm_nn_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_int, ctypes.c_void_p]),
+    "lbm_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "lbm_create_with_workspace": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(_ctx_p)]),
     "lbm_last_error": (ctypes.c_char_p, [_ctx_p]),
     "lbm_destroy": (None, [_ctx_p]),
 }
@@ -162,6 +165,17 @@ def lbm_default_opts() -> lbm_solve_opts:
 def lbm_create(nx: int, ny: int, nz: int, cuda_device: int = 0):
     h = _ctx_p()
     st = load().lbm_create(nx, ny, nz, cuda_device, ctypes.byref(h))
+    return st, h
+
+
+def lbm_workspace_bytes(nx: int, ny: int, nz: int, storage: int = 0) -> int:
+    return int(load().lbm_workspace_bytes(nx, ny, nz, storage))
+
+
+def lbm_create_with_workspace(nx: int, ny: int, nz: int, cuda_device: int, dev_ptr: int, nbytes: int):
+    h = _ctx_p()
+    st = load().lbm_create_with_workspace(nx, ny, nz, cuda_device, ctypes.c_void_p(dev_ptr), nbytes,
+                                          ctypes.byref(h))
     return st, h
 
 
@@ -354,10 +368,16 @@ class LBMError(RuntimeError):
 class Solver:
     """One solver context for an (nz, ny, nx) cell on one CUDA device."""
 
-    def __init__(self, nx: int, ny: int, nz: int, device: int = 0):
-        st, h = lbm_create(nx, ny, nz, device)
+    def __init__(self, nx: int, ny: int, nz: int, device: int = 0, workspace=None):
+        """workspace: optional (device pointer, bytes) from which all of the
+        context's device memory is carved (lbm_create_with_workspace); the
+        caller keeps it alive until close()."""
+        if workspace is None:
+            st, h = lbm_create(nx, ny, nz, device)
+        else:
+            st, h = lbm_create_with_workspace(nx, ny, nz, device, int(workspace[0]), int(workspace[1]))
         if st != LBM_OK:
-            raise LBMError(st, f"lbm_create({nx}, {ny}, {nz}, {device}) failed")
+            raise LBMError(st, f"creating the context for {nx}x{ny}x{nz} on device {device} failed")
         self.h = h
         self.shape = (nz, ny, nx)
 
