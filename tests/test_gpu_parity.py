@@ -53,11 +53,13 @@ CASES = [
     ((13, 10, 22), 0, 0), ((13, 10, 22), 0, 1),
     ((18, 7, 11), 1, 0), ((18, 7, 11), 1, 1),
     ((2, 2, 2), 2, 1), ((5, 3, 4), 1, 0),
+    # rows of 128 nodes: the iterations run as fused pairs (two steps a launch)
+    ((128, 16, 24), 2, 0), ((24, 128, 16), 0, 1),
 ]
 
 
 @pytest.mark.parametrize("shape,axis,lateral", CASES)
-@pytest.mark.parametrize("n", [1, 10, 300])
+@pytest.mark.parametrize("n", [1, 10, 300, 2000])
 def test_fixed_iteration_parity(shape, axis, lateral, n):
     nx, ny, nz = shape
     rng = np.random.default_rng(hash((shape, axis, lateral)) & 0xffff)
@@ -378,3 +380,26 @@ def test_lateral_order_chosen_for_fused_pairs(lateral):
         assert np.max(np.abs(T - ref.temperature())) <= T_TOL
         assert k == pytest.approx(ref.k_eff()[0], rel=K_TOL)
     assert np.max(np.abs(res[0][0] - res[1][0])) <= 1e-6
+
+
+@pytest.mark.parametrize("axis,lateral", [(2, 0), (0, 1)])
+def test_converged_braided_cell_matches_oracle(axis, lateral):
+    """A 32 x 32 x 48 braided cell (yarn ellipse 5 x 3, interior angle 30 deg,
+    yarn fraction 0.4) solved to R_T <= 1e-8 on the GPU; the oracle, from the
+    same linear start, runs the same number of iterations on its own
+    voxelisation of the cell: same geometry, T and k_eff."""
+    nx, ny, nz = 32, 32, 48
+    g = math.radians(30.0)
+    anchors = I.braid_anchors(nx, ny, 21, n_max=256)
+    S = lbm.Solver(nx, ny, nz)
+    S.set_geometry_braid(g, anchors, 0.4, A=5.0, B=3.0)
+    lam = I.braid_tensors(30.0)
+    S.set_tensors(lam)
+    info = S.solve(axis, lateral, S.opts(tol=1e-8, max_iters=500_000), allow=())
+    assert info.status == lbm.LBM_OK and info.iters > 1000
+    phase, _, _ = O.braid_phase(nx, ny, nz, g, anchors, 0.4, A=5.0, B=3.0)
+    assert np.array_equal(S.geometry(), phase)
+    ref = _oracle(phase, lam, axis, lateral, info.lattice_scale, info.iters)
+    assert np.max(np.abs(S.temperature() - ref.temperature())) <= T_TOL
+    assert info.k_eff == pytest.approx(ref.k_eff()[0], rel=K_TOL)
+    S.close()
