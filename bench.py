@@ -251,6 +251,31 @@ def cpu_oracle_sample(seconds_target=15.0):
     return glups, O.max_threads(), n, dt
 
 
+def cpu_oracle_one_core(seconds_target=3.0):
+    """The same oracle sample on one host core (iterations of the full cell)."""
+    from oracle import oracle as O
+    from paper_1503_08718_gb300 import inputs as I
+
+    anchors = I.braid_anchors(NX, NY, SEED, n_max=NMAX)
+    phase, _, _ = O.braid_phase(NX, NY, NZ, math.radians(G_DEG), anchors, PHI)
+    lam = I.braid_tensors(G_DEG)
+    all_cores = O.max_threads()
+    O.set_threads(1)
+    try:
+        L = O.Lattice(phase, lam, O.lattice_scale(lam), 2, 0)
+        L.init_linear()
+        t0 = time.perf_counter()
+        L.step(1)
+        dt1 = time.perf_counter() - t0
+        n = max(1, min(50, int(seconds_target / max(dt1, 1e-6))))
+        t0 = time.perf_counter()
+        L.step(n)
+        dt = time.perf_counter() - t0
+    finally:
+        O.set_threads(all_cores)
+    return NX * NY * NZ * n / dt / 1e9, n, dt
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -427,9 +452,12 @@ def run_ours(args):
         cpu = None
         if not args.skip_cpu:
             g, cores, n, dt = cpu_oracle_sample(seconds_target=args.ref_seconds)
+            g1, n1, dt1 = cpu_oracle_one_core()
             cpu = {"value": g, "unit": "GLUPS", "cores": cores, "kind": "oracle",
                    "sample": f"{n} FP64 oracle iterations of the full {NX}x{NY}x{NZ} cell "
-                             f"({dt:.1f} s)"}
+                             f"({dt:.1f} s)",
+                   "one_core": {"value": g1, "unit": "GLUPS",
+                                "sample": f"{n1} iterations of the same cell ({dt1:.1f} s)"}}
         line = {
             "metric": "GLUPS", "value": glups, "unit": "GLUPS", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
