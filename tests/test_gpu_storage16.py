@@ -53,7 +53,8 @@ def _run(phase, lam, axis, lateral, n, storage):
 
 @pytest.mark.parametrize("storage", STORAGES)
 @pytest.mark.parametrize("shape,axis,lateral", [((37, 30, 20), 2, 1), ((21, 18, 26), 0, 0),
-                                                ((16, 9, 12), 1, 1), ((13, 10, 8), 2, 0)])
+                                                ((16, 9, 12), 1, 1), ((13, 10, 8), 2, 0),
+                                                ((128, 16, 24), 2, 0), ((24, 128, 16), 0, 1)])
 @pytest.mark.parametrize("n", [10, 300])
 def test_fixed_iteration_error_bounds(storage, shape, axis, lateral, n):
     nx, ny, nz = shape
@@ -83,14 +84,15 @@ def test_bench_cell_after_20_iterations(storage):
 
 
 @pytest.mark.parametrize("storage", STORAGES)
-def test_no_stagnation_layered_cell_reaches_the_fixed_point(storage):
+@pytest.mark.parametrize("nx,ny", [(32, 32), (128, 8)])
+def test_no_stagnation_layered_cell_reaches_the_fixed_point(storage, nx, ny):
     """Round-to-nearest 16-bit storage freezes once the per-step updates fall
     below half an ulp; with stochastic rounding the iteration keeps moving
     toward the fixed point, whose k_eff is the harmonic mean 94/245."""
     yarn = I.transversely_isotropic(6.0, 0.8, I.axis_in_xz_from_z(30.0))
     lam = np.stack([I.isotropic(0.2), yarn])
-    S = lbm.Solver(32, 32, 32)
-    S.set_geometry(I.layered_phase(32, 32, 32), 2)
+    S = lbm.Solver(nx, ny, 32)
+    S.set_geometry(I.layered_phase(nx, ny, 32), 2)
     S.set_tensors(lam)
     info = S.solve(2, 0, S.opts(storage=storage, tol=0.0, max_iters=200_000))
     assert info.iters == 200_000
