@@ -732,8 +732,10 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
         tau[4] += 0.5;
         tau[8] += 0.5;
         inv3(tau, S);
-        sb[2 * p] = make_float4((float)S[0], (float)S[4], (float)S[8], (float)S[5]);
-        sb[2 * p + 1] = make_float4((float)S[2], (float)S[1], 0.f, 0.f);
+        // the device's per-phase table is B = (I - S_b) / 2
+        sb[2 * p] = make_float4((float)(0.5 * (1.0 - S[0])), (float)(0.5 * (1.0 - S[4])),
+                                (float)(0.5 * (1.0 - S[8])), (float)(-0.5 * S[5]));
+        sb[2 * p + 1] = make_float4((float)(-0.5 * S[2]), (float)(-0.5 * S[1]), 0.f, 0.f);
     }
 
     // buffers

@@ -21,12 +21,14 @@
 // S_b = tau^-1 (the 3x3 off-diagonal block of Eq. 12 inverted).  Because the
 // rows of M in Eq. 11 are orthogonal, M^-1 maps this back to
 //   fhat_0 = T / 4,   fhat_{2k-1,2k} = T / 8 +- jhat_k / 2,
-// which is M^-1 S M applied exactly (no 7x7 product on the device).
-// Interfaces need no code: each node uses its own phase's S_b and streaming
+// which is M^-1 S M applied exactly (no 7x7 product on the device).  The
+// device holds, per phase, the symmetric B = (I - S_b) / 2, so jhat_k / 2 =
+// (B j)_k: one 3x3 product and no further scaling per node.
+// Interfaces need no code: each node uses its own phase's B and streaming
 // is plain (Eq. 21, the half-lattice division scheme of Section 2.3).
 //
 // Flux (Eq. 15-16).  With D = eps (tau - I/2) and grad T = -tau^-1 j / eps,
-// q = -D grad T = (I - S_b / 2) j = (j + jhat) / 2 at every node.
+// q = -D grad T = (I - S_b / 2) j = (j + jhat) / 2 = j / 2 + B j at every node.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -239,10 +241,10 @@ __device__ void close_plane(const StepArgs& a, int z) {
 // The collision of one node (Eq. 5, 8-13 in the reduced form above) from its
 // seven pulled values relative to R_src, with the frame constants kT, kJ;
 // returns the seven post-collision values relative to R_dst, and th = T - R_dst,
-// j_z and sigma_z for the flux.  Every step kernel uses this one function.
+// j_z and (B j)_z for the flux.  Every step kernel uses this one function.
 struct Collided {
     float o[7];
-    float th, jz, sz;
+    float th, jz, hz;
 };
 
 __device__ __forceinline__ Collided collide_node(float g0, float g1, float g2, float g3, float g4,
@@ -252,21 +254,21 @@ __device__ __forceinline__ Collided collide_node(float g0, float g1, float g2, f
     // T - R_dst(z) (Eq. 14) and the flux moment j, with the frame constants
     c.th = (((g0 + g1) + (g2 + g3)) + ((g4 + g5) + g6)) + kT;
     const float jx = g1 - g2, jy = g3 - g4, jz = (g5 - g6) + kJ;
-    // sigma = S_b j with S_b symmetric: (xx, yy, zz, yz) = sa, (xz, xy) = sc.xy
-    const float sx = fmaf(sa.x, jx, fmaf(sc.y, jy, sc.x * jz));
-    const float sy = fmaf(sc.y, jx, fmaf(sa.y, jy, sa.w * jz));
-    const float sz = fmaf(sc.x, jx, fmaf(sa.w, jy, sa.z * jz));
-    const float hx = jx - sx, hy = jy - sy, hz = jz - sz;
+    // jhat / 2 = B j with B = (I - S_b) / 2 symmetric: (xx, yy, zz, yz) = sa,
+    // (xz, xy) = sc.xy
+    const float hx = fmaf(sa.x, jx, fmaf(sc.y, jy, sc.x * jz));
+    const float hy = fmaf(sc.y, jx, fmaf(sa.y, jy, sa.w * jz));
+    const float hz = fmaf(sc.x, jx, fmaf(sa.w, jy, sa.z * jz));
     const float t8 = 0.125f * c.th;
     c.o[0] = 0.25f * c.th;
-    c.o[1] = fmaf(0.5f, hx, t8);
-    c.o[2] = fmaf(-0.5f, hx, t8);
-    c.o[3] = fmaf(0.5f, hy, t8);
-    c.o[4] = fmaf(-0.5f, hy, t8);
-    c.o[5] = fmaf(0.5f, hz, t8);
-    c.o[6] = fmaf(-0.5f, hz, t8);
+    c.o[1] = t8 + hx;
+    c.o[2] = t8 - hx;
+    c.o[3] = t8 + hy;
+    c.o[4] = t8 - hy;
+    c.o[5] = t8 + hz;
+    c.o[6] = t8 - hz;
     c.jz = jz;
-    c.sz = sz;
+    c.hz = hz;
     return c;
 }
 
@@ -478,7 +480,7 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
         const float4 sa = s_sb[2 * p];
         const float4 sc = s_sb[2 * p + 1];
         const Collided cc = collide_node(g0, g1, g2, g3, g4, g5, g6, sa, sc, kT, kJ);
-        const float th = cc.th, jz = cc.jz, sz = cc.sz;
+        const float th = cc.th, jz = cc.jz, hz = cc.hz;
         const bool real = RAGGED ? k < n_real : active;   // n_real is 0 for inactive threads
 #pragma unroll
         for (int i = 0; i < 7; ++i) o[i][k] = cc.o[i];
@@ -486,7 +488,7 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
             const float tdev = th + dref;                    // T - T_ref
             thv[k] = tdev;
             if (real) {
-                q_sum += fmaf(-0.5f, sz, jz);                // (j_z + jhat_z) / 2
+                q_sum += fmaf(0.5f, jz, hz);                 // (j_z + jhat_z) / 2
                 dT_sum += fabsf(tdev - thp[k]);
                 T_sum += fabsf(tdev + tref);
                 Tp_sum += tdev + tref;
@@ -630,7 +632,7 @@ __global__ void __launch_bounds__(fused2_threads(KW), f2_minb(KW)) fused2_kernel
     constexpr int Q3 = (5 * FY + 1) * NXB, Q4 = (6 * FY + 1) * NXB;
     extern __shared__ float4 smem4[];
     float* fn = reinterpret_cast<float*>(smem4);   // [3][f2_slot_rows][NXB]
-    // S_b per phase split into (xx, yy, zz, yz) and (xz, xy) tables: up to
+    // B per phase split into (xx, yy, zz, yz) and (xz, xy) tables: up to
     // 8 (16) distinct phases in a warp read one 128-byte wavefront
     float4* s_sa = reinterpret_cast<float4*>(fn + 3 * RS);
     float2* s_sc = reinterpret_cast<float2*>(s_sa + a.n_phases);
@@ -682,7 +684,7 @@ __global__ void __launch_bounds__(fused2_threads(KW), f2_minb(KW)) fused2_kernel
         out[1] = plane_consts(a.rdst, a.rdst, min(max(jj, 0), nz - 1), nz, a.eps_hot, a.eps_cold);
     };
     if (tid == 0) plane_pair(0, s_kc[0]);
-    __syncthreads();                               // the S_b tables and s_kc[0] are ready
+    __syncthreads();                               // the B tables and s_kc[0] are ready
 
     // L2 prefetch, F2_PF planes ahead: lanes 0..7 of each warp each fetch one
     // population's row segment (what the first step at that plane pulls) or
