@@ -634,10 +634,15 @@ lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* phase, int n_phases) {
     if (!phase) return fail(c, LBM_ERR_INVALID_ARG, "phase is NULL");
     if (n_phases < 1 || n_phases > 255) return fail(c, LBM_ERR_INVALID_ARG, "n_phases must be in [1, 255]");
     const size_t N = (size_t)c->n[0] * c->n[1] * c->n[2];
-    for (size_t i = 0; i < N; ++i)
-        if (phase[i] >= n_phases)
-            return fail(c, LBM_ERR_INVALID_ARG, "phase id %d at voxel %zu is >= n_phases %d",
-                        (int)phase[i], i, n_phases);
+    // largest id first (a branch-free scan the compiler vectorises), then the
+    // first offending voxel only if there is one
+    uint8_t top = 0;
+    for (size_t i = 0; i < N; ++i) top = phase[i] > top ? phase[i] : top;
+    if (top >= n_phases)
+        for (size_t i = 0; i < N; ++i)
+            if (phase[i] >= n_phases)
+                return fail(c, LBM_ERR_INVALID_ARG, "phase id %d at voxel %zu is >= n_phases %d",
+                            (int)phase[i], i, n_phases);
     CUDA_TRY(c, cudaSetDevice(c->device));
     CUDA_TRY(c, cudaMemcpy(c->d_phase, phase, N, cudaMemcpyHostToDevice));
     if (c->have_tensors && (int)c->lambda.size() != 6 * n_phases) c->have_tensors = false;
