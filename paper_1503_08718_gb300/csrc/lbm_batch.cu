@@ -423,10 +423,8 @@ lbm_status lbm_batch_solve(lbm_batch* b, lbm_lateral lateral, const lbm_solve_op
             S[4] = (tau[0] * tau[8] - tau[2] * tau[6]) / det;
             S[5] = (tau[2] * tau[3] - tau[0] * tau[5]) / det;
             S[8] = (tau[0] * tau[4] - tau[1] * tau[3]) / det;
-            // the device's per-phase table is B = (I - S_b) / 2
-            sb[2 * q] = make_float4((float)(0.5 * (1.0 - S[0])), (float)(0.5 * (1.0 - S[4])),
-                                    (float)(0.5 * (1.0 - S[8])), (float)(-0.5 * S[5]));
-            sb[2 * q + 1] = make_float4((float)(-0.5 * S[2]), (float)(-0.5 * S[1]), 0.f, 0.f);
+            // the device's per-phase table: B = (I - S_b) / 2 for FP32, S_b for 16 bits
+            lbm::phase_entry(S, op.storage == LBM_STORE_F32, &sb[2 * (size_t)q]);
         }
         BCUDA(b, cudaMemcpyAsync(base + p.off_sb, sb.data(), sizeof(float4) * sb.size(),
                                  cudaMemcpyHostToDevice, st));

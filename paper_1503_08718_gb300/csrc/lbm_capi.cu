@@ -737,10 +737,8 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
         tau[4] += 0.5;
         tau[8] += 0.5;
         inv3(tau, S);
-        // the device's per-phase table is B = (I - S_b) / 2
-        sb[2 * p] = make_float4((float)(0.5 * (1.0 - S[0])), (float)(0.5 * (1.0 - S[4])),
-                                (float)(0.5 * (1.0 - S[8])), (float)(-0.5 * S[5]));
-        sb[2 * p + 1] = make_float4((float)(-0.5 * S[2]), (float)(-0.5 * S[1]), 0.f, 0.f);
+        // the device's per-phase table: B = (I - S_b) / 2 for FP32, S_b for 16 bits
+        lbm::phase_entry(S, op.storage == LBM_STORE_F32, &sb[2 * (size_t)p]);
     }
 
     // buffers

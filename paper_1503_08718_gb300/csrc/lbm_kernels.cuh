@@ -21,11 +21,13 @@
 // S_b = tau^-1 (the 3x3 off-diagonal block of Eq. 12 inverted).  Because the
 // rows of M in Eq. 11 are orthogonal, M^-1 maps this back to
 //   fhat_0 = T / 4,   fhat_{2k-1,2k} = T / 8 +- jhat_k / 2,
-// which is M^-1 S M applied exactly (no 7x7 product on the device).  The
-// device holds, per phase, the symmetric B = (I - S_b) / 2, so jhat_k / 2 =
-// (B j)_k: one 3x3 product and no further scaling per node.
-// Interfaces need no code: each node uses its own phase's B and streaming
-// is plain (Eq. 21, the half-lattice division scheme of Section 2.3).
+// which is M^-1 S M applied exactly (no 7x7 product on the device).  With
+// FP32 storage the device holds, per phase, the symmetric B = (I - S_b) / 2,
+// so jhat_k / 2 = (B j)_k: one 3x3 product and no further scaling per node.
+// The 16-bit-storage step (8 nodes per thread, tight on registers) holds S_b
+// and forms jhat = j - S_b j, which fits its register budget without spills.
+// Interfaces need no code: each node uses its own phase's table entry and
+// streaming is plain (Eq. 21, the half-lattice division scheme of Section 2.3).
 //
 // Flux (Eq. 15-16).  With D = eps (tau - I/2) and grad T = -tau^-1 j / eps,
 // q = -D grad T = (I - S_b / 2) j = (j + jhat) / 2 = j / 2 + B j at every node.
@@ -239,14 +241,28 @@ __device__ void close_plane(const StepArgs& a, int z) {
 }
 
 // The collision of one node (Eq. 5, 8-13 in the reduced form above) from its
-// seven pulled values relative to R_src, with the frame constants kT, kJ;
-// returns the seven post-collision values relative to R_dst, and th = T - R_dst,
-// j_z and (B j)_z for the flux.  Every step kernel uses this one function.
+// seven pulled values relative to R_src, with the frame constants kT, kJ and
+// the phase's table entry (sa, sc) = B (BTAB) or S_b; returns the seven
+// post-collision values relative to R_dst, th = T - R_dst and q_z, the flux
+// along z (Eq. 16).  Every step kernel uses this one function.
 struct Collided {
     float o[7];
-    float th, jz, hz;
+    float th, qz;
 };
 
+// host side of the table: the entry of one phase from S_b (FP64, 3x3 row-major)
+inline void phase_entry(const double* S, bool btab, float4* e) {
+    if (btab) {
+        e[0] = make_float4((float)(0.5 * (1.0 - S[0])), (float)(0.5 * (1.0 - S[4])),
+                           (float)(0.5 * (1.0 - S[8])), (float)(-0.5 * S[5]));
+        e[1] = make_float4((float)(-0.5 * S[2]), (float)(-0.5 * S[1]), 0.f, 0.f);
+    } else {
+        e[0] = make_float4((float)S[0], (float)S[4], (float)S[8], (float)S[5]);
+        e[1] = make_float4((float)S[2], (float)S[1], 0.f, 0.f);
+    }
+}
+
+template <bool BTAB>
 __device__ __forceinline__ Collided collide_node(float g0, float g1, float g2, float g3, float g4,
                                                  float g5, float g6, float4 sa, float4 sc, float kT,
                                                  float kJ) {
@@ -254,21 +270,30 @@ __device__ __forceinline__ Collided collide_node(float g0, float g1, float g2, f
     // T - R_dst(z) (Eq. 14) and the flux moment j, with the frame constants
     c.th = (((g0 + g1) + (g2 + g3)) + ((g4 + g5) + g6)) + kT;
     const float jx = g1 - g2, jy = g3 - g4, jz = (g5 - g6) + kJ;
-    // jhat / 2 = B j with B = (I - S_b) / 2 symmetric: (xx, yy, zz, yz) = sa,
-    // (xz, xy) = sc.xy
-    const float hx = fmaf(sa.x, jx, fmaf(sc.y, jy, sc.x * jz));
-    const float hy = fmaf(sc.y, jx, fmaf(sa.y, jy, sa.w * jz));
-    const float hz = fmaf(sc.x, jx, fmaf(sa.w, jy, sa.z * jz));
+    // the symmetric table entry: (xx, yy, zz, yz) = sa, (xz, xy) = sc.xy
+    const float ax = fmaf(sa.x, jx, fmaf(sc.y, jy, sc.x * jz));
+    const float ay = fmaf(sc.y, jx, fmaf(sa.y, jy, sa.w * jz));
+    const float az = fmaf(sc.x, jx, fmaf(sa.w, jy, sa.z * jz));
     const float t8 = 0.125f * c.th;
     c.o[0] = 0.25f * c.th;
-    c.o[1] = t8 + hx;
-    c.o[2] = t8 - hx;
-    c.o[3] = t8 + hy;
-    c.o[4] = t8 - hy;
-    c.o[5] = t8 + hz;
-    c.o[6] = t8 - hz;
-    c.jz = jz;
-    c.hz = hz;
+    if (BTAB) {                          // a = B j = jhat / 2
+        c.o[1] = t8 + ax;
+        c.o[2] = t8 - ax;
+        c.o[3] = t8 + ay;
+        c.o[4] = t8 - ay;
+        c.o[5] = t8 + az;
+        c.o[6] = t8 - az;
+        c.qz = fmaf(0.5f, jz, az);      // j_z / 2 + (B j)_z
+    } else {                             // a = S_b j, jhat = j - a
+        const float hx = jx - ax, hy = jy - ay, hz = jz - az;
+        c.o[1] = fmaf(0.5f, hx, t8);
+        c.o[2] = fmaf(-0.5f, hx, t8);
+        c.o[3] = fmaf(0.5f, hy, t8);
+        c.o[4] = fmaf(-0.5f, hy, t8);
+        c.o[5] = fmaf(0.5f, hz, t8);
+        c.o[6] = fmaf(-0.5f, hz, t8);
+        c.qz = fmaf(-0.5f, az, jz);     // (j_z + jhat_z) / 2
+    }
     return c;
 }
 
@@ -479,8 +504,8 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
         const int p = (k < 4 ? (ph.x >> (8 * k)) : (ph.y >> (8 * (k - 4)))) & 0xff;
         const float4 sa = s_sb[2 * p];
         const float4 sc = s_sb[2 * p + 1];
-        const Collided cc = collide_node(g0, g1, g2, g3, g4, g5, g6, sa, sc, kT, kJ);
-        const float th = cc.th, jz = cc.jz, hz = cc.hz;
+        const Collided cc = collide_node<FMT == 0>(g0, g1, g2, g3, g4, g5, g6, sa, sc, kT, kJ);
+        const float th = cc.th;
         const bool real = RAGGED ? k < n_real : active;   // n_real is 0 for inactive threads
 #pragma unroll
         for (int i = 0; i < 7; ++i) o[i][k] = cc.o[i];
@@ -488,7 +513,7 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
             const float tdev = th + dref;                    // T - T_ref
             thv[k] = tdev;
             if (real) {
-                q_sum += fmaf(0.5f, jz, hz);                 // (j_z + jhat_z) / 2
+                q_sum += cc.qz;                              // (j_z + jhat_z) / 2
                 dT_sum += fabsf(tdev - thp[k]);
                 T_sum += fabsf(tdev + tref);
                 Tp_sum += tdev + tref;
@@ -612,7 +637,7 @@ __device__ __forceinline__ Quad7 collide_quad(const float4& g0, const float4& g1
     for (int k = 0; k < 4; ++k) {
         const int ph = (phw >> (8 * k)) & 255u;
         const float2 sc = s_sc[ph];
-        const Collided c = collide_node(f4get(g0, k), f4get(g1, k), f4get(g2, k), f4get(g3, k),
+        const Collided c = collide_node<true>(f4get(g0, k), f4get(g1, k), f4get(g2, k), f4get(g3, k),
                                         f4get(g4, k), f4get(g5, k), f4get(g6, k), s_sa[ph],
                                         make_float4(sc.x, sc.y, 0.f, 0.f), kT, kJ);
 #pragma unroll
