@@ -3,7 +3,7 @@
 // The network (a small 3D encoder-decoder, specified in the header) predicts
 // the steady temperature of a cell from its material field; the lattice
 // Boltzmann iteration then starts from f^eq of that prediction instead of the
-// linear profile and remains the judge of the answer (the paper's method only
+// linear profile and still decides the answer (the paper's method only
 // needs a steady state, Section 2.3).  Every layer here works on channels-last
 // BF16 activations [voxel][channel] with FP32 accumulation:
 //
