@@ -58,8 +58,11 @@ batch_step_kernel(const StepArgs* __restrict__ args, const int* __restrict__ pre
                   const int* __restrict__ order, const BatchCtl* __restrict__ bctl, int variant,
                   unsigned rseed) {
     const int n_active = bctl->n_active;
-    const int b = (int)blockIdx.x;
-    if (b >= prefix[n_active]) return;        // block of a solve that has converged
+    const int total = prefix[n_active];
+    if ((int)blockIdx.x >= total) return;     // block of a solve that has converged
+    // odd steps walk the blocks backwards, so that a step starts on the state
+    // the previous one wrote last (still in L2)
+    const int b = (rseed & 1u) ? total - 1 - (int)blockIdx.x : (int)blockIdx.x;
     int lo = 0, hi = n_active - 1;            // last s with prefix[s] <= b
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;

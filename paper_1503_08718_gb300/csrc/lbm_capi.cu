@@ -28,6 +28,7 @@ struct lbm_ctx {
     int n_sm = 152;                        // multiprocessors of the device
     bool fuse_ok[2] = {false, false};      // fused kernel usable for rows of 128, 256 nodes
     int pair_flip = 0;                     // chunk direction of the next lbm_advance pair
+    mutable int step_flip = 0;             // plane order of the next single-step launch
     char* ws = nullptr;                    // caller's device workspace (nullptr: own allocations)
     size_t ws_bytes = 0;
     size_t ws_static = 0;                  // end of the part carved at creation
@@ -258,7 +259,9 @@ void launch_fmt(const lbm::StepArgs& a, bool periodic, bool check, bool ragged, 
 
 cudaError_t launch_step(const lbm_ctx* c, int src, bool check, Frame fr, cudaStream_t st,
                         const Closing& cl = Closing()) {
-    const lbm::StepArgs a = step_args(c, src, fr, cl);
+    lbm::StepArgs a = step_args(c, src, fr, cl);
+    a.zrev = c->step_flip;                  // alternate launches reverse the plane order
+    c->step_flip ^= 1;
     const dim3 grid(c->blocks_per_plane, c->L.NZ);
     const size_t smem = sizeof(float4) * 2 * c->n_phases;
     const bool periodic = c->lateral == LBM_LATERAL_PERIODIC;

@@ -92,6 +92,7 @@ struct StepArgs {
     int nx, ny, nz, pitch, n_phases;
     int quads_per_plane;             // (pitch / V) * ny vectors per plane
     int blocks_per_plane;
+    int zrev;                        // 1: blocks walk the planes from the top (alternate steps)
     float eps_hot, eps_cold;         // eps * T_wall
     unsigned rseed;                  // launch salt of the stochastic rounding
     double t_ref;                    // offset of the residual snapshot
@@ -835,10 +836,13 @@ __global__ void __launch_bounds__(fused2_threads(KW), f2_minb(KW)) fused2_kernel
 }
 
 // The single-solve step: blockIdx.x is the block within the plane,
-// blockIdx.y the plane.
+// blockIdx.y the plane, counted from the top when zrev is set: consecutive
+// steps alternate, so that a step starts on the planes the previous one
+// wrote last (still in L2).
 template <int FMT, bool PERIODIC, bool CHECK, bool RAGGED>
 __global__ void __launch_bounds__(kThreads, (CHECK && FMT != 0) ? 2 : 4) step_kernel(const StepArgs a) {
-    step_body<FMT, PERIODIC, CHECK, RAGGED, kThreads>(a, blockIdx.x, blockIdx.y, a.rseed);
+    const int z = a.zrev ? a.nz - 1 - (int)blockIdx.y : (int)blockIdx.y;
+    step_body<FMT, PERIODIC, CHECK, RAGGED, kThreads>(a, blockIdx.x, z, a.rseed);
 }
 
 static __global__ void add_iters_kernel(Ctl* c, long long n) { c->iter += n; }
