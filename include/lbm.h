@@ -102,21 +102,28 @@ typedef struct {
     int32_t checks;         /* number of checks performed since lbm_start */
 } lbm_solve_info;
 
-/* Fills o with the defaults listed in lbm_solve_opts. */
+/* Fills o with the defaults listed in lbm_solve_opts (wall temperatures of
+ * Eq. 23, the lattice scale of Eq. 13 through tau_max, the R_T stop rule,
+ * which the paper leaves open). */
 void lbm_default_opts(lbm_solve_opts* o);
 
-/* Creates a context for an nx*ny*nz cell on CUDA device cuda_device.
- * Sizes must be >= 2 and nx*ny*nz < 2^31.  *out receives the context. */
+/* Creates a context for an nx*ny*nz cell (the voxel lattice of Section 2.3,
+ * one node per voxel) on CUDA device cuda_device.  Sizes must be >= 2 and
+ * nx*ny*nz < 2^31.  *out receives the context; the context owns its device
+ * memory until lbm_destroy.  LBM_ERR_INVALID_ARG for bad sizes or device,
+ * LBM_ERR_OUT_OF_MEMORY if an allocation fails. */
 lbm_status lbm_create(int nx, int ny, int nz, int cuda_device, lbm_ctx** out);
 
-/* Device bytes a context for an nx*ny*nz cell needs when all of its device
+/* No counterpart in the paper (device memory ownership).
+ * Device bytes a context for an nx*ny*nz cell needs when all of its device
  * memory comes from the caller (lbm_create_with_workspace): the cell's
  * buffers, one solve along any axis with the given storage (lbm_storage) and
  * up to 255 phases, and the voxeliser's scratch.  0 for invalid sizes or
  * storage.  Host-only: needs no GPU. */
 size_t lbm_workspace_bytes(int nx, int ny, int nz, int storage);
 
-/* Like lbm_create, but every device buffer of the context is carved from the
+/* No counterpart in the paper (device memory ownership).
+ * Like lbm_create, but every device buffer of the context is carved from the
  * caller's block dev_ptr[0 .. bytes): for callers whose device memory belongs
  * to another allocator (a framework's caching pool, e.g. a torch tensor) or
  * to a fixed budget.  dev_ptr must be device memory of cuda_device, 256-byte
@@ -159,12 +166,15 @@ lbm_status lbm_advance(lbm_ctx* c, int64_t n_steps);
  * Synchronises the stream; info (nullable) receives the results. */
 lbm_status lbm_check(lbm_ctx* c, lbm_solve_info* info);
 
-/* Iterates from the current state in whole check intervals (CUDA graph with
- * a device-side while condition, no host round trip per check) until R_T <=
- * tol, max_iters, a stall or a non-finite value.  Synchronous. */
+/* Iterates the lattice (Eq. 5, 21, 23-25) toward the steady state of
+ * Section 2.3 from the current state in whole check intervals (CUDA graph
+ * with a device-side while condition, no host round trip per check; each
+ * check evaluates the flux of Eq. 16 and k_eff of Eq. 22) until R_T <= tol,
+ * max_iters, a stall or a non-finite value.  Synchronous. */
 lbm_status lbm_run(lbm_ctx* c, lbm_solve_info* info);
 
-/* lbm_start followed by lbm_run. */
+/* lbm_start followed by lbm_run: the whole method of Section 2 on one cell
+ * (Eq. 5-25 to the steady state, k_eff by Eq. 22). */
 lbm_status lbm_solve(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral,
                      const lbm_solve_opts* o, lbm_solve_info* info);
 
@@ -175,13 +185,15 @@ lbm_status lbm_k_eff(const lbm_ctx* c, double* out);
  * original axis order). Synchronous. */
 lbm_status lbm_get_temperature(lbm_ctx* c, float* host_out);
 
-/* Convergence history of the current solve: for each of the most recent
+/* Convergence history of the current solve (k_eff of Eq. 22 and the
+ * residuals at each check): for each of the most recent
  * min(checks, max_entries, 65536) checks, oldest first, four doubles
  * (iteration, k_eff, R_T, R_Q) into host_out.  *n_out (nullable) receives
  * the number of entries written.  Synchronous. */
 lbm_status lbm_get_history(lbm_ctx* c, double* host_out, int max_entries, int* n_out);
 
-/* Plane sums Q[k] of the axial flux at the last check (n == N_axis doubles). */
+/* Plane sums Q[k] of the axial flux of Eq. 16 at the last check, the
+ * integrand of Eq. 22 (n == N_axis doubles, host_out caller-owned). */
 lbm_status lbm_get_plane_flux(const lbm_ctx* c, double* host_out, int n);
 
 /* Synthetic four-directional braided cell (yarns along
@@ -213,17 +225,20 @@ typedef struct {
     int32_t status;         /* LBM_OK if every solve converged, else LBM_ERR_NOT_CONVERGED */
 } lbm_batch_info;
 
-/* Creates an empty batch on CUDA device cuda_device. */
+/* Creates an empty batch (for the sweeps of Section 5) on CUDA device
+ * cuda_device. */
 lbm_status lbm_batch_create(int cuda_device, lbm_batch** out);
 
-/* Adds one steady solve: an nx*ny*nz cell (phase map and n_phases tensors,
+/* Adds one steady solve of Section 2 to the sweep: an nx*ny*nz cell (phase
+ * map and n_phases tensors,
  * host, copied; same layout and checks as lbm_set_geometry / lbm_set_tensors)
  * with the temperature difference along `axis`.  *id (nullable) receives the
  * solve's index. */
 lbm_status lbm_batch_add(lbm_batch* b, int nx, int ny, int nz, const uint8_t* phase, int n_phases,
                          const double* lambda, lbm_axis axis, int* id);
 
-/* Solves every added problem with one lateral type and one set of options
+/* Solves every added problem (the sweeps of Section 5, Fig. 9) with one
+ * lateral type and one set of options
  * (each solve takes its own lattice scale from its tensors unless
  * opts.lattice_scale is set; t_init must be NULL).  All solves stay resident
  * in device memory; one CUDA graph launch advances every unconverged solve by
@@ -233,17 +248,20 @@ lbm_status lbm_batch_add(lbm_batch* b, int nx, int ny, int nz, const uint8_t* ph
 lbm_status lbm_batch_solve(lbm_batch* b, lbm_lateral lateral, const lbm_solve_opts* o,
                            lbm_batch_info* info);
 
-/* Result of solve `id` after lbm_batch_solve (iterations, k_eff, residuals,
- * lattice scale, status). */
+/* Result of solve `id` after lbm_batch_solve (iterations, k_eff of Eq. 22,
+ * residuals, lattice scale, status). */
 lbm_status lbm_batch_result(const lbm_batch* b, int id, lbm_solve_info* info);
 
-/* Final temperature of solve `id` (nx*ny*nz floats, original axis order). */
+/* Final temperature (Eq. 14) of solve `id` (nx*ny*nz floats, original axis
+ * order, host_out caller-owned). */
 lbm_status lbm_batch_get_temperature(lbm_batch* b, int id, float* host_out);
 
-/* Message of the last failed batch call (batch-owned string). NULL-safe. */
+/* No counterpart in the paper.  Message of the last failed batch call
+ * (batch-owned string). NULL-safe. */
 const char* lbm_batch_last_error(const lbm_batch* b);
 
-/* Frees the batch and its device memory. NULL-safe. */
+/* No counterpart in the paper.  Frees the batch and its device memory.
+ * NULL-safe. */
 void lbm_batch_destroy(lbm_batch* b);
 
 /* ---- Learned warm start: layers of the 3D convolutional network ---------
@@ -256,7 +274,8 @@ void lbm_batch_destroy(lbm_batch* b);
  * (z the temperature-difference axis).  Activations and weights are BF16,
  * accumulation FP32.  stream: cudaStream_t (NULL = legacy default stream).
  * Calls are asynchronous; they return LBM_ERR_INVALID_ARG on a bad size or
- * NULL pointer and LBM_ERR_CUDA on a launch error. */
+ * NULL pointer and LBM_ERR_CUDA on a launch error.  The paper has no
+ * network: none of these layers has a counterpart in it. */
 
 /* y = act(bias + conv(x, w)): ksize 3 (27 taps, periodic in x and y, zero
  * outside in z) or 1.  x [V][cin] (cin a multiple of 16), w [taps][cin][cout]
@@ -379,14 +398,16 @@ lbm_status lbm_yarn_conductivity(double lam_fL, double lam_fT, double lam_m, dou
 lbm_status lbm_braid_unit_cell(double phi_f, int n_f, double d_f, double gamma_rad, double* a,
                                double* h, double* c, double* d, double* phi_fy);
 
-/* Copies the phase map (nx*ny*nz uint8, original order) to host_out. */
+/* Copies the phase map (the voxelised cell of Section 5, Fig. 7; nx*ny*nz
+ * uint8, original order) to host_out (caller-owned). */
 lbm_status lbm_get_geometry(lbm_ctx* c, uint8_t* host_out);
 
-/* Message of the last failed call on this context (context-owned string,
- * valid until the next call).  NULL-safe. */
+/* No counterpart in the paper.  Message of the last failed call on this
+ * context (context-owned string, valid until the next call).  NULL-safe. */
 const char* lbm_last_error(const lbm_ctx* c);
 
-/* Frees the context and all device memory it owns. NULL-safe. */
+/* No counterpart in the paper.  Frees the context and all device memory it
+ * owns (a caller's workspace stays the caller's). NULL-safe. */
 void lbm_destroy(lbm_ctx* c);
 
 #ifdef __cplusplus
