@@ -230,17 +230,16 @@ typedef struct {
 lbm_status lbm_batch_create(int cuda_device, lbm_batch** out);
 
 /* Adds one steady solve of Section 2 to the sweep: an nx*ny*nz cell (phase
- * map and n_phases tensors,
- * host, copied; same layout and checks as lbm_set_geometry / lbm_set_tensors)
- * with the temperature difference along `axis`.  *id (nullable) receives the
- * solve's index. */
+ * map and n_phases tensors, host, copied; same layout and checks as
+ * lbm_set_geometry / lbm_set_tensors) with the temperature difference along
+ * `axis`.  *id (nullable) receives the solve's index. */
 lbm_status lbm_batch_add(lbm_batch* b, int nx, int ny, int nz, const uint8_t* phase, int n_phases,
                          const double* lambda, lbm_axis axis, int* id);
 
 /* Solves every added problem (the sweeps of Section 5, Fig. 9) with one
- * lateral type and one set of options
- * (each solve takes its own lattice scale from its tensors unless
- * opts.lattice_scale is set; t_init must be NULL).  All solves stay resident
+ * lateral type and one set of options (each solve takes its own lattice
+ * scale from its tensors unless opts.lattice_scale is set; t_init must be
+ * NULL).  All solves stay resident
  * in device memory; one CUDA graph launch advances every unconverged solve by
  * whole check intervals until each has met tol or max_iters.  Before the
  * launch the block size is picked among 128, 256 and 512 threads by timing
