@@ -278,6 +278,40 @@ def cpu_oracle_one_core(seconds_target=3.0):
     return NX * NY * NZ * n / dt / 1e9, n, dt
 
 
+def oracle_extras():
+    """Further oracle timings on the host cores: the 32^3 layered cell solved to
+    R_T <= 1e-8, 500 iterations of the 256x256x512 braid, and the time the
+    oracle would need for the bench cell's 33 400 iterations to k_eff within
+    1e-4, extrapolated from its measured rate."""
+    from oracle import oracle as O
+    from paper_1503_08718_gb300 import inputs as I
+
+    out = {"cores": O.max_threads()}
+    yarn = I.transversely_isotropic(6.0, 0.8, I.axis_in_xz_from_z(30.0))
+    lam = np.stack([I.isotropic(0.2), yarn])
+    L = O.Lattice(I.layered_phase(32, 32, 32), lam, O.lattice_scale(lam), 2, 0)
+    L.init_linear()
+    t0 = time.perf_counter()
+    rc, rt = L.solve(tol=1e-8, check_every=K)
+    dt = time.perf_counter() - t0
+    out["layered_32_converged"] = {"iters": L.iter, "seconds": dt, "k_eff": L.k_eff()[0],
+                                   "exact": 94.0 / 245.0, "residual_T": rt}
+    n4 = (256, 256, 512)
+    anchors = I.braid_anchors(n4[0], n4[1], 7, n_max=1024)
+    phase, _, _ = O.braid_phase(*n4, math.radians(35.0), anchors, 0.50)
+    lam4 = I.braid_tensors(35.0)
+    L4 = O.Lattice(phase, lam4, O.lattice_scale(lam4), 2, 0)
+    L4.init_linear()
+    t0 = time.perf_counter()
+    L4.step(500)
+    dt4 = time.perf_counter() - t0
+    out["braid_256x256x512_500_iters"] = {"seconds": dt4, "glups": n4[0] * n4[1] * n4[2] * 500 / dt4 / 1e9}
+    g, _, n, dt2 = cpu_oracle_sample(seconds_target=5.0)
+    out["bench_cell_time_to_keff_1e-4_s"] = NX * NY * NZ * 33_400 / (g * 1e9)
+    out["bench_cell_rate_glups"] = g
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -305,6 +339,8 @@ def run_reference(args):
         "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
+    if args.oracle_extras:
+        line["oracle_extras"] = oracle_extras()
     print(json.dumps(line), flush=True)
 
 
@@ -515,6 +551,9 @@ def main():
                     help="omit the time-to-k_eff runs and the batched sweep")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline leg")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
+    ap.add_argument("--oracle-extras", action="store_true",
+                    help="reference arm: also time the oracle on the layered 32^3 cell to "
+                         "convergence and on 500 iterations of the 256x256x512 braid")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per fused-step launch from an ncu capture")
     args = ap.parse_args()
