@@ -42,15 +42,31 @@ G_DEG, PHI, SEED, NMAX = 30.0, 0.45, 42, 128
 K = 100
 ITERS = 1000
 BYTES_PER_LUP = {"f32": 57, "bf16": 29, "f16": 29}   # 7 values read + 7 written + 1 B phase id
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture of this workload (profiles/fused2_kernel_braid128x128x256.md and
-# profiles/step_kernel_braid128x128x256.md; ncu empties the caches before each
-# captured launch, so these are cold-L2 figures); set to None when the kernel
-# changes
-TRAFFIC = {("fused2", "f32"): 188.85e6, ("step", "f32"): 187.0e6, ("step", "bf16"): 74.6e6}
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
+# capture of this workload (dram__bytes_read.sum + dram__bytes_write.sum),
+# keyed by (kernel, storage) and stamped with the SHA-256 prefix of the
+# kernel source it was taken on; a stamp that no longer matches the source
+# reports null instead of a stale figure.
+TRAFFIC = {}
+KERNEL_SOURCE = os.path.join(ROOT, "paper_1503_08718_gb300", "csrc", "lbm_kernels.cuh")
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 WORKLOAD = (f"braid {NX}x{NY}x{NZ} g=30deg phi=0.45 seed=42, dT along z, periodic laterals, "
             f"FP32 D3Q7 MRT")
+
+
+def kernel_source_sha16():
+    import hashlib
+    with open(KERNEL_SOURCE, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def traffic_for(key):
+    """DRAM bytes per launch for (kernel, storage) if captured on the current
+    kernel source, else None."""
+    ent = TRAFFIC.get(key)
+    if ent is None or ent[1] != kernel_source_sha16():
+        return None
+    return ent[0]
 
 
 def dist_env():
@@ -404,28 +420,34 @@ def run_ours(args):
     pairs = 2 * (R // 4) if (args.storage == "f32" and args.fuse) else 0
     launches_per_interval = 2 + pairs + (R - 2 * pairs)
     launches_per_step = (iters // K) * launches_per_interval + 2   # + permute, init
-    # roofline of the dominant kernel: the fused two-step kernel in FP32 (one
-    # read and one write of the state per launch: 57 B per voxel for two
-    # updates), else the single step (57 or 29 B per update).  Its average
-    # launch time is measured with CUDA events on the solver's stream over a
-    # run of its launches alone (lbm_advance); frac_whole_step charges every
-    # launch of the timed bench step to it instead (a lower bound).
+    # roofline of the dominant kernel: the fused two-step kernel in FP32,
+    # else the single step.  Algorithmic bytes per launch follow the
+    # per-update figure (57 B/LUP FP32, 29 B/LUP 16-bit: 7 values read, 7
+    # written, 1 B phase id) times the updates one launch performs
+    # (voxels x 2 for the two-step kernel).  A two-step launch moves the state
+    # through HBM once (57 B per voxel for two updates), so its `frac` exceeds
+    # 1 by construction; `frac_moved` divides the bytes it actually has to
+    # move by the same time (its bandwidth efficiency).  Its average launch
+    # time is measured with CUDA events on the solver's stream over a run of
+    # its launches alone (lbm_advance); frac_whole_step charges every launch
+    # of the timed bench step to it instead (a lower bound).
+    upd = 2 if pairs else 1
     if pairs:
         dom_launches = args.steps * (iters // K) * pairs
-        dom_bytes = BYTES_PER_LUP["f32"] * n_vox
         dominant = "fused2_kernel (2 updates per launch)"
         dom_key = ("fused2", "f32")
     else:
         dom_launches = args.steps * iters
-        dom_bytes = BYTES_PER_LUP[args.storage] * n_vox
         dominant = "step_kernel"
         dom_key = ("step", args.storage)
+    moved_bytes = BYTES_PER_LUP[args.storage] * n_vox
+    dom_bytes = moved_bytes * upd
     per_launch_s = (ms / 1000.0) / dom_launches
     achieved_step = dom_bytes / per_launch_s / 1e9
-    launch_us, n_timed, timing_mode = kernel_launch_us(S, opts, stream, 2 if pairs else 1)
+    launch_us, n_timed, timing_mode = kernel_launch_us(S, opts, stream, upd)
     achieved = dom_bytes / (launch_us * 1e-6) / 1e9
     peak, peak_kind = peaks()
-    traffic = args.traffic if args.traffic is not None else TRAFFIC.get(dom_key)
+    traffic = args.traffic if args.traffic is not None else traffic_for(dom_key)
 
     # the same step with 16-bit distribution storage (FP32 collision,
     # stochastic rounding): GLUPS and the roofline at 29 B/LUP
@@ -511,7 +533,15 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_kind, "kernel": dominant,
-                         "bytes_per_launch": dom_bytes, "launch_us": launch_us,
+                         "updates_per_launch": upd,
+                         "bytes_per_launch": dom_bytes,
+                         "frac_basis": (f"{BYTES_PER_LUP[args.storage]} B/LUP x {n_vox} voxels x "
+                                        f"{upd} updates per launch"),
+                         "moved_bytes_per_launch": moved_bytes,
+                         "frac_moved": moved_bytes / (launch_us * 1e-6) / 1e9 / peak,
+                         "traffic_over_moved": (traffic / moved_bytes) if traffic else None,
+                         "kernel_source_sha16": kernel_source_sha16(),
+                         "launch_us": launch_us,
                          "launches_timed": n_timed, "launch_timing": timing_mode,
                          "frac_whole_step": achieved_step / peak},
             "cpu_baseline": cpu,

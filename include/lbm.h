@@ -22,14 +22,22 @@
  *   - The hot wall (t_hot) is the face at the axis minimum, walls sit half a
  *     spacing outside the first and last node, L = N_axis and A = N_b N_c.
  *   - Pointers documented as "host" are read (or written) during the call
- *     only and never retained; every buffer the library needs on the device
- *     is allocated and owned by the context.
+ *     only and never retained.  Every buffer the library needs on the device
+ *     is allocated and owned by the context, with two exceptions:
+ *     lbm_create_with_workspace carves them from the caller's block instead,
+ *     and lbm_braid_voxelize_noalloc works in caller memory plus one small
+ *     file-scope device array of its own.
  *   - A call that fails returns a non-zero lbm_status and records a message
  *     retrievable with lbm_last_error().  After LBM_ERR_CUDA the context is
  *     poisoned: only lbm_last_error() and lbm_destroy() remain valid.
  *   - One context per host thread; contexts are independent.
- *   - Computation is FP32 with distributions stored as deviations from
- *     w_i * T_ref, T_ref = (t_hot + t_cold) / 2; plane-flux and residual
+ *   - The collision is FP32.  Distributions are stored (FP32, or BF16 /
+ *     FP16 with opts.storage) as deviations g_i = f_i - w_i R(z) from a
+ *     per-plane reference temperature R(z) along the temperature-difference
+ *     axis: the plane mean of T at the previous check, rounded to a
+ *     power-of-two grid so that every change of frame is exact in FP32.
+ *     The map is linear, so the frame changes no result in exact
+ *     arithmetic; it keeps the stored values small.  Plane-flux and residual
  *     reductions are FP64.
  */
 #ifndef LBM_H
@@ -191,6 +199,28 @@ lbm_status lbm_get_temperature(lbm_ctx* c, float* host_out);
  * (iteration, k_eff, R_T, R_Q) into host_out.  *n_out (nullable) receives
  * the number of entries written.  Synchronous. */
 lbm_status lbm_get_history(lbm_ctx* c, double* host_out, int max_entries, int* n_out);
+
+/* No counterpart in the paper (checkpoint and resume of the iteration).
+ * Bytes of a snapshot of the current solve: its distributions, reference
+ * frames, residual snapshot, control block, check history and last plane
+ * fluxes.  0 without a started solve (or for NULL / a poisoned context). */
+size_t lbm_state_bytes(const lbm_ctx* c);
+
+/* No counterpart in the paper.  Writes the snapshot of the current solve
+ * (lbm_state_bytes bytes) to host_out (caller-owned).  Synchronous.
+ * LBM_ERR_STATE without a started solve, LBM_ERR_INVALID_ARG if host_out is
+ * NULL or bytes is too small. */
+lbm_status lbm_get_state(lbm_ctx* c, void* host_out, size_t bytes);
+
+/* No counterpart in the paper.  Resumes from a snapshot taken by
+ * lbm_get_state: the context must have the same geometry and tensors and a
+ * solve started (lbm_start) with the same axis, lateral type, storage,
+ * check interval and walls; the snapshot replaces that solve's state, so a
+ * following lbm_run / lbm_advance continues the saved iteration (bit for
+ * bit the iterates of an uninterrupted run driven the same way).  host_in
+ * is read during the call only.  Synchronous.  LBM_ERR_INVALID_ARG for a
+ * snapshot of another solve or a truncated one. */
+lbm_status lbm_set_state(lbm_ctx* c, const void* host_in, size_t bytes);
 
 /* Plane sums Q[k] of the axial flux of Eq. 16 at the last check, the
  * integrand of Eq. 22 (n == N_axis doubles, host_out caller-owned). */
@@ -354,13 +384,17 @@ lbm_status lbm_nn_adam(float* p, const float* g, float* m, float* v, void* p_bf1
  * LBM_NOALLOC_MAX_YARNS + 1 64-bit bins (8.2 KB) that every GPU loading the
  * library holds until the process exits.  The first call on a device (the
  * current device) looks up that array's device address once; make that first
- * call before any stream capture.  Every call on a device shares the array
+ * call before any stream capture, and do not call it again on a device after
+ * cudaDeviceReset (the cached address would be stale).  Every call on a device shares the array
  * and clears the bins it uses; calls that overlap on the GPU (concurrent
  * streams or threads) race on it and must be serialised by the caller.
  *
  * nx, ny, nz: cell size (>= 1, product < 2^31).
  * g_rad, A, B, phi: as lbm_set_geometry_braid.
  * d_anchors: device, 16-byte aligned, n_max (x0, y0) double pairs.
+ *            d_anchors and d_phase must be device (or managed) memory of the
+ *            current device; anything else (a host pointer, say) returns
+ *            LBM_ERR_INVALID_ARG before any kernel runs.
  * n_max: 1 .. LBM_NOALLOC_MAX_YARNS; larger values return
  *        LBM_ERR_INVALID_ARG with a message saying so.
  * d_phase: device, nx*ny*nz uint8 output (x fastest), written on `stream`.

@@ -1019,6 +1019,121 @@ lbm_status lbm_get_history(lbm_ctx* c, double* host_out, int max_entries, int* n
     return LBM_OK;
 }
 
+// ---- checkpoint / resume ----
+// A snapshot holds everything the iteration carries from one step to the
+// next: the current distributions, the reference frames, the temperature
+// snapshot of the residual, the control block (iteration count, residual
+// bookkeeping), the check history and the last plane fluxes, behind a header
+// that names the solve it belongs to.
+namespace {
+
+struct StateHeader {
+    char magic[8];                         // "MRTLBMS1"
+    int32_t n[3], axis, lateral, fmt, NX, NY, NZ, pitch, check_every, pad;
+    double s, t_hot, t_cold;
+    int64_t f_bytes, cells;
+};
+
+size_t state_bytes(const lbm_ctx* c) {
+    const size_t esize = c->fmt == LBM_STORE_F32 ? 4 : 2;
+    const size_t cells = (size_t)c->pstride;
+    return sizeof(StateHeader) + 7 * cells * esize + sizeof(float) * 5 * (size_t)c->L.NZ +
+           sizeof(float) * cells + sizeof(Ctl) + sizeof(double) * 4 * kHistCap +
+           sizeof(double) * (size_t)c->L.NZ;
+}
+
+StateHeader state_header(const lbm_ctx* c) {
+    StateHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, "MRTLBMS1", 8);
+    for (int i = 0; i < 3; ++i) h.n[i] = c->n[i];
+    h.axis = c->axis;
+    h.lateral = c->lateral;
+    h.fmt = c->fmt;
+    h.NX = c->L.NX;
+    h.NY = c->L.NY;
+    h.NZ = c->L.NZ;
+    h.pitch = c->L.pitch;
+    h.check_every = c->opts.check_every;
+    h.s = c->s;
+    h.t_hot = c->opts.t_hot;
+    h.t_cold = c->opts.t_cold;
+    h.cells = c->pstride;
+    h.f_bytes = 7 * c->pstride * (c->fmt == LBM_STORE_F32 ? 4 : 2);
+    return h;
+}
+
+}  // namespace
+
+size_t lbm_state_bytes(const lbm_ctx* c) {
+    if (!c || c->poisoned || !c->started) return 0;
+    return state_bytes(c);
+}
+
+lbm_status lbm_get_state(lbm_ctx* c, void* host_out, size_t bytes) {
+    CHECK_CTX(c);
+    if (!c->started) return fail(c, LBM_ERR_STATE, "no solve state to save");
+    if (!host_out || bytes < state_bytes(c))
+        return fail(c, LBM_ERR_INVALID_ARG, "host_out must hold lbm_state_bytes() = %zu bytes",
+                    state_bytes(c));
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const StateHeader h = state_header(c);
+    char* p = static_cast<char*>(host_out);
+    std::memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    cudaStream_t st = c->stream;
+    const size_t cells = (size_t)c->pstride;
+    CUDA_TRY(c, cudaMemcpyAsync(p, c->d_f[c->cur], (size_t)h.f_bytes, cudaMemcpyDeviceToHost, st));
+    p += h.f_bytes;
+    CUDA_TRY(c, cudaMemcpyAsync(p, c->d_ref, sizeof(float) * 5 * c->L.NZ, cudaMemcpyDeviceToHost, st));
+    p += sizeof(float) * 5 * c->L.NZ;
+    CUDA_TRY(c, cudaMemcpyAsync(p, c->d_tsnap, sizeof(float) * cells, cudaMemcpyDeviceToHost, st));
+    p += sizeof(float) * cells;
+    CUDA_TRY(c, cudaMemcpyAsync(p, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    p += sizeof(Ctl);
+    CUDA_TRY(c, cudaMemcpyAsync(p, c->d_hist, sizeof(double) * 4 * kHistCap, cudaMemcpyDeviceToHost, st));
+    p += sizeof(double) * 4 * kHistCap;
+    CUDA_TRY(c, cudaMemcpyAsync(p, c->d_Q, sizeof(double) * c->L.NZ, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_ctx* c, const void* host_in, size_t bytes) {
+    CHECK_CTX(c);
+    if (!c->started) return fail(c, LBM_ERR_STATE, "call lbm_start for the same solve first");
+    if (!host_in || bytes < sizeof(StateHeader))
+        return fail(c, LBM_ERR_INVALID_ARG, "host_in is NULL or too short");
+    StateHeader h;
+    std::memcpy(&h, host_in, sizeof h);
+    const StateHeader want = state_header(c);
+    if (std::memcmp(h.magic, want.magic, 8) != 0)
+        return fail(c, LBM_ERR_INVALID_ARG, "not a solver state snapshot");
+    if (std::memcmp(&h, &want, sizeof h) != 0)
+        return fail(c, LBM_ERR_INVALID_ARG, "the snapshot belongs to another solve (cell size, axis, "
+                                            "lateral type, storage, check interval, walls or scale differ)");
+    if (bytes < state_bytes(c)) return fail(c, LBM_ERR_INVALID_ARG, "the snapshot is truncated");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const char* p = static_cast<const char*>(host_in) + sizeof h;
+    cudaStream_t st = c->stream;
+    const size_t cells = (size_t)c->pstride;
+    c->cur = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_f[0], p, (size_t)h.f_bytes, cudaMemcpyHostToDevice, st));
+    p += h.f_bytes;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_ref, p, sizeof(float) * 5 * c->L.NZ, cudaMemcpyHostToDevice, st));
+    p += sizeof(float) * 5 * c->L.NZ;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_tsnap, p, sizeof(float) * cells, cudaMemcpyHostToDevice, st));
+    p += sizeof(float) * cells;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_ctl, p, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    p += sizeof(Ctl);
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_hist, p, sizeof(double) * 4 * kHistCap, cudaMemcpyHostToDevice, st));
+    p += sizeof(double) * 4 * kHistCap;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_Q, p, sizeof(double) * c->L.NZ, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_plane_cnt, 0, sizeof(int) * c->L.NZ, st));
+    lbm_status s2 = read_ctl(c, st);
+    if (s2 != LBM_OK) return s2;
+    return LBM_OK;
+}
+
 lbm_status lbm_get_geometry(lbm_ctx* c, uint8_t* host_out) {
     CHECK_CTX(c);
     if (!host_out) return fail(c, LBM_ERR_INVALID_ARG, "host_out is NULL");

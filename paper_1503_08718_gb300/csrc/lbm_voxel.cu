@@ -222,7 +222,10 @@ constexpr int kMaxDevices = 64;
 // calls on a device share it.
 static __device__ __align__(256) unsigned long long g_noalloc_hist[kNoAllocMaxYarns + 1];
 
-// Device address of g_noalloc_hist per device, looked up once per device.
+// Device address of g_noalloc_hist per device, looked up once per device
+// (by the first call on it).  The address holds for the life of the device's
+// primary context: a process that resets the device (cudaDeviceReset) must
+// not call this entry point again.
 unsigned long long* g_hist_addr[kMaxDevices] = {};
 std::mutex g_hist_mutex;
 
@@ -263,6 +266,22 @@ extern "C" lbm_status lbm_braid_voxelize_noalloc(int nx, int ny, int nz, double 
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         put_msg(err, err_len, e != cudaSuccess ? cudaGetErrorString(e) : "device index too large");
         return LBM_ERR_CUDA;
+    }
+    // both buffers must be memory this device can address: a host pointer
+    // passed by mistake would otherwise fault inside the kernels
+    {
+        const void* ptrs[2] = {d_anchors, d_phase};
+        for (const void* p : ptrs) {
+            cudaPointerAttributes pa;
+            const cudaError_t ea = cudaPointerGetAttributes(&pa, p);
+            if (ea != cudaSuccess || !(pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) ||
+                (pa.type == cudaMemoryTypeDevice && pa.device != dev)) {
+                cudaGetLastError();
+                put_msg(err, err_len, "d_anchors and d_phase must be device (or managed) memory of the "
+                                      "current device");
+                return LBM_ERR_INVALID_ARG;
+            }
+        }
     }
     unsigned long long* hist = nullptr;
     {

@@ -171,3 +171,14 @@ def braid_sweep_cells(n_cells: int = 64, seed0: int = 1000):
                           g_deg=ang, seed=seed0 + c))
     return cells
 
+
+
+def warm_cell_params(seed: int, g_range=(20.0, 45.0), phi_range=(0.30, 0.60)):
+    """Braiding angle and yarn fraction of the seeded braided cells of the
+    learned warm start (training, evaluation and the combined-form batch):
+    splitmix64(10000 + seed) draws g in U(20, 45) deg, then phi in
+    U(0.30, 0.60); the yarn anchors come from braid_anchors(..., seed)."""
+    r = SplitMix64(10_000 + int(seed))
+    g = g_range[0] + (g_range[1] - g_range[0]) * r.uniform()
+    phi = phi_range[0] + (phi_range[1] - phi_range[0]) * r.uniform()
+    return g, phi

@@ -129,6 +129,9 @@ _PROTOS = {
     "lbm_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "lbm_create_with_workspace": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(_ctx_p)]),
+    "lbm_state_bytes": (ctypes.c_size_t, [_ctx_p]),
+    "lbm_get_state": (ctypes.c_int, [_ctx_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "lbm_set_state": (ctypes.c_int, [_ctx_p, ctypes.c_void_p, ctypes.c_size_t]),
     "lbm_last_error": (ctypes.c_char_p, [_ctx_p]),
     "lbm_destroy": (None, [_ctx_p]),
 }
@@ -282,6 +285,20 @@ def lbm_braid_voxelize_noalloc(nx: int, ny: int, nz: int, g_rad: float, A: float
                                            d_phase, ctypes.byref(used), ctypes.byref(frac),
                                            stream, msg, len(msg))
     return st, used.value, frac.value, msg.value.decode()
+
+
+def lbm_state_bytes(ctx) -> int:
+    return int(load().lbm_state_bytes(ctx))
+
+
+def lbm_get_state(ctx, out: np.ndarray) -> int:
+    assert out.dtype == np.uint8 and out.flags.c_contiguous
+    return load().lbm_get_state(ctx, out.ctypes.data, out.nbytes)
+
+
+def lbm_set_state(ctx, state: np.ndarray) -> int:
+    state = np.ascontiguousarray(state, dtype=np.uint8)
+    return load().lbm_set_state(ctx, state.ctypes.data, state.nbytes)
 
 
 def lbm_last_error(ctx) -> str:
@@ -460,6 +477,14 @@ class Solver:
         st, h = lbm_get_history(self.h)
         self._ok(st)
         return h
+
+    def get_state(self) -> np.ndarray:
+        out = np.empty(lbm_state_bytes(self.h), np.uint8)
+        self._ok(lbm_get_state(self.h, out))
+        return out
+
+    def set_state(self, state: np.ndarray):
+        self._ok(lbm_set_state(self.h, state))
 
     def plane_flux(self, n_axis: int) -> np.ndarray:
         out = np.empty(n_axis, np.float64)

@@ -74,3 +74,19 @@ def test_noalloc_voxeliser_rejects_too_many_yarns(torch_cuda):
         8, 8, 4, 0.5, 10.0, 6.0, d_anchors.data_ptr(), n, 0.1, d_phase.data_ptr(), None)
     assert st == lbm.LBM_ERR_INVALID_ARG
     assert "1024" in msg
+
+
+def test_noalloc_voxeliser_rejects_host_pointers(torch_cuda):
+    """A host buffer passed where device memory is expected is refused on
+    the host (LBM_ERR_INVALID_ARG) before any kernel could touch it."""
+    torch = torch_cuda
+    anchors = np.ascontiguousarray(I.braid_anchors(8, 8, 3, n_max=16))
+    host_phase = np.zeros((4, 8, 8), np.uint8)
+    d_anchors = torch.from_numpy(anchors).to("cuda")
+    d_phase = torch.empty((4, 8, 8), dtype=torch.uint8, device="cuda")
+    for a_ptr, p_ptr in ((anchors.ctypes.data, d_phase.data_ptr()),
+                         (d_anchors.data_ptr(), host_phase.ctypes.data)):
+        st, _, _, msg = lbm.lbm_braid_voxelize_noalloc(
+            8, 8, 4, 0.5, 10.0, 6.0, a_ptr, 16, 0.1, p_ptr, None)
+        assert st == lbm.LBM_ERR_INVALID_ARG
+        assert "device" in msg
