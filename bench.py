@@ -145,7 +145,7 @@ def make_cell(lbm, I, device):
     return S, lam, used, frac
 
 
-def kernel_launch_us(S, opts, stream, steps_per_launch, n=200, warm=20):
+def kernel_launch_us(S, opts, stream, steps_per_launch, n=200, warm=20, axis=2, lateral=0):
     """Average device time of one launch of the plain step kernel (two steps
     per launch when fused): n launches issued by lbm_advance are captured
     into a CUDA graph on the solver's stream (so stream-launch gaps are not
@@ -153,7 +153,7 @@ def kernel_launch_us(S, opts, stream, steps_per_launch, n=200, warm=20):
     even, so a replay ends in the buffer it started from.  Falls back to
     timing the launches directly if capture is unavailable."""
     import torch
-    S.start(2, 0, opts)
+    S.start(axis, lateral, opts)
     S.advance(warm * steps_per_launch)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -179,35 +179,165 @@ def kernel_launch_us(S, opts, stream, steps_per_launch, n=200, warm=20):
     return e0.elapsed_time(e1) * 1000.0 / n, n, mode
 
 
-def time_to_keff(lbm, S, stream, iters_ref=250_000, rel=1e-4):
-    """Time to k_eff within `rel` of the reference on the bench cell from the
-    linear start: the first check after which every later k_eff stays within
-    rel of the FP32 value after iters_ref iterations, times the measured
-    device time per iteration.  For FP32 and for 16-bit storage."""
-    out = {}
-    k_ref = None
+REFERENCE_FILE = os.path.join(ROOT, "tests", "golden", "keff_reference.json")
+
+
+def reference_keff(label, phase):
+    """Converged FP64 oracle value k* of a cell, written by
+    tests/golden/make_keff_reference.py, if that file holds the cell and its
+    phase map hash matches the one voxelised here."""
+    import hashlib
+    try:
+        with open(REFERENCE_FILE) as fh:
+            ent = json.load(fh)["cells"][label]
+    except (OSError, KeyError, ValueError):
+        return None
+    if not ent.get("converged") or ent["phase_sha256"] != hashlib.sha256(phase.tobytes()).hexdigest():
+        return None
+    return ent
+
+
+def first_within(h, k_ref, rel):
+    """Index of the first check after which every later k_eff stays within
+    rel of k_ref, or None."""
+    err = np.abs(h[:, 1] / k_ref - 1.0)
+    bad = np.nonzero(err > rel)[0]
+    first = 0 if bad.size == 0 else int(bad[-1]) + 1
+    return first if first < len(h) else None
+
+
+def time_to_keff(lbm, S, stream, iters=60_000, rel=1e-4):
+    """Time to k_eff within `rel` of the converged FP64 oracle value k* on the
+    bench cell from the linear start, for FP32 and 16-bit storage: the first
+    check after which every later k_eff stays within rel of k*, times the
+    measured device time per iteration (every check interval is the same
+    work).  Without a stored k* for this cell, the FP32 value after 250 000
+    iterations stands in (k_ref_source says which)."""
+    ref = reference_keff("braid128x128x256_z", S.geometry())
+    out = {"rel": rel}
+    if ref is not None:
+        k_ref = ref["k_star"]
+        out.update(k_ref=k_ref, k_ref_source="FP64 oracle, converged to R_Q <= %g in %d iterations"
+                   % (ref["rq_tol"], ref["iters"]))
+    else:
+        o = S.opts(tol=0.0, max_iters=250_000, check_every=K)
+        o.stream = int(stream.cuda_stream)
+        S.start(2, 0, o)
+        k_ref = S.run().k_eff
+        out.update(k_ref=k_ref, k_ref_source="GPU FP32 after 250000 iterations (no oracle k* stored)")
     for name in ("f32", "bf16", "f16"):
-        o = S.opts(tol=0.0, max_iters=iters_ref, check_every=K, storage=STORAGE[name])
+        o = S.opts(tol=0.0, max_iters=iters, check_every=K, storage=STORAGE[name])
         o.stream = int(stream.cuda_stream)
         S.start(2, 0, o)
         info = S.run()
         h = S.history()
-        if k_ref is None:
-            k_ref = float(h[-1, 1])
-        err = np.abs(h[:, 1] / k_ref - 1.0)
-        bad = np.nonzero(err > rel)[0]
-        first = 0 if bad.size == 0 else int(bad[-1]) + 1
+        first = first_within(h, k_ref, rel)
         ms_per_iter = info.elapsed_ms / info.iters
-        reached = first < len(h)
-        n_it = int(h[first, 0]) if reached else None
-        out[name] = {"iters": n_it, "ms": n_it * ms_per_iter if reached else None,
-                     "ms_per_iter": ms_per_iter,
+        n_it = int(h[first, 0]) if first is not None else None
+        out[name] = {"iters": n_it, "ms": n_it * ms_per_iter if n_it else None,
+                     "ms_per_iter": ms_per_iter, "iters_run": int(info.iters),
+                     "k_final": float(h[-1, 1]),
                      "k_final_rel_vs_ref": float(h[-1, 1] / k_ref - 1.0)}
-    out["k_ref"] = k_ref
-    out["k_ref_iters"] = iters_ref
-    out["rel"] = rel
     if out["f32"]["ms"] and out["bf16"]["ms"]:
         out["speedup_bf16_vs_f32"] = out["f32"]["ms"] / out["bf16"]["ms"]
+    return out
+
+
+def solve_glups(S, axis, lateral, opts, n_vox):
+    """GLUPS of one solve (lbm_start + lbm_run), device time from the
+    solver's CUDA events."""
+    S.start(axis, lateral, opts)
+    info = S.run()
+    return n_vox * info.iters / info.elapsed_ms / 1e6, info
+
+
+def config1_layered(lbm, I, stream):
+    """The 32^3 layered cell (z layers of 8 voxels, matrix 0.2, yarn 6.0 /
+    0.8 at 30 deg from z in the xz-plane), z axis, periodic laterals, to
+    R_T <= 1e-8: iterations, device time, GLUPS and k_eff against the exact
+    94/245.  The state (1.9 MB) is L2-resident: GLUPS, no HBM roofline."""
+    yarn = I.transversely_isotropic(6.0, 0.8, I.axis_in_xz_from_z(30.0))
+    lam = np.stack([I.isotropic(0.2), yarn])
+    with lbm.Solver(32, 32, 32) as S:
+        S.set_geometry(I.layered_phase(32, 32, 32), 2)
+        S.set_tensors(lam)
+        o = S.opts(tol=1e-8)
+        o.stream = int(stream.cuda_stream)
+        S.start(2, 0, o)                      # warm-up (graph build)
+        S.run()
+        g, info = solve_glups(S, 2, 0, o, 32 ** 3)
+        exact = 94.0 / 245.0
+        return {"workload": "layered 32^3, z axis, periodic, FP32, to R_T <= 1e-8",
+                "glups": g, "iters": int(info.iters), "ms": info.elapsed_ms,
+                "k_eff": info.k_eff, "k_rel_vs_exact": info.k_eff / exact - 1.0,
+                "plan": S.launch_plan(), "l2_resident": True}
+
+
+def config2_all_solves(lbm, S, stream, n_vox, iters=1000):
+    """The bench cell along x, y and z with periodic and adiabatic laterals
+    (FP32, fused pairs where the rows allow them): GLUPS of each solve."""
+    rows = []
+    for axis in (0, 1, 2):
+        for lateral in (0, 1):
+            o = S.opts(tol=0.0, max_iters=iters)
+            o.stream = int(stream.cuda_stream)
+            solve_glups(S, axis, lateral, o, n_vox)       # warm-up (graph build)
+            g, info = solve_glups(S, axis, lateral, o, n_vox)
+            rows.append({"axis": "xyz"[axis], "lateral": ("periodic", "adiabatic")[lateral],
+                         "glups": g, "iters": int(info.iters), "k_eff": info.k_eff,
+                         "steps_per_launch": S.launch_plan()["steps_per_launch"]})
+    return rows
+
+
+def config4_precision(lbm, I, stream, peak, with_oracle, iters=2000, n_check=20):
+    """The 256x256x512 braid (35 deg, yarn fraction 0.50, seed 7), every axis,
+    periodic laterals, FP32 / BF16 / FP16 storage: GLUPS over `iters`
+    iterations, the dominant kernel's average launch time and roofline
+    fraction (57 or 29 B per update), and the k_eff error against the FP64
+    oracle after n_check iterations from the linear start."""
+    n = (256, 256, 512)
+    n_vox = n[0] * n[1] * n[2]
+    anchors = I.braid_anchors(n[0], n[1], 7, n_max=1024)
+    lam = I.braid_tensors(35.0)
+    out = {"workload": "braid 256x256x512 g=35deg phi=0.50 seed=7, periodic laterals",
+           "per_axis": []}
+    ph_ref = None
+    if with_oracle:
+        from oracle import oracle as O
+        ph_ref, _, _ = O.braid_phase(*n, math.radians(35.0), anchors, 0.50)
+    with lbm.Solver(*n) as S:
+        S.set_geometry_braid(math.radians(35.0), anchors, 0.50)
+        S.set_tensors(lam)
+        if ph_ref is not None:
+            out["voxeliser_bit_exact"] = bool(np.array_equal(S.geometry(), ph_ref))
+        for axis in (0, 1, 2):
+            k_oracle = None
+            if ph_ref is not None:
+                L = O.Lattice(ph_ref, lam, O.lattice_scale(lam), axis, 0)
+                L.init_linear()
+                L.step(n_check)
+                k_oracle = L.k_eff()[0]
+                del L
+            for name in ("f32", "bf16", "f16"):
+                o = S.opts(tol=0.0, max_iters=iters, storage=STORAGE[name])
+                o.stream = int(stream.cuda_stream)
+                solve_glups(S, axis, 0, o, n_vox)             # warm-up
+                g, info = solve_glups(S, axis, 0, o, n_vox)
+                spl = S.launch_plan()["steps_per_launch"]
+                us, _, _ = kernel_launch_us(S, o, stream, spl, n=100, warm=10, axis=axis)
+                moved = BYTES_PER_LUP[name] * n_vox
+                row = {"axis": "xyz"[axis], "storage": name, "glups": g,
+                       "steps_per_launch": spl, "dominant_kernel_us": us,
+                       "roofline_frac": moved * spl / (us * 1e-6) / 1e9 / peak,
+                       "frac_moved": moved / (us * 1e-6) / 1e9 / peak}
+                if k_oracle is not None:
+                    o2 = S.opts(storage=STORAGE[name])
+                    o2.stream = int(stream.cuda_stream)
+                    S.start(axis, 0, o2)
+                    S.advance(n_check - 1)
+                    k = S.check().k_eff
+                    row["k_rel_vs_oracle_at_%d" % n_check] = k / k_oracle - 1.0
+                out["per_axis"].append(row)
     return out
 
 
@@ -230,6 +360,7 @@ def sweep(lbm, I, n_cells=64, iters=500):
     info = B.solve(0, opts)
     batched = info.total_updates / info.elapsed_ms / 1e6
     B.close()
+    plans = []
     seq_ms, seq_upd = 0.0, 0
     for ph, lam in phases:
         nz, ny, nx = ph.shape
@@ -237,14 +368,126 @@ def sweep(lbm, I, n_cells=64, iters=500):
             S1.set_geometry(ph, 5)
             S1.set_tensors(lam)
             for axis in (0, 1, 2):
+                S1.solve(axis, 0, opts)                   # warm-up (graph build)
                 r = S1.solve(axis, 0, opts)
                 seq_ms += r.elapsed_ms
                 seq_upd += r.iters * ph.size
+                plans.append(S1.launch_plan()["steps_per_launch"])
     return {"solves": 3 * len(cells), "cells": len(cells),
             "voxels_per_axis": int(sum(p.size for p, _ in phases)), "iters_per_solve": iters,
             "batched_glups": batched, "sequential_glups": seq_upd / seq_ms / 1e6,
             "batched_ms": info.elapsed_ms, "sequential_ms": seq_ms,
-            "block_threads": info.block_threads, "unit": "GLUPS"}
+            "block_threads": info.block_threads,
+            "batched_steps_per_launch": info.steps_per_launch,
+            "sequential_fused_solves": int(sum(p == 2 for p in plans)),
+            "batched_over_sequential": batched / (seq_upd / seq_ms / 1e6), "unit": "GLUPS"}
+
+
+WARM_WEIGHTS = os.path.join(ROOT, "paper_1503_08718_gb300", "weights", "warmnet_braid64.npz")
+COMBINED_SEEDS = tuple(range(7000, 7016))
+
+
+def combined_form(lbm, I, stream, rel=1e-4, budget=40_000):
+    """The combined form against the plain FP32 solver on 16 held-out 64^3
+    braided cells (seeds 7000..7015 of the warm-start distribution, z axis,
+    periodic laterals), each with its converged FP64 oracle value k*.
+
+    plain: the single-solve FP32 path (two steps per launch), one cell after
+    another from the linear start; per cell the device time until k_eff stays
+    within rel of k* (history x device time per iteration), summed.
+    Batched variants: one graph launch for all 16 cells; their time is the
+    device time (per-check timestamps) at which the last solve entered the
+    band for good, plus, for warm starts, the network's batched inference
+    (one forward pass over the 16 cells, CUDA events).  Reported: batched
+    FP32 linear start, batched FP32 warm start, and the combined form,
+    batched + warm start + BF16 storage."""
+    import torch
+    from paper_1503_08718_gb300 import warmstart as W
+
+    if not os.path.exists(WARM_WEIGHTS):
+        return {"unavailable": "no trained warm-start weights"}
+    cells = []
+    for s in COMBINED_SEEDS:
+        g, phi = I.warm_cell_params(s)
+        with lbm.Solver(64, 64, 64) as V:
+            V.set_geometry_braid(math.radians(g), I.braid_anchors(64, 64, s, n_max=256), phi)
+            ph = V.geometry()
+        ref = reference_keff(f"warm64_{s}", ph)
+        if ref is not None:
+            cells.append((ph, I.braid_tensors(g), ref["k_star"]))
+    if len(cells) < 4:
+        return {"unavailable": "fewer than 4 of the cells have a converged oracle k* stored"}
+    out = {"workload": f"{len(cells)} held-out braids 64^3 (seeds 7000-7015 with a stored k*), "
+                       "z axis, periodic",
+           "rel": rel, "budget_iters": budget}
+    # plain FP32, one cell at a time
+    tot, iters = 0.0, []
+    for ph, lam, kst in cells:
+        with lbm.Solver(64, 64, 64) as S:
+            S.set_geometry(ph, 5)
+            S.set_tensors(lam)
+            o = S.opts(tol=0.0, max_iters=budget)
+            o.stream = int(stream.cuda_stream)
+            S.start(2, 0, o)
+            S.run()                                   # warm-up (graph build)
+            S.start(2, 0, o)
+            info = S.run()
+            h = S.history()
+            f = first_within(h, kst, rel)
+            if f is None:
+                return {"unavailable": "plain FP32 did not reach the band within the budget"}
+            tot += info.elapsed_ms / info.iters * h[f, 0]
+            iters.append(int(h[f, 0]))
+    out["plain_f32_sequential"] = {"ms": tot, "iters_mean": float(np.mean(iters))}
+    # network inference for all cells at once
+    net = W.WarmNet()
+    net.load(WARM_WEIGHTS)
+    phs = np.stack([c[0] for c in cells])
+    x0, tl = net.make_input(phs, [c[1] for c in cells])
+    vol = (len(cells), 64, 64, 64)
+    net.forward(x0, vol, tl)                          # warm-up (module load)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    pred, _ = net.forward(x0, vol, tl)
+    e1.record()
+    torch.cuda.synchronize()
+    infer_ms = e0.elapsed_time(e1)
+    T0 = pred.view(*vol).cpu().numpy().astype(np.float32)
+    out["inference_ms"] = infer_ms
+
+    def batched(storage, warm):
+        B = lbm.Batch()
+        for i, (ph, lam, _) in enumerate(cells):
+            B.add(ph, lam, 2)
+            if warm:
+                B.set_initial(i, np.ascontiguousarray(T0[i]))
+        info = B.solve(0, lbm.Solver.opts(tol=0.0, max_iters=budget, storage=storage))
+        worst, its, kerr = 0.0, [], []
+        for i, (_, _, kst) in enumerate(cells):
+            h = B.history(i)
+            f = first_within(h, kst, rel)
+            if f is None:
+                B.close()
+                return None
+            worst = max(worst, h[f, 4])
+            its.append(int(h[f, 0]))
+            kerr.append(abs(h[-1, 1] / kst - 1.0))
+        B.close()
+        return {"ms": worst + (infer_ms if warm else 0.0), "batch_ms_to_band": worst,
+                "iters_mean": float(np.mean(its)), "iters_max": int(max(its)),
+                "k_final_max_rel_err": float(max(kerr)),
+                "steps_per_launch": info.steps_per_launch, "block_threads": info.block_threads}
+
+    out["batched_f32_linear"] = batched(lbm.LBM_STORE_F32, False)
+    out["batched_f32_warm"] = batched(lbm.LBM_STORE_F32, True)
+    out["combined_bf16_warm_batched"] = batched(lbm.LBM_STORE_BF16, True)
+    c = out["combined_bf16_warm_batched"]
+    if c:
+        out["combined_over_plain_time"] = c["ms"] / out["plain_f32_sequential"]["ms"]
+        out["warm_iters_saved"] = (1.0 - out["batched_f32_warm"]["iters_mean"] /
+                                   out["batched_f32_linear"]["iters_mean"]) if out["batched_f32_warm"] else None
+    return out
 
 
 def cpu_oracle_sample(seconds_target=15.0):
@@ -416,8 +659,9 @@ def run_ours(args):
     glups = lups / (ms / 1000.0) / 1e9
     # per check interval: the first step, fused pairs (FP32, the cell's 128 x
     # 128 rows allow them), the remaining single steps and the check step
+    plan = S.launch_plan()
     R = K - 2
-    pairs = 2 * (R // 4) if (args.storage == "f32" and args.fuse) else 0
+    pairs = 2 * (R // 4) if plan["steps_per_launch"] == 2 else 0
     launches_per_interval = 2 + pairs + (R - 2 * pairs)
     launches_per_step = (iters // K) * launches_per_interval + 2   # + permute, init
     # roofline of the dominant kernel: the fused two-step kernel in FP32,
@@ -482,8 +726,15 @@ def run_ours(args):
 
     extras = {}
     if not args.no_extras:
+        extras["configs"] = {
+            "cfg1_layered32": config1_layered(lbm, I, stream),
+            "cfg2_bench_cell_all_solves": config2_all_solves(lbm, S, stream, n_vox),
+            "cfg3_sweep": sweep(lbm, I),
+            "cfg4_braid256x256x512": config4_precision(lbm, I, stream, peak,
+                                                       with_oracle=not args.skip_cpu),
+        }
         extras["time_to_keff"] = time_to_keff(lbm, S, stream)
-        extras["sweep"] = sweep(lbm, I)
+        extras["combined_form"] = combined_form(lbm, I, stream)
 
     # end to end through the public API with host buffers
     anchors = I.braid_anchors(NX, NY, SEED, n_max=NMAX)
@@ -549,6 +800,7 @@ def run_ours(args):
                     "h2d_bytes_per_step": n_vox + lam.nbytes,
                     "d2h_bytes_per_step": 4 * n_vox + 8},
             "gpu_launches": launches_per_step * args.steps,
+            "launch_plan": plan,
             "clocks": clk.summary(),
             "k_eff_after_step": info.k_eff,
             "storage_variants": variants or None,

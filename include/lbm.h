@@ -87,11 +87,13 @@ typedef struct {
                                launches each interval and reads the stop flag after it
                                (same kernels and results; for tools that cannot trace
                                conditional graphs) */
-    int32_t fuse;           /* 1: FP32 plain steps run two at a time in one kernel
-                               (temporal blocking; needs rows of nx = 128 or 256 nodes
-                               and ny a multiple of 4 or 8 respectively, after the axis
-                               permutation, else single steps); identical results;
-                               the default; 0: single steps only */
+    int32_t fuse;           /* 1 (default): FP32 plain steps run two at a time in one
+                               kernel (temporal blocking) when the canonical rows hold a
+                               multiple of 4 nodes (lbm_start orders the lateral axes to
+                               allow it); identical results; a batch's autotuner then
+                               also times single steps and keeps the faster.  2: as 1,
+                               but a batch uses two-step launches whenever every solve
+                               allows them.  0: single steps only */
     int32_t reserved;
     const float* t_init;    /* host, nx*ny*nz initial T field in the original axis
                                order, or NULL for the linear profile between walls */
@@ -222,6 +224,20 @@ lbm_status lbm_get_state(lbm_ctx* c, void* host_out, size_t bytes);
  * snapshot of another solve or a truncated one. */
 lbm_status lbm_set_state(lbm_ctx* c, const void* host_in, size_t bytes);
 
+/* No counterpart in the paper (how the solve is laid out and launched).
+ * After lbm_start: the canonical layout (rows of nx nodes, the temperature
+ * axis nz last; pitch = padded row length) and the kernel plan of the plain
+ * steps: steps_per_launch 2 when FP32 plain steps run as fused pairs
+ * (temporal blocking) with tiles of tile_rows rows, zchunk planes and
+ * block_threads threads per block, else 1 (single steps; tile fields 0). */
+typedef struct {
+    int32_t nx, ny, nz, pitch;
+    int32_t steps_per_launch;
+    int32_t tile_rows, zchunk, block_threads;
+} lbm_launch_plan;
+
+lbm_status lbm_get_launch_plan(const lbm_ctx* c, lbm_launch_plan* out);
+
 /* Plane sums Q[k] of the axial flux of Eq. 16 at the last check, the
  * integrand of Eq. 22 (n == N_axis doubles, host_out caller-owned). */
 lbm_status lbm_get_plane_flux(const lbm_ctx* c, double* host_out, int n);
@@ -251,8 +267,12 @@ typedef struct {
     int32_t n_converged;    /* solves that met R_T <= tol */
     int64_t total_updates;  /* lattice updates performed (voxels x iterations, summed) */
     double elapsed_ms;      /* device time of the graph launch (CUDA events) */
-    int32_t block_threads;  /* block size the autotuner picked (128, 256 or 512) */
+    int32_t block_threads;  /* block size the autotuner picked for the plain steps: single
+                               steps (128, 256 or 512 threads) or FP32 two-step launches
+                               (256 .. 640 threads; see lbm_batch_solve) */
     int32_t status;         /* LBM_OK if every solve converged, else LBM_ERR_NOT_CONVERGED */
+    int32_t steps_per_launch; /* 2 if the plain steps ran as two-step launches, else 1 */
+    int32_t reserved;
 } lbm_batch_info;
 
 /* Creates an empty batch (for the sweeps of Section 5) on CUDA device
@@ -268,12 +288,17 @@ lbm_status lbm_batch_add(lbm_batch* b, int nx, int ny, int nz, const uint8_t* ph
 
 /* Solves every added problem (the sweeps of Section 5, Fig. 9) with one
  * lateral type and one set of options (each solve takes its own lattice
- * scale from its tensors unless opts.lattice_scale is set; t_init must be
- * NULL).  All solves stay resident
+ * scale from its tensors unless opts.lattice_scale is set; opts.t_init must
+ * be NULL: per-solve start fields come from lbm_batch_set_initial).  All
+ * solves stay resident
  * in device memory; one CUDA graph launch advances every unconverged solve by
  * whole check intervals until each has met tol or max_iters.  Before the
- * launch the block size is picked among 128, 256 and 512 threads by timing
- * steps of the batch.  Synchronous. */
+ * launch an autotuner times six plain steps of the batch itself for each
+ * candidate and keeps the fastest: single steps with 128, 256 or 512 threads
+ * per block, and (FP32 storage with opts.fuse, every solve's canonical rows a
+ * multiple of 4 nodes) two steps per launch with 256 .. 640 threads per
+ * block (tile height from the row width) and z chunks of 8, 16 or 32 planes.
+ * Every candidate computes the same iterates bit for bit.  Synchronous. */
 lbm_status lbm_batch_solve(lbm_batch* b, lbm_lateral lateral, const lbm_solve_opts* o,
                            lbm_batch_info* info);
 
@@ -284,6 +309,20 @@ lbm_status lbm_batch_result(const lbm_batch* b, int id, lbm_solve_info* info);
 /* Final temperature (Eq. 14) of solve `id` (nx*ny*nz floats, original axis
  * order, host_out caller-owned). */
 lbm_status lbm_batch_get_temperature(lbm_batch* b, int id, float* host_out);
+
+/* Initial temperature of solve `id` (host, nx*ny*nz floats in the original
+ * axis order, copied; NULL restores the linear profile): the solve starts
+ * from f^eq of this field (Eq. 6), e.g. a learned prediction of the steady
+ * field (the method needs only the steady state, Section 2.3).  Applies to
+ * the next lbm_batch_solve. */
+lbm_status lbm_batch_set_initial(lbm_batch* b, int id, const float* t_init);
+
+/* Convergence history of solve `id` after lbm_batch_solve: for each of its
+ * most recent min(checks, max_entries, 4096) checks, oldest first, five
+ * doubles (iteration, k_eff of Eq. 22, R_T, R_Q, device time in ms from the
+ * start of the batch's iteration to the end of that check) into host_out.
+ * *n_out (nullable) receives the number of entries.  Synchronous. */
+lbm_status lbm_batch_get_history(lbm_batch* b, int id, double* host_out, int max_entries, int* n_out);
 
 /* No counterpart in the paper.  Message of the last failed batch call
  * (batch-owned string). NULL-safe. */

@@ -35,8 +35,8 @@ struct BatchDesc {
     StepArgs a;          // src/dst/rsrc/rdst are filled in per launch
     void* f[2];          // distribution buffers
     float* ref;          // frames R_a, R_b, R_c, init tables [5][NZ]
-    int blocks;          // blocks of one step = blocks_per_plane * NZ
-    int pad;
+    int blocks;          // blocks of one single step = blocks_per_plane * NZ
+    int blocks2;         // blocks of one two-step launch (tiles x z chunks), 0 without
 };
 
 // argument variants per solve: buffer parity (2) x reference frame (AA, AB, BB)
@@ -45,8 +45,13 @@ constexpr int kVariants = 6;
 struct BatchCtl {
     int n_active;        // solves still iterating
     int total_blocks;    // blocks of the active solves
-    int pad[2];
+    unsigned long long t0;   // device time (ns) when the solve's graph launch began
 };
+
+constexpr int kBatchHistCap = 4096;   // checks kept per solve
+
+// Records the device time at which the batch's iteration starts.
+__global__ void batch_stamp_kernel(BatchCtl* bctl) { bctl->t0 = lbm::globaltimer_ns(); }
 
 // Block -> solve: prefix[s] = first block of the s-th active solve, order[s]
 // its solve index; prefix[n_active] = total.  Each solve has one ready-made
@@ -79,23 +84,57 @@ batch_step_kernel(const StepArgs* __restrict__ args, const int* __restrict__ pre
         lbm::step_body<FMT, PERIODIC, CHECK, true, THREADS>(a, local - z * a.blocks_per_plane, z, rseed);
 }
 
-// After a check: keep the solves that are not done, rebuild the prefix and
+// Two fused FP32 steps per launch over every active solve: block b finds its
+// solve in the prefix of two-step block counts and runs one tile (f2_fy rows,
+// f2_zchunk planes) of the single-solve two-step kernel's body.  Every block
+// of the launch has the same size; a solve whose rows hold fewer threads
+// leaves the rest idle.  flip reverses the block order and the chunks'
+// marching direction on alternate launches (a launch starts on what the
+// previous one wrote last).
+template <bool PERIODIC>
+__global__ void __launch_bounds__(lbm::F2_MAX_THREADS, 1)
+batch_fused2_kernel(const StepArgs* __restrict__ args, const int* __restrict__ prefix2,
+                    const int* __restrict__ order, const BatchCtl* __restrict__ bctl, int variant, int flip) {
+    const int n_active = bctl->n_active;
+    const int total = prefix2[n_active];
+    if ((int)blockIdx.x >= total) return;     // block of a solve that has converged
+    const int b = flip ? total - 1 - (int)blockIdx.x : (int)blockIdx.x;
+    int lo = 0, hi = n_active - 1;            // last s with prefix2[s] <= b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix2[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const StepArgs& a = args[order[lo] * kVariants + variant];
+    const int local = b - prefix2[lo];
+    const int bz = local / a.f2_bxy;
+    const int by = local - bz * a.f2_bxy;
+    float4* s_sa;
+    float2* s_sc;
+    float* fn = lbm::fused2_tables(a, 3 * lbm::f2_slot_rows(a.f2_fy) * a.pitch, &s_sa, &s_sc);
+    lbm::fused2_body<PERIODIC, 0>(a, fn, s_sa, s_sc, a.f2_fy, by, bz, a.f2_zchunk, flip);
+}
+
+// After a check: keep the solves that are not done, rebuild the prefixes and
 // set the while condition (any solve still active).
 __global__ void batch_control_kernel(const BatchDesc* __restrict__ descs, int n_solves,
-                                     int* __restrict__ prefix, int* __restrict__ order,
-                                     BatchCtl* __restrict__ bctl,
+                                     int* __restrict__ prefix, int* __restrict__ prefix2,
+                                     int* __restrict__ order, BatchCtl* __restrict__ bctl,
                                      cudaGraphConditionalHandle handle, int use_handle) {
     if (threadIdx.x != 0) return;
-    int n = 0, total = 0;
+    int n = 0, total = 0, total2 = 0;
     for (int s = 0; s < n_solves; ++s) {
         const Ctl* c = descs[s].a.ck.ctl;
         if (c->done) continue;
         order[n] = s;
         prefix[n] = total;
+        prefix2[n] = total2;
         total += descs[s].blocks;
+        total2 += descs[s].blocks2;
         ++n;
     }
     prefix[n] = total;
+    prefix2[n] = total2;
     bctl->n_active = n;
     bctl->total_blocks = total;
     if (use_handle) cudaGraphSetConditional(handle, n > 0 ? 1u : 0u);
@@ -107,6 +146,7 @@ struct Cell {
     int n_phases;
     std::vector<uint8_t> phase;
     std::vector<double> lambda;
+    std::vector<float> t_init;     // initial temperature (original order) or empty
 };
 
 }  // namespace
@@ -127,11 +167,15 @@ struct lbm_batch {
     std::vector<Layout> layouts;
     std::vector<double> scale;             // lattice scale s per solve
     int* d_prefix = nullptr;
+    int* d_prefix2 = nullptr;              // prefix of two-step block counts
     int* d_order = nullptr;
     BatchCtl* d_bctl = nullptr;
     Ctl* h_ctl = nullptr;                  // pinned, one per solve
     int fmt = 0, lateral = 0, threads = 256, K = 100;
     int max_blocks = 0, max_phases = 1;
+    bool fused = false;                    // plain steps as two-step launches
+    int f2_threads = 0, max_blocks2 = 0;
+    size_t f2_smem = 0;
     int cur = 0;
     bool solved = false;
     lbm_solve_opts opts{};
@@ -166,13 +210,14 @@ void free_device(lbm_batch* b) {
     cudaFree(b->d_descs);
     cudaFree(b->d_args);
     cudaFree(b->d_prefix);
+    cudaFree(b->d_prefix2);
     cudaFree(b->d_order);
     cudaFree(b->d_bctl);
     if (b->h_ctl) cudaFreeHost(b->h_ctl);
     b->arena = nullptr;
     b->d_descs = nullptr;
     b->d_args = nullptr;
-    b->d_prefix = b->d_order = nullptr;
+    b->d_prefix = b->d_prefix2 = b->d_order = nullptr;
     b->d_bctl = nullptr;
     b->h_ctl = nullptr;
     b->arena_bytes = 0;
@@ -222,9 +267,34 @@ cudaError_t launch_step(const lbm_batch* b, bool check, int parity, int frame, u
     return cudaGetLastError();
 }
 
+// Two FP32 steps of every active solve (state in buffer `parity`, frame BB).
+cudaError_t launch_pair(const lbm_batch* b, int parity, int flip, cudaStream_t st) {
+    const int variant = parity * 3 + 2;
+    if (b->lateral == LBM_LATERAL_PERIODIC)
+        batch_fused2_kernel<true><<<b->max_blocks2, b->f2_threads, b->f2_smem, st>>>(
+            b->d_args, b->d_prefix2, b->d_order, b->d_bctl, variant, flip);
+    else
+        batch_fused2_kernel<false><<<b->max_blocks2, b->f2_threads, b->f2_smem, st>>>(
+            b->d_args, b->d_prefix2, b->d_order, b->d_bctl, variant, flip);
+    return cudaGetLastError();
+}
+
+// Tile of a solve's two-step launch with blocks of `threads` threads: the
+// tallest tile whose rows fit the block.  False if the rows are not a
+// multiple of 4 nodes or a row needs more than a third of the block.
+bool f2_tile(int nx, int ny, int threads, int* fy, int* bxy) {
+    if (nx % 4) return false;
+    const int rows = threads / (nx / 4);
+    if (rows < 3) return false;
+    *fy = rows - 2;
+    *bxy = (ny + *fy - 1) / *fy;
+    return true;
+}
+
 // Lays out one solve inside the arena and writes its descriptor.
 struct Plan {
     size_t off_f[2], off_phase, off_tsnap, off_ref, off_part, off_Q, off_cnt, off_ctl, off_sb;
+    size_t off_hist, off_hist_t;
     size_t bytes;
 };
 
@@ -242,6 +312,8 @@ Plan plan_solve(const Layout& L, int n_phases, size_t esize, int bpp, size_t bas
     p.off_cnt = o; o = align256(o + (size_t)L.NZ * sizeof(int));
     p.off_ctl = o; o = align256(o + sizeof(Ctl));
     p.off_sb = o; o = align256(o + 2 * (size_t)n_phases * sizeof(float4));
+    p.off_hist = o; o = align256(o + 4 * (size_t)kBatchHistCap * sizeof(double));
+    p.off_hist_t = o; o = align256(o + (size_t)kBatchHistCap * sizeof(unsigned long long));
     p.bytes = o - base;
     return p;
 }
@@ -366,6 +438,14 @@ lbm_status lbm_batch_solve(lbm_batch* b, lbm_lateral lateral, const lbm_solve_op
             L.n[i] = c.n[i];
             L.perm[i] = perms[c.axis][i];
         }
+        // FP32 storage: order the lateral axes so that rows are a multiple
+        // of 4 nodes (two-step launches need it) and as short as possible
+        // (taller tiles per block); the relabelling is exact
+        if (op.storage == LBM_STORE_F32) {
+            const int a0 = c.n[L.perm[0]], a1 = c.n[L.perm[1]];
+            const bool ok0 = a0 % 4 == 0, ok1 = a1 % 4 == 0;
+            if ((ok1 && !ok0) || (ok0 && ok1 && a1 < a0)) std::swap(L.perm[0], L.perm[1]);
+        }
         L.NX = c.n[L.perm[0]];
         L.NY = c.n[L.perm[1]];
         L.NZ = c.n[L.perm[2]];
@@ -382,15 +462,21 @@ lbm_status lbm_batch_solve(lbm_batch* b, lbm_lateral lateral, const lbm_solve_op
     BCUDA(b, cudaMalloc((void**)&b->d_descs, sizeof(BatchDesc) * n_solves));
     BCUDA(b, cudaMalloc((void**)&b->d_args, sizeof(StepArgs) * kVariants * n_solves));
     BCUDA(b, cudaMalloc((void**)&b->d_prefix, sizeof(int) * (n_solves + 1)));
+    BCUDA(b, cudaMalloc((void**)&b->d_prefix2, sizeof(int) * (n_solves + 1)));
     BCUDA(b, cudaMalloc((void**)&b->d_order, sizeof(int) * n_solves));
     BCUDA(b, cudaMalloc((void**)&b->d_bctl, sizeof(BatchCtl)));
     BCUDA(b, cudaMallocHost((void**)&b->h_ctl, sizeof(Ctl) * n_solves));
 
     // per solve: geometry (permuted on the device), S_b = tau^-1, frames, init
     uint8_t* d_stage = nullptr;
-    size_t max_cells = 0;
-    for (auto& c : b->cells) max_cells = std::max(max_cells, c.phase.size());
+    float* d_tstage = nullptr;
+    size_t max_cells = 0, max_init = 0;
+    for (auto& c : b->cells) {
+        max_cells = std::max(max_cells, c.phase.size());
+        max_init = std::max(max_init, c.t_init.size());
+    }
     BCUDA(b, cudaMalloc((void**)&d_stage, max_cells));
+    if (max_init) BCUDA(b, cudaMalloc((void**)&d_tstage, sizeof(float) * max_init));
     b->descs.assign(n_solves, BatchDesc{});
     b->scale.assign(n_solves, 0.0);
     cudaStream_t st = b->stream;
@@ -431,13 +517,34 @@ lbm_status lbm_batch_solve(lbm_batch* b, lbm_lateral lateral, const lbm_solve_op
         }
         BCUDA(b, cudaMemcpyAsync(base + p.off_sb, sb.data(), sizeof(float4) * sb.size(),
                                  cudaMemcpyHostToDevice, st));
+        // initial frame: the plane means of the initial field on the
+        // quantum grid (the linear profile, or the solve's own start field)
+        std::vector<double> mean(L.NZ, 0.0);
+        if (!c.t_init.empty()) {
+            const size_t N = c.t_init.size();
+            for (size_t i = 0; i < N; ++i) {
+                const int cc[3] = {(int)(i % c.n[0]), (int)((i / c.n[0]) % c.n[1]),
+                                   (int)(i / ((size_t)c.n[0] * c.n[1]))};
+                mean[cc[L.perm[2]]] += c.t_init[i];
+            }
+            for (auto& m : mean) m /= (double)L.NX * (double)L.NY;
+        } else {
+            for (int z = 0; z < L.NZ; ++z)
+                mean[z] = op.t_hot + (op.t_cold - op.t_hot) * ((double)z + 0.5) / (double)L.NZ;
+        }
         std::vector<float> ref(5 * (size_t)L.NZ);
         for (int z = 0; z < L.NZ; ++z) {
             const double T0 = op.t_hot + (op.t_cold - op.t_hot) * ((double)z + 0.5) / (double)L.NZ;
-            const double r = std::nearbyint(T0 / quantum) * quantum;
+            const double r = std::nearbyint(mean[z] / quantum) * quantum;
             ref[z] = ref[L.NZ + z] = ref[2 * L.NZ + z] = (float)r;
             ref[3 * L.NZ + z] = (float)(T0 - r);
             ref[4 * L.NZ + z] = (float)(T0 - t_ref);
+        }
+        const float* tinit = nullptr;
+        if (!c.t_init.empty()) {
+            BCUDA(b, cudaMemcpyAsync(d_tstage, c.t_init.data(), sizeof(float) * c.t_init.size(),
+                                     cudaMemcpyHostToDevice, st));
+            tinit = d_tstage;
         }
         float* d_ref = reinterpret_cast<float*>(base + p.off_ref);
         BCUDA(b, cudaMemcpyAsync(d_ref, ref.data(), sizeof(float) * ref.size(), cudaMemcpyHostToDevice, st));
@@ -450,13 +557,13 @@ lbm_status lbm_batch_solve(lbm_batch* b, lbm_lateral lateral, const lbm_solve_op
         float* tsnap = reinterpret_cast<float*>(base + p.off_tsnap);
         if (op.storage == LBM_STORE_BF16)
             lbm::init_kernel<1><<<grid_1d(cells), 256, 0, st>>>(base + p.off_f[0], tsnap, cells, L, d_ref,
-                                                               th, ts, (float)t_ref, nullptr);
+                                                               th, ts, (float)t_ref, tinit);
         else if (op.storage == LBM_STORE_F16)
             lbm::init_kernel<2><<<grid_1d(cells), 256, 0, st>>>(base + p.off_f[0], tsnap, cells, L, d_ref,
-                                                               th, ts, (float)t_ref, nullptr);
+                                                               th, ts, (float)t_ref, tinit);
         else
             lbm::init_kernel<0><<<grid_1d(cells), 256, 0, st>>>(base + p.off_f[0], tsnap, cells, L, d_ref,
-                                                               th, ts, (float)t_ref, nullptr);
+                                                               th, ts, (float)t_ref, tinit);
         BCUDA(b, cudaGetLastError());
         BCUDA(b, cudaMemsetAsync(base + p.off_cnt, 0, sizeof(int) * L.NZ, st));
         Ctl h{};
@@ -504,25 +611,76 @@ lbm_status lbm_batch_solve(lbm_batch* b, lbm_lateral lateral, const lbm_solve_op
         k.inv_area = 1.0 / ((double)L.NX * (double)L.NY);
         k.quantum = quantum;
         k.inv_quantum = 1.0 / quantum;
+        k.hist = reinterpret_cast<double*>(base + p.off_hist);
+        k.hist_t = reinterpret_cast<unsigned long long*>(base + p.off_hist_t);
+        k.hist_cap = kBatchHistCap;
     }
     cudaFree(d_stage);
+    cudaFree(d_tstage);
     b->cur = 0;
 
-    // block counts per block size; the descriptor table and the full prefix
-    auto upload = [&](int threads) -> lbm_status {
-        b->threads = threads;
-        std::vector<int> prefix(n_solves + 1), order(n_solves);
-        int tot = 0;
+    // A launch configuration: single steps with blocks of `threads` threads,
+    // and (f2_threads > 0) plain steps as two-step launches with blocks of
+    // f2_threads threads and z chunks of about `zc` planes.
+    struct Cfg {
+        int threads, f2_threads, zc;
+    };
+    int optin = 0;
+    BCUDA(b, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+    int n_sm = 152;
+    BCUDA(b, cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, b->device));
+    // per solve two-step tiles for a block size; false if some solve cannot
+    auto f2_ok = [&](int t, size_t* smem) {
+        *smem = 0;
+        for (int s = 0; s < n_solves; ++s) {
+            int fy, bxy;
+            const Layout& L = b->layouts[s];
+            if (L.pitch != L.NX || !f2_tile(L.NX, L.NY, t, &fy, &bxy)) return false;
+            *smem = std::max(*smem, lbm::fused2_smem_bytes(L.NX, fy, b->max_phases));
+        }
+        return *smem + 64 <= (size_t)optin;
+    };
+
+    auto upload = [&](const Cfg& cf) -> lbm_status {
+        b->threads = cf.threads;
+        b->fused = cf.f2_threads > 0;
+        b->f2_threads = cf.f2_threads;
+        std::vector<int> prefix(n_solves + 1), prefix2(n_solves + 1), order(n_solves);
+        int tot = 0, tot2 = 0;
+        size_t smem2 = 0;
         for (int s = 0; s < n_solves; ++s) {
             StepArgs& a = b->descs[s].a;
-            a.blocks_per_plane = (a.quads_per_plane + threads - 1) / threads;
+            a.blocks_per_plane = (a.quads_per_plane + cf.threads - 1) / cf.threads;
             b->descs[s].blocks = a.blocks_per_plane * a.nz;
+            b->descs[s].blocks2 = 0;
+            a.f2_fy = a.f2_bxy = a.f2_zchunk = 0;
+            if (b->fused) {
+                int fy = 0, bxy = 0;
+                f2_tile(a.nx, a.ny, cf.f2_threads, &fy, &bxy);
+                const int zc = std::min(cf.zc, a.nz);
+                const int zb = (a.nz + ((a.nz + zc - 1) / zc) - 1) / ((a.nz + zc - 1) / zc);  // balanced
+                a.f2_fy = fy;
+                a.f2_bxy = bxy;
+                a.f2_zchunk = zb;
+                b->descs[s].blocks2 = bxy * ((a.nz + zb - 1) / zb);
+                smem2 = std::max(smem2, lbm::fused2_smem_bytes(a.nx, fy, b->max_phases));
+            }
             prefix[s] = tot;
+            prefix2[s] = tot2;
             order[s] = s;
             tot += b->descs[s].blocks;
+            tot2 += b->descs[s].blocks2;
         }
         prefix[n_solves] = tot;
+        prefix2[n_solves] = tot2;
         b->max_blocks = tot;
+        b->max_blocks2 = tot2;
+        b->f2_smem = smem2;
+        if (b->fused) {
+            const int dyn = (int)smem2;
+            BCUDA(b, cudaFuncSetAttribute(batch_fused2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+            BCUDA(b, cudaFuncSetAttribute(batch_fused2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+        }
         BatchCtl bc{};
         bc.n_active = n_solves;
         bc.total_blocks = tot;
@@ -549,6 +707,8 @@ lbm_status lbm_batch_solve(lbm_batch* b, lbm_lateral lateral, const lbm_solve_op
                                  cudaMemcpyHostToDevice, st));
         BCUDA(b, cudaMemcpyAsync(b->d_prefix, prefix.data(), sizeof(int) * (n_solves + 1),
                                  cudaMemcpyHostToDevice, st));
+        BCUDA(b, cudaMemcpyAsync(b->d_prefix2, prefix2.data(), sizeof(int) * (n_solves + 1),
+                                 cudaMemcpyHostToDevice, st));
         BCUDA(b, cudaMemcpyAsync(b->d_order, order.data(), sizeof(int) * n_solves,
                                  cudaMemcpyHostToDevice, st));
         BCUDA(b, cudaMemcpyAsync(b->d_bctl, &bc, sizeof bc, cudaMemcpyHostToDevice, st));
@@ -556,24 +716,46 @@ lbm_status lbm_batch_solve(lbm_batch* b, lbm_lateral lateral, const lbm_solve_op
         return LBM_OK;
     };
 
-    // autotune the block size on the batch: time a few plain steps (state
-    // buffer 1 is scratch until the first real step writes it)
-    int best = 256;
+    // The autotuner times each candidate on the batch itself: six plain
+    // steps (three two-step launches, or six single steps; state buffer 1 is
+    // scratch until the first real step writes it).  Candidates: single steps
+    // with 128, 256 or 512 threads, and (FP32, fuse on) two-step launches
+    // with 256 .. 640 threads per block and z chunks of 8, 16 or 32 planes.
+    // opts.fuse = 2 keeps only the two-step candidates when there are any.
+    std::vector<Cfg> cands = {{128, 0, 0}, {256, 0, 0}, {512, 0, 0}};
+    if (op.fuse && op.storage == LBM_STORE_F32) {
+        std::vector<Cfg> two;
+        for (int t2 : {256, 320, 384, 512, 640}) {
+            size_t sm = 0;
+            if (!f2_ok(t2, &sm)) continue;
+            for (int zc : {8, 16, 32}) two.push_back({256, t2, zc});
+        }
+        if (op.fuse == 2 && !two.empty()) cands = two;
+        else cands.insert(cands.end(), two.begin(), two.end());
+    }
+    Cfg best = cands[0];
     float best_ms = INFINITY;
-    const int candidates[3] = {128, 256, 512};
-    for (int cand : candidates) {
-        lbm_status s2 = upload(cand);
+    for (const Cfg& cf : cands) {
+        lbm_status s2 = upload(cf);
         if (s2 != LBM_OK) return s2;
-        BCUDA(b, launch_step(b, false, 0, 0, 0u, st));   // warm-up
+        auto run6 = [&]() -> cudaError_t {
+            cudaError_t e = cudaSuccess;
+            if (b->fused)
+                for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_pair(b, 0, r & 1, st);
+            else
+                for (int r = 0; r < 6 && e == cudaSuccess; ++r) e = launch_step(b, false, 0, 0, 0u, st);
+            return e;
+        };
+        BCUDA(b, run6());                                  // warm-up
         BCUDA(b, cudaEventRecord(b->ev0, st));
-        for (int r = 0; r < 6; ++r) BCUDA(b, launch_step(b, false, 0, 0, 0u, st));
+        BCUDA(b, run6());
         BCUDA(b, cudaEventRecord(b->ev1, st));
         BCUDA(b, cudaEventSynchronize(b->ev1));
         float ms = 0.f;
         BCUDA(b, cudaEventElapsedTime(&ms, b->ev0, b->ev1));
         if (ms < best_ms) {
             best_ms = ms;
-            best = cand;
+            best = cf;
         }
     }
     lbm_status s3 = upload(best);
@@ -596,14 +778,27 @@ lbm_status lbm_batch_solve(lbm_batch* b, lbm_lateral lateral, const lbm_solve_op
         e = cudaStreamBeginCaptureToGraph(b->cap_stream, np.conditional.phGraph_out[0], nullptr,
                                           nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        int parity = 0;
-        for (int k = 0; k < K && e == cudaSuccess; ++k) {
-            e = launch_step(b, k == K - 1, parity, k == 0 ? 1 : 2, (unsigned)k, b->cap_stream);
+        // the interval: one single step into frame R_b, plain steps (as
+        // two-step launches in an even number of pairs when the autotuner
+        // chose them, so the interval ends in the buffer it started from),
+        // the check step, then the control kernel
+        const int R = K - 2;
+        const int pairs = b->fused ? 2 * (R / 4) : 0;
+        int parity = 0, k = 0;
+        e = launch_step(b, false, parity, 1, (unsigned)k++, b->cap_stream);
+        parity ^= 1;
+        for (int i = 0; i < pairs && e == cudaSuccess; ++i, k += 2) {
+            e = launch_pair(b, parity, i & 1, b->cap_stream);
             parity ^= 1;
         }
+        for (; k < K - 1 && e == cudaSuccess; ++k) {
+            e = launch_step(b, false, parity, 2, (unsigned)k, b->cap_stream);
+            parity ^= 1;
+        }
+        if (e == cudaSuccess) e = launch_step(b, true, parity, 2, (unsigned)k, b->cap_stream);
         if (e == cudaSuccess) {
             batch_control_kernel<<<1, 32, 0, b->cap_stream>>>(b->d_descs, n_solves, b->d_prefix,
-                                                              b->d_order, b->d_bctl, h, 1);
+                                                              b->d_prefix2, b->d_order, b->d_bctl, h, 1);
             e = cudaGetLastError();
         }
         cudaGraph_t captured = nullptr;
@@ -617,6 +812,8 @@ lbm_status lbm_batch_solve(lbm_batch* b, lbm_lateral lateral, const lbm_solve_op
         b->poisoned = true;
         return bfail(b, LBM_ERR_CUDA, "building the batch graph failed: %s", cudaGetErrorString(e));
     }
+    batch_stamp_kernel<<<1, 1, 0, st>>>(b->d_bctl);
+    BCUDA(b, cudaGetLastError());
     BCUDA(b, cudaEventRecord(b->ev0, st));
     e = cudaGraphLaunch(exec, st);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev1, st);
@@ -646,7 +843,9 @@ lbm_status lbm_batch_solve(lbm_batch* b, lbm_lateral lateral, const lbm_solve_op
         info->n_converged = converged;
         info->total_updates = updates;
         info->elapsed_ms = ms;
-        info->block_threads = b->threads;
+        info->block_threads = b->fused ? b->f2_threads : b->threads;
+        info->steps_per_launch = b->fused ? 2 : 1;
+        info->reserved = 0;
         info->status = converged == n_solves ? LBM_OK : LBM_ERR_NOT_CONVERGED;
     }
     return LBM_OK;
@@ -694,6 +893,46 @@ lbm_status lbm_batch_get_temperature(lbm_batch* b, int id, float* host_out) {
         b->poisoned = true;
         return bfail(b, LBM_ERR_CUDA, "%s", cudaGetErrorString(e));
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_initial(lbm_batch* b, int id, const float* t_init) {
+    if (!b) return LBM_ERR_INVALID_ARG;
+    if (b->poisoned) return bfail(b, LBM_ERR_CUDA, "batch poisoned by an earlier CUDA error");
+    if (id < 0 || id >= (int)b->cells.size()) return bfail(b, LBM_ERR_INVALID_ARG, "bad id");
+    Cell& c = b->cells[id];
+    if (!t_init) {
+        c.t_init.clear();
+    } else {
+        const size_t N = (size_t)c.n[0] * c.n[1] * c.n[2];
+        c.t_init.assign(t_init, t_init + N);
+    }
+    b->solved = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_get_history(lbm_batch* b, int id, double* host_out, int max_entries, int* n_out) {
+    if (!b || !host_out || max_entries < 0) return LBM_ERR_INVALID_ARG;
+    if (b->poisoned) return LBM_ERR_CUDA;
+    if (!b->solved) return bfail(b, LBM_ERR_STATE, "no solve yet");
+    if (id < 0 || id >= (int)b->cells.size()) return bfail(b, LBM_ERR_INVALID_ARG, "bad id");
+    BCUDA(b, cudaSetDevice(b->device));
+    const lbm::CheckArgs& k = b->descs[id].a.ck;
+    std::vector<double> ring(4 * (size_t)kBatchHistCap);
+    std::vector<unsigned long long> tr(kBatchHistCap);
+    BatchCtl bc{};
+    BCUDA(b, cudaMemcpy(ring.data(), k.hist, sizeof(double) * ring.size(), cudaMemcpyDeviceToHost));
+    BCUDA(b, cudaMemcpy(tr.data(), k.hist_t, sizeof(unsigned long long) * tr.size(), cudaMemcpyDeviceToHost));
+    BCUDA(b, cudaMemcpy(&bc, b->d_bctl, sizeof bc, cudaMemcpyDeviceToHost));
+    const long long checks = b->h_ctl[id].checks;
+    const long long kept = std::min<long long>(checks, kBatchHistCap);
+    const long long n = std::min<long long>(kept, max_entries);
+    for (long long i = 0; i < n; ++i) {
+        const long long slot = (checks - n + i) % kBatchHistCap;
+        std::memcpy(host_out + 5 * i, &ring[4 * (size_t)slot], sizeof(double) * 4);
+        host_out[5 * i + 4] = (double)(long long)(tr[slot] - bc.t0) * 1e-6;
+    }
+    if (n_out) *n_out = (int)n;
     return LBM_OK;
 }
 

@@ -26,7 +26,8 @@ struct lbm_ctx {
     int n[3] = {0, 0, 0};
     int device = 0;
     int n_sm = 152;                        // multiprocessors of the device
-    bool fuse_ok[2] = {false, false};      // fused kernel usable for rows of 128, 256 nodes
+    bool fuse_ok = false;                  // the two-step kernels got their shared memory
+    int f2_smem_max = 0;                   // dynamic shared memory they may use (bytes)
     int pair_flip = 0;                     // chunk direction of the next lbm_advance pair
     mutable int step_flip = 0;             // plane order of the next single-step launch
     char* ws = nullptr;                    // caller's device workspace (nullptr: own allocations)
@@ -85,6 +86,7 @@ struct lbm_ctx {
     bool have_k = false;
 
     // graph of one check interval inside a while node, one per buffer parity
+    lbm::F2Plan f2{};                      // two-step kernel plan of the current solve
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     std::vector<char> gsig[2];             // kernel arguments baked into each graph
     int g_interval = 0;
@@ -273,43 +275,54 @@ cudaError_t launch_step(const lbm_ctx* c, int src, bool check, Frame fr, cudaStr
 }
 
 // Two plain FP32 steps in one launch (temporal blocking), when the layout
-// allows it: rows of 128 or 256 nodes without padding, whole tiles of rows.
-bool fused_rows(const lbm_ctx* c, int nx, int ny) {
-    return (nx == 128 || nx == 256) && c->fuse_ok[nx / 128 - 1] && ny % lbm::f2_fy(nx / 128) == 0;
+// allows it: rows of a multiple of 4 nodes (no padding).  The plan picks the
+// tile height and the z chunk for the cell.
+template <bool PER, int NXC>
+const void* f2_kernel_ptr() {
+    return reinterpret_cast<const void*>(lbm::fused2_kernel<PER, NXC>);
+}
+
+const void* f2_kernel(bool periodic, int nxc) {
+    if (nxc == 128) return periodic ? f2_kernel_ptr<true, 128>() : f2_kernel_ptr<false, 128>();
+    if (nxc == 256) return periodic ? f2_kernel_ptr<true, 256>() : f2_kernel_ptr<false, 256>();
+    return periodic ? f2_kernel_ptr<true, 0>() : f2_kernel_ptr<false, 0>();
+}
+
+lbm::F2Plan f2_plan_for(const lbm_ctx* c, int nx, int ny, int nz, int n_phases, bool periodic) {
+    if (!c->fuse_ok) return lbm::F2Plan{};
+    return lbm::f2_plan(nx, ny, nz, n_phases, c->n_sm, c->f2_smem_max,
+                        [&](int nxc, int threads, size_t smem) {
+                            int nb = 0;
+                            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f2_kernel(periodic, nxc), threads,
+                                                                              smem) != cudaSuccess) {
+                                cudaGetLastError();
+                                return 0;
+                            }
+                            return nb;
+                        });
 }
 
 bool fusable(const lbm_ctx* c) {
-    return c->opts.fuse && c->fmt == LBM_STORE_F32 && c->L.pitch == c->L.NX && fused_rows(c, c->L.NX, c->L.NY);
+    return c->opts.fuse && c->fmt == LBM_STORE_F32 && c->f2.ok;
 }
 
 // flip: 1 reverses every chunk's marching direction; alternate launches
 // flip, so that each chunk starts on the planes it wrote last (still in L2).
 cudaError_t launch_pair(const lbm_ctx* c, int src, Frame fr, int flip, cudaStream_t st) {
     const lbm::StepArgs a = step_args(c, src, fr);
-    const int kw = c->L.NX / 128;
-    const int bxy = c->L.NY / lbm::f2_fy(kw);
-    // z chunks: balance the fill of the last wave against the two extra
-    // planes of the first step each chunk computes; chunks of >= 8 planes
-    const long long slots = (long long)lbm::f2_minb(kw) * c->n_sm;
-    int zchunk = c->L.NZ;
-    double best = -1.0;
-    for (int nzc = 1; nzc <= c->L.NZ / 8 || nzc == 1; ++nzc) {
-        const int zc = (c->L.NZ + nzc - 1) / nzc;
-        const long long blocks = (long long)bxy * ((c->L.NZ + zc - 1) / zc);
-        const double fill = (double)blocks / (double)(((blocks + slots - 1) / slots) * slots);
-        const double score = fill * zc / (zc + 2.0);
-        if (score > best + 1e-9) { best = score; zchunk = zc; }
-    }
-    const dim3 grid(bxy, (c->L.NZ + zchunk - 1) / zchunk);
-    const int threads = lbm::fused2_threads(kw);
-    const size_t smem = lbm::fused2_smem_bytes(kw, c->n_phases);
+    const lbm::F2Plan& p = c->f2;
+    const dim3 grid(p.bxy, p.nzc);
+    const size_t smem = lbm::fused2_smem_bytes(c->L.NX, p.fy, c->n_phases);
     const bool per = c->lateral == LBM_LATERAL_PERIODIC;
-    if (kw == 1) {
-        if (per) lbm::fused2_kernel<true, 1><<<grid, threads, smem, st>>>(a, zchunk, flip);
-        else lbm::fused2_kernel<false, 1><<<grid, threads, smem, st>>>(a, zchunk, flip);
+    if (p.nxc == 128) {
+        if (per) lbm::fused2_kernel<true, 128><<<grid, p.threads, smem, st>>>(a, p.fy, p.zchunk, flip);
+        else lbm::fused2_kernel<false, 128><<<grid, p.threads, smem, st>>>(a, p.fy, p.zchunk, flip);
+    } else if (p.nxc == 256) {
+        if (per) lbm::fused2_kernel<true, 256><<<grid, p.threads, smem, st>>>(a, p.fy, p.zchunk, flip);
+        else lbm::fused2_kernel<false, 256><<<grid, p.threads, smem, st>>>(a, p.fy, p.zchunk, flip);
     } else {
-        if (per) lbm::fused2_kernel<true, 2><<<grid, threads, smem, st>>>(a, zchunk, flip);
-        else lbm::fused2_kernel<false, 2><<<grid, threads, smem, st>>>(a, zchunk, flip);
+        if (per) lbm::fused2_kernel<true, 0><<<grid, p.threads, smem, st>>>(a, p.fy, p.zchunk, flip);
+        else lbm::fused2_kernel<false, 0><<<grid, p.threads, smem, st>>>(a, p.fy, p.zchunk, flip);
     }
     return cudaGetLastError();
 }
@@ -426,7 +439,8 @@ std::vector<char> graph_signature(const lbm_ctx* c, int parity) {
     const lbm::StepArgs a = step_args(c, parity, kAB, interval_closing(c));
     std::vector<char> sig(sizeof a + 3 * sizeof(int));
     std::memcpy(sig.data(), &a, sizeof a);
-    const int extra[3] = {c->lateral, c->opts.check_every, c->fmt * 2 + (fusable(c) ? 1 : 0)};
+    const int extra[3] = {c->lateral, c->opts.check_every,
+                          (c->fmt * 2 + (fusable(c) ? 1 : 0)) | (c->f2.fy << 4) | (c->f2.zchunk << 12)};
     std::memcpy(sig.data() + sizeof a, extra, sizeof extra);
     return sig;
 }
@@ -571,19 +585,27 @@ lbm_status create_ctx(int nx, int ny, int nz, int cuda_device, char* ws, size_t 
               cudaMallocHost((void**)&c->h_ctl, sizeof(Ctl)) == cudaSuccess &&
               cudaEventCreate(&c->ev0) == cudaSuccess && cudaEventCreate(&c->ev1) == cudaSuccess &&
               cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, cuda_device) == cudaSuccess;
-    // the fused two-step kernel needs more than the default 48 KB of shared
-    // memory; a row width whose kernel cannot get it runs single steps
+    // the fused two-step kernels need more than the default 48 KB of shared
+    // memory; without it every solve runs single steps
     if (ok) {
-        c->fuse_ok[0] =
-            cudaFuncSetAttribute(lbm::fused2_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)lbm::fused2_smem_bytes(1, 255)) == cudaSuccess &&
-            cudaFuncSetAttribute(lbm::fused2_kernel<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)lbm::fused2_smem_bytes(1, 255)) == cudaSuccess;
-        c->fuse_ok[1] =
-            cudaFuncSetAttribute(lbm::fused2_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)lbm::fused2_smem_bytes(2, 255)) == cudaSuccess &&
-            cudaFuncSetAttribute(lbm::fused2_kernel<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)lbm::fused2_smem_bytes(2, 255)) == cudaSuccess;
+        int optin = 0;
+        c->fuse_ok = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, cuda_device) ==
+                     cudaSuccess;
+        int most = optin;
+        for (int per = 0; per < 2 && c->fuse_ok; ++per)
+            for (int nxc : {128, 256, 0}) {
+                const void* k = f2_kernel(per == 1, nxc);
+                cudaFuncAttributes fa;
+                if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) {
+                    c->fuse_ok = false;
+                    break;
+                }
+                const int dyn = optin - (int)fa.sharedSizeBytes;
+                most = std::min(most, dyn);
+                c->fuse_ok = c->fuse_ok && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                                dyn) == cudaSuccess;
+            }
+        c->f2_smem_max = c->fuse_ok ? most : 0;
         cudaGetLastError();
     }
     if (!ok) {
@@ -714,11 +736,17 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
         L.n[i] = c->n[i];
         L.perm[i] = perms[axis][i];
     }
-    if (op.fuse && op.storage == LBM_STORE_F32 && !fused_rows(c, c->n[L.perm[0]], c->n[L.perm[1]]) &&
-        fused_rows(c, c->n[L.perm[1]], c->n[L.perm[0]])) {
-        const int t = L.perm[0];
-        L.perm[0] = L.perm[1];
-        L.perm[1] = t;
+    lbm::F2Plan f2{};
+    if (op.fuse && op.storage == LBM_STORE_F32) {
+        const bool per = lateral == LBM_LATERAL_PERIODIC;
+        f2 = f2_plan_for(c, c->n[L.perm[0]], c->n[L.perm[1]], c->n[L.perm[2]], c->n_phases, per);
+        const lbm::F2Plan sw = f2_plan_for(c, c->n[L.perm[1]], c->n[L.perm[0]], c->n[L.perm[2]], c->n_phases, per);
+        if (sw.ok && (!f2.ok || sw.score > f2.score * 1.001)) {
+            const int t = L.perm[0];
+            L.perm[0] = L.perm[1];
+            L.perm[1] = t;
+            f2 = sw;
+        }
     }
     L.NX = c->n[L.perm[0]];
     L.NY = c->n[L.perm[1]];
@@ -767,6 +795,7 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
     c->Q_host.assign(L.NZ, 0.0);
 
     c->opts = op;
+    c->f2 = f2;
     c->fmt = op.storage;
     c->axis = axis;
     c->lateral = lateral;
@@ -1131,6 +1160,23 @@ lbm_status lbm_set_state(lbm_ctx* c, const void* host_in, size_t bytes) {
     CUDA_TRY(c, cudaMemsetAsync(c->d_plane_cnt, 0, sizeof(int) * c->L.NZ, st));
     lbm_status s2 = read_ctl(c, st);
     if (s2 != LBM_OK) return s2;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_launch_plan(const lbm_ctx* c, lbm_launch_plan* out) {
+    if (!c || !out) return LBM_ERR_INVALID_ARG;
+    if (!c->started) return LBM_ERR_STATE;
+    std::memset(out, 0, sizeof *out);
+    out->nx = c->L.NX;
+    out->ny = c->L.NY;
+    out->nz = c->L.NZ;
+    out->pitch = c->L.pitch;
+    out->steps_per_launch = fusable(c) ? 2 : 1;
+    if (fusable(c)) {
+        out->tile_rows = c->f2.fy;
+        out->zchunk = c->f2.zchunk;
+        out->block_threads = c->f2.threads;
+    }
     return LBM_OK;
 }
 

@@ -38,6 +38,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 namespace lbm {
 
 constexpr int kThreads = 256;        // threads per step block
@@ -77,6 +79,7 @@ struct CheckArgs {
     cudaGraphConditionalHandle handle;
     int use_handle;
     double* hist;                    // history ring [hist_cap][4] or null
+    unsigned long long* hist_t;      // device time (ns) of each history row, or null
     int hist_cap;
 };
 
@@ -95,6 +98,7 @@ struct StepArgs {
     int zrev;                        // 1: blocks walk the planes from the top (alternate steps)
     float eps_hot, eps_cold;         // eps * T_wall
     unsigned rseed;                  // launch salt of the stochastic rounding
+    int f2_fy, f2_bxy, f2_zchunk;    // two-step tiles of this solve in a batch launch
     double t_ref;                    // offset of the residual snapshot
     CheckArgs ck;
 };
@@ -116,6 +120,12 @@ __device__ __forceinline__ void set_comp(float4& v, int k, float s) {
     else if (k == 1) v.y = s;
     else if (k == 2) v.z = s;
     else v.w = s;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 // Closing a check (Eq. 15-16 plane sums, Eq. 22, the stop rule).  Every
@@ -192,6 +202,7 @@ __device__ void close_check(const StepArgs& a) {
             else status = 5;                              // LBM_ERR_NOT_CONVERGED (so far)
         }
         c->status = status;
+        if (ck.hist_t) ck.hist_t[(c->checks - 1) % ck.hist_cap] = globaltimer_ns();
         if (ck.hist) {
             double* hrow = ck.hist + 4 * ((c->checks - 1) % ck.hist_cap);
             hrow[0] = (double)c->iter;
@@ -591,10 +602,13 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
 }
 
 // Two fused steps (temporal blocking) in FP32.  A block owns FY rows of the
-// full x extent (nx = 128 KW: KW warps per row, each thread 4 consecutive
-// nodes) and marches through a chunk of planes.  Block row r = 0 .. FY + 1
-// is grid row y0 - 1 + r: rows 1 .. FY are the tile, rows 0 and FY + 1 the
-// halo whose populations 3 and 4 the tile's second step pulls.
+// full x extent (each thread 4 consecutive nodes, nq = nx / 4 threads per
+// row) and marches through a chunk of planes.  Block row r = 0 .. FY + 1 is
+// grid row y0 - 1 + r: rows 1 .. FY are the tile, rows 0 and FY + 1 the halo
+// whose populations 3 and 4 the tile's second step pulls.  The last tile of a
+// cell whose ny is not a multiple of FY has fyb < FY rows; its halo is block
+// row fyb + 1 and the rows after it idle.  Threads past (FY + 2) nq idle too
+// (a batch launches every block with the same size).
 // Iteration i computes step n at plane i for all rows (pulled from global
 // memory, written to a ring of three shared planes) and step n + 1 at plane
 // i - 2 for the tile rows (pulled from the ring, written to global memory).
@@ -602,20 +616,22 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
 // in flight while it runs.  Every node's arithmetic is the single step's
 // (collide_node), so two fused steps equal two single steps bit for bit.
 // Step n runs from frame rsrc to rdst, step n + 1 within rdst.
-// Tile rows and resident blocks per SM by row width (measured on the
-// 128 x 128 x 256 cell: 8 rows at 2 blocks per SM beat 4 at 3 and 16 at 1).
-__host__ __device__ constexpr int f2_fy(int kw) { return kw == 1 ? 8 : 8; }
-__host__ __device__ constexpr int f2_minb(int kw) { return kw == 1 ? 2 : 1; }
-__host__ __device__ constexpr int f2_rows(int kw) { return f2_fy(kw) + 2; }
 constexpr int F2_PF = 1;                           // L2 prefetch distance in planes
+constexpr int F2_MAX_THREADS = 640;
 
-__host__ __device__ constexpr int fused2_threads(int kw) { return 32 * kw * f2_rows(kw); }
+// Kernel variants: rows of 128 nodes (tuned: 8-row tiles, 320 threads, two
+// blocks per SM), 256 nodes (8-row tiles, 640 threads) and any multiple of 4
+// (runtime row width); the launch bounds keep every variant at or below 96
+// registers so that two 320-thread blocks fit an SM.
+__host__ __device__ constexpr int f2_bound_threads(int nxc) { return nxc == 128 ? 320 : F2_MAX_THREADS; }
+__host__ __device__ constexpr int f2_bound_blocks(int nxc) { return nxc == 128 ? 2 : 1; }
+
 // A ring plane keeps, per population, only the rows the second step reads:
 // the FY tile rows for 0, 1, 2, 5, 6; block rows 0 .. FY for 3 and 1 .. FY + 1
 // for 4 (the halo row and, at an adiabatic face, the own row's bounce-back).
-__host__ __device__ constexpr int f2_slot_rows(int kw) { return 7 * f2_fy(kw) + 2; }
-__host__ __device__ constexpr size_t fused2_smem_bytes(int kw, int n_phases) {
-    return sizeof(float) * 3 * f2_slot_rows(kw) * 128 * kw + (sizeof(float4) + sizeof(float2)) * n_phases;
+__host__ __device__ constexpr int f2_slot_rows(int fy) { return 7 * fy + 2; }
+__host__ __device__ constexpr size_t fused2_smem_bytes(int nx, int fy, int n_phases) {
+    return sizeof(float) * 3 * (size_t)f2_slot_rows(fy) * nx + (sizeof(float4) + sizeof(float2)) * n_phases;
 }
 
 __device__ __forceinline__ float4 f4neg(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
@@ -647,40 +663,57 @@ __device__ __forceinline__ Quad7 collide_quad(const float4& g0, const float4& g1
     return q;
 }
 
-template <bool PERIODIC, int KW>
-__global__ void __launch_bounds__(fused2_threads(KW), f2_minb(KW)) fused2_kernel(const StepArgs a, int zchunk, int flip) {
-    constexpr int FY = f2_fy(KW), F2_ROWS = f2_rows(KW);
-    constexpr int NXB = 128 * KW;                  // nodes per row (= nx)
-    constexpr int RS = f2_slot_rows(KW) * NXB;     // floats per ring plane
-    // population offsets within a ring plane, for block row r at row r - 1:
-    // population 3 keeps block rows 0 .. FY, population 4 rows 1 .. FY + 1
-    constexpr int Q1 = FY * NXB, Q2 = 2 * FY * NXB, Q5 = 3 * FY * NXB, Q6 = 4 * FY * NXB;
-    constexpr int Q3 = (5 * FY + 1) * NXB, Q4 = (6 * FY + 1) * NXB;
+// Loads the B tables into shared memory after the ring; returns the ring.
+__device__ __forceinline__ float* fused2_tables(const StepArgs& a, int ring_floats, float4** s_sa,
+                                                float2** s_sc) {
     extern __shared__ float4 smem4[];
-    float* fn = reinterpret_cast<float*>(smem4);   // [3][f2_slot_rows][NXB]
+    float* fn = reinterpret_cast<float*>(smem4);   // [3][f2_slot_rows][nx]
     // B per phase split into (xx, yy, zz, yz) and (xz, xy) tables: up to
     // 8 (16) distinct phases in a warp read one 128-byte wavefront
-    float4* s_sa = reinterpret_cast<float4*>(fn + 3 * RS);
-    float2* s_sc = reinterpret_cast<float2*>(s_sa + a.n_phases);
-    const int tid = threadIdx.x;
-    for (int i = tid; i < a.n_phases; i += 32 * KW * F2_ROWS) {
-        s_sa[i] = a.sb[2 * i];
-        s_sc[i] = make_float2(a.sb[2 * i + 1].x, a.sb[2 * i + 1].y);
+    *s_sa = reinterpret_cast<float4*>(fn + ring_floats);
+    *s_sc = reinterpret_cast<float2*>(*s_sa + a.n_phases);
+    for (int i = threadIdx.x; i < a.n_phases; i += blockDim.x) {
+        (*s_sa)[i] = a.sb[2 * i];
+        (*s_sc)[i] = make_float2(a.sb[2 * i + 1].x, a.sb[2 * i + 1].y);
     }
+    return fn;
+}
 
+// One block of the two-step kernel: tile `by` of FY rows, chunk `bz` of
+// zchunk planes.  NXC: compile-time row width (128, 256) or 0 (a.pitch).
+// The caller has loaded the B tables (fused2_tables) but not yet synchronised.
+template <bool PERIODIC, int NXC>
+__device__ __forceinline__ void fused2_body(const StepArgs& a, float* fn, const float4* s_sa,
+                                            const float2* s_sc, const int FY, const int by, const int bz,
+                                            const int zchunk, const int flip) {
+    const int NXB = NXC ? NXC : a.pitch;           // nodes per row (= nx = pitch)
+    const int nq = NXB >> 2;                       // threads per row
+    const int RS = f2_slot_rows(FY) * NXB;         // floats per ring plane
+    // population offsets within a ring plane, for block row r at row r - 1:
+    // population 3 keeps block rows 0 .. FY, population 4 rows 1 .. FY + 1
+    const int Q1 = FY * NXB, Q2 = 2 * FY * NXB, Q5 = 3 * FY * NXB, Q6 = 4 * FY * NXB;
+    const int Q3 = (5 * FY + 1) * NXB, Q4 = (6 * FY + 1) * NXB;
+    const int tid = threadIdx.x;
     const int lane = tid & 31;
-    const int r = tid / (32 * KW);                 // block row (warp-uniform)
-    const int x = 4 * (tid - r * 32 * KW);         // first of this thread's 4 nodes
+    const int r = tid / nq;                        // block row
+    const int x = 4 * (tid - r * nq);              // first of this thread's 4 nodes
     const int ny = a.ny, nz = a.nz, pitch = a.pitch;
-    const int y0 = blockIdx.x * FY;
-    int y = y0 - 1 + r;
-    bool row_in = true;
+    const int y0 = by * FY;
+    const int fyb = min(FY, ny - y0);              // tile rows of this block
+    const bool live = r <= fyb + 1;
+    int y = live ? y0 - 1 + r : 0;
+    bool row_in = live;
     if (PERIODIC) y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-    else row_in = y >= 0 && y < ny;
-    const bool tile_row = r >= 1 && r <= FY;
+    else row_in = live && y >= 0 && y < ny;
+    const bool tile_row = r >= 1 && r <= fyb;
     const bool ylo = y == 0, yhi = y == ny - 1;
     const int xm = x == 0 ? NXB - 1 : x - 1;       // x - 1 of node x, wrapped
     const int xp = x + 4 == NXB ? 0 : x + 4;       // x + 1 of node x + 3, wrapped
+    // x-neighbours come from the adjacent lane, except where that lane holds
+    // another row or another warp holds the neighbour (a row of exactly one
+    // warp wraps within the warp)
+    const bool own_left = nq == 32 || !(lane == 0 || x == 0);
+    const bool own_right = nq == 32 || !(lane == 31 || x + 4 == NXB);
     const long long P = a.pstride;
     const long long PL = (long long)ny * pitch;
     const long long yrow = (long long)y * pitch;
@@ -692,13 +725,13 @@ __global__ void __launch_bounds__(fused2_threads(KW), f2_minb(KW)) fused2_kernel
                                   : (yhi ? 3 * P + yrow : 4 * P + yrow + pitch);
     const float* __restrict__ src = reinterpret_cast<const float*>(a.src);
     float* __restrict__ dst = reinterpret_cast<float*>(a.dst);
-    const int z0 = blockIdx.y * zchunk;
+    const int z0 = bz * zchunk;
     const int z1 = min(z0 + zchunk, nz);
     // chunks march alternately up and down, so that two neighbouring chunks
     // read the planes at their common boundary at about the same time; flip
     // reverses all of them (consecutive launches alternate, so a chunk starts
     // on the planes it wrote last)
-    const bool up = ((blockIdx.y & 1) == 0) == (flip == 0);
+    const bool up = ((bz & 1) == 0) == (flip == 0);
     const int dz = up ? 1 : -1;
     // frame constants of the two planes an iteration updates, computed one
     // iteration ahead by thread 0 into a double buffer: [t & 1][step n, n + 1]
@@ -712,25 +745,26 @@ __global__ void __launch_bounds__(fused2_threads(KW), f2_minb(KW)) fused2_kernel
     if (tid == 0) plane_pair(0, s_kc[0]);
     __syncthreads();                               // the B tables and s_kc[0] are ready
 
-    // L2 prefetch, F2_PF planes ahead: lanes 0..7 of each warp each fetch one
-    // population's row segment (what the first step at that plane pulls) or
-    // the phase bytes, by one bulk prefetch
+    // L2 prefetch, F2_PF planes ahead: threads 0..7 of each row each fetch one
+    // population's row (what the first step at that plane pulls) or the
+    // phase bytes, by one bulk prefetch
+    const int q = x >> 2;
+    const int pf_k = q;                            // what this thread prefetches (< 8)
     const char* pf_base = nullptr;
     long long pf_plane = 4 * PL;                   // bytes per plane
-    unsigned pf_bytes = 512;
+    unsigned pf_bytes = 4u * NXB;
     {
-        const long long xw = x - 4 * lane;         // this warp's first node
-        const long long off = lane == 0 ? yrow : lane == 1 ? P + yrow : lane == 2 ? 2 * P + yrow
-                            : lane == 3 ? o3 : lane == 4 ? o4 : lane == 5 ? 5 * P - PL + yrow
+        const long long off = pf_k == 0 ? yrow : pf_k == 1 ? P + yrow : pf_k == 2 ? 2 * P + yrow
+                            : pf_k == 3 ? o3 : pf_k == 4 ? o4 : pf_k == 5 ? 5 * P - PL + yrow
                             : 6 * P + PL + yrow;
-        pf_base = reinterpret_cast<const char*>(src + off + xw);
-        if (lane == 7) {
-            pf_base = reinterpret_cast<const char*>(a.phase + yrow + xw);
+        pf_base = reinterpret_cast<const char*>(src + off);
+        if (pf_k == 7) {
+            pf_base = reinterpret_cast<const char*>(a.phase + yrow);
             pf_plane = PL;
-            pf_bytes = 128;
+            pf_bytes = NXB;
         }
     }
-    const bool pf_lane = row_in && lane < 8;
+    const bool pf_lane = row_in && pf_k < 8 && (pf_k != 7 || (NXB & 15) == 0);
     unsigned phA = 0u, phB = 0u;                   // phase words of planes i - 2dz and i - dz
     // ring slot of plane p: p mod 3.  si tracks plane i; planes j, j - 1 and
     // j + 1 then sit in slots si + 1, si, si + 2 (up) or si + 2, si + 1, si
@@ -748,12 +782,12 @@ __global__ void __launch_bounds__(fused2_threads(KW), f2_minb(KW)) fused2_kernel
         {
             const int ip = i + F2_PF * dz;
             // the wall planes pull their own populations: nothing to prefetch there
-            if (pf_lane && ip >= z0 - 1 && ip <= z1 && ip >= 0 && ip < nz && (lane != 5 || ip > 0) &&
-                (lane != 6 || ip < nz - 1))
+            if (pf_lane && ip >= z0 - 1 && ip <= z1 && ip >= 0 && ip < nz && (pf_k != 5 || ip > 0) &&
+                (pf_k != 6 || ip < nz - 1))
                 asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(pf_base + ip * pf_plane),
                              "r"(pf_bytes) : "memory");
         }
-        // ---- loads of step n at plane i (warp-uniform condition) ----
+        // ---- loads of step n at plane i ----
         const bool first = i >= z0 - 1 && i <= z1 && i >= 0 && i < nz && row_in;
         float4 q0, q1, q2, q3, q4, q5, q6;
         unsigned phC = 0u;
@@ -768,64 +802,75 @@ __global__ void __launch_bounds__(fused2_threads(KW), f2_minb(KW)) fused2_kernel
             q5 = __ldg(reinterpret_cast<const float4*>(s + (i > 0 ? 5 * P - PL : 6 * P) + yrow + x));
             q6 = __ldg(reinterpret_cast<const float4*>(s + (i < nz - 1 ? 6 * P + PL : 5 * P) + yrow + x));
             phC = __ldg(reinterpret_cast<const unsigned*>(a.phase + (long long)i * PL + yrow + x));
+        } else {
+            q0 = q1 = q2 = q3 = q4 = q5 = q6 = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         // ---- step n + 1 at plane j, tile rows ----
         const int own = (r - 1) * NXB + x;          // this thread's nodes in a ring plane
-        if (tile_row && j >= z0 && j < z1) {
+        {
+            const bool second = tile_row && j >= z0 && j < z1;
             const float* fs = fn + sj * RS + own;
             const float* fb = fn + sjm * RS + own;
             const float* fa = fn + sjp * RS + own;
-            const float4 g0 = *reinterpret_cast<const float4*>(fs);
-            const float4 c1 = *reinterpret_cast<const float4*>(fs + Q1);
-            const float4 c2 = *reinterpret_cast<const float4*>(fs + Q2);
-            const float4 g3 = (PERIODIC || !ylo) ? *reinterpret_cast<const float4*>(fs + Q3 - NXB)
-                                                 : *reinterpret_cast<const float4*>(fs + Q4);
-            const float4 g4 = (PERIODIC || !yhi) ? *reinterpret_cast<const float4*>(fs + Q4 + NXB)
-                                                 : *reinterpret_cast<const float4*>(fs + Q3);
-            const float4 g5 = j > 0 ? *reinterpret_cast<const float4*>(fb + Q5)
-                                    : f4neg(*reinterpret_cast<const float4*>(fs + Q6));
-            const float4 g6 = j < nz - 1 ? *reinterpret_cast<const float4*>(fa + Q6)
-                                         : f4neg(*reinterpret_cast<const float4*>(fs + Q5));
-            // x-neighbours: from the next lane, across warps from the ring row
+            float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = g0, c2 = g0, g3 = g0, g4 = g0, g5 = g0, g6 = g0;
+            if (second) {
+                g0 = *reinterpret_cast<const float4*>(fs);
+                c1 = *reinterpret_cast<const float4*>(fs + Q1);
+                c2 = *reinterpret_cast<const float4*>(fs + Q2);
+                g3 = (PERIODIC || !ylo) ? *reinterpret_cast<const float4*>(fs + Q3 - NXB)
+                                        : *reinterpret_cast<const float4*>(fs + Q4);
+                g4 = (PERIODIC || !yhi) ? *reinterpret_cast<const float4*>(fs + Q4 + NXB)
+                                        : *reinterpret_cast<const float4*>(fs + Q3);
+                g5 = j > 0 ? *reinterpret_cast<const float4*>(fb + Q5)
+                           : f4neg(*reinterpret_cast<const float4*>(fs + Q6));
+                g6 = j < nz - 1 ? *reinterpret_cast<const float4*>(fa + Q6)
+                                : f4neg(*reinterpret_cast<const float4*>(fs + Q5));
+            }
+            // x-neighbours: from the next lane (every lane takes part), else
+            // from the ring row
             float l1 = __shfl_sync(kFull, c1.w, (lane + 31) & 31);
             float r2 = __shfl_sync(kFull, c2.x, (lane + 1) & 31);
-            if (KW > 1 && lane == 0) l1 = fs[Q1 - x + xm];
-            if (KW > 1 && lane == 31) r2 = fs[Q2 - x + xp];
-            if (!PERIODIC && x == 0) l1 = c2.x;                 // Eq. 24 at x = 0
-            if (!PERIODIC && x + 4 == NXB) r2 = c1.w;           // and at x = nx - 1
-            const float4 g1 = make_float4(l1, c1.x, c1.y, c1.z);
-            const float4 g2 = make_float4(c2.y, c2.z, c2.w, r2);
-            const Quad7 o = collide_quad(g0, g1, g2, g3, g4, g5, g6, phA, s_sa, s_sc, kn1.kT, kn1.kJ);
-            float* d = dst + (long long)j * PL + yrow + x;
+            if (second) {
+                if (!own_left) l1 = fs[Q1 - x + xm];
+                if (!own_right) r2 = fs[Q2 - x + xp];
+                if (!PERIODIC && x == 0) l1 = c2.x;                 // Eq. 24 at x = 0
+                if (!PERIODIC && x + 4 == NXB) r2 = c1.w;           // and at x = nx - 1
+                const float4 g1 = make_float4(l1, c1.x, c1.y, c1.z);
+                const float4 g2 = make_float4(c2.y, c2.z, c2.w, r2);
+                const Quad7 o = collide_quad(g0, g1, g2, g3, g4, g5, g6, phA, s_sa, s_sc, kn1.kT, kn1.kJ);
+                float* d = dst + (long long)j * PL + yrow + x;
 #pragma unroll
-            for (int p = 0; p < 7; ++p) *reinterpret_cast<float4*>(d + p * P) = o.o[p];
+                for (int p = 0; p < 7; ++p) *reinterpret_cast<float4*>(d + p * P) = o.o[p];
+            }
         }
         // ---- step n at plane i into the ring ----
-        if (first) {
+        {
             if (i == 0) q5 = f4neg(q5);
             if (i == nz - 1) q6 = f4neg(q6);
             float l1 = __shfl_sync(kFull, q1.w, (lane + 31) & 31);
             float r2 = __shfl_sync(kFull, q2.x, (lane + 1) & 31);
-            if (KW > 1 && lane == 0) l1 = __ldg(src + (long long)i * PL + P + yrow + xm);
-            if (KW > 1 && lane == 31) r2 = __ldg(src + (long long)i * PL + 2 * P + yrow + xp);
-            if (!PERIODIC && x == 0) l1 = q2.x;
-            if (!PERIODIC && x + 4 == NXB) r2 = q1.w;
-            const float4 g1 = make_float4(l1, q1.x, q1.y, q1.z);
-            const float4 g2 = make_float4(q2.y, q2.z, q2.w, r2);
-            const Quad7 o = collide_quad(q0, g1, g2, q3, q4, q5, q6, phC, s_sa, s_sc, kn.kT, kn.kJ);
-            float* w = fn + si * RS + own;           // block row 0 only writes population 3
-            if (tile_row) {
-                *reinterpret_cast<float4*>(w) = o.o[0];
-                *reinterpret_cast<float4*>(w + Q1) = o.o[1];
-                *reinterpret_cast<float4*>(w + Q2) = o.o[2];
-                *reinterpret_cast<float4*>(w + Q3) = o.o[3];
-                *reinterpret_cast<float4*>(w + Q4) = o.o[4];
-                *reinterpret_cast<float4*>(w + Q5) = o.o[5];
-                *reinterpret_cast<float4*>(w + Q6) = o.o[6];
-            } else if (r == 0) {
-                *reinterpret_cast<float4*>(w + Q3) = o.o[3];
-            } else {
-                *reinterpret_cast<float4*>(w + Q4) = o.o[4];
+            if (first) {
+                if (!own_left) l1 = __ldg(src + (long long)i * PL + P + yrow + xm);
+                if (!own_right) r2 = __ldg(src + (long long)i * PL + 2 * P + yrow + xp);
+                if (!PERIODIC && x == 0) l1 = q2.x;
+                if (!PERIODIC && x + 4 == NXB) r2 = q1.w;
+                const float4 g1 = make_float4(l1, q1.x, q1.y, q1.z);
+                const float4 g2 = make_float4(q2.y, q2.z, q2.w, r2);
+                const Quad7 o = collide_quad(q0, g1, g2, q3, q4, q5, q6, phC, s_sa, s_sc, kn.kT, kn.kJ);
+                float* w = fn + si * RS + own;       // block row 0 only writes population 3
+                if (tile_row) {
+                    *reinterpret_cast<float4*>(w) = o.o[0];
+                    *reinterpret_cast<float4*>(w + Q1) = o.o[1];
+                    *reinterpret_cast<float4*>(w + Q2) = o.o[2];
+                    *reinterpret_cast<float4*>(w + Q3) = o.o[3];
+                    *reinterpret_cast<float4*>(w + Q4) = o.o[4];
+                    *reinterpret_cast<float4*>(w + Q5) = o.o[5];
+                    *reinterpret_cast<float4*>(w + Q6) = o.o[6];
+                } else if (r == 0) {
+                    *reinterpret_cast<float4*>(w + Q3) = o.o[3];
+                } else {                                 // r == fyb + 1
+                    *reinterpret_cast<float4*>(w + Q4) = o.o[4];
+                }
             }
         }
         phA = phB;
@@ -833,6 +878,73 @@ __global__ void __launch_bounds__(fused2_threads(KW), f2_minb(KW)) fused2_kernel
         si = up ? s_inc : s_dec;
         __syncthreads();
     }
+}
+
+template <bool PERIODIC, int NXC>
+__global__ void __launch_bounds__(f2_bound_threads(NXC), f2_bound_blocks(NXC))
+    fused2_kernel(const StepArgs a, int fy, int zchunk, int flip) {
+    const int NXB = NXC ? NXC : a.pitch;
+    float4* s_sa;
+    float2* s_sc;
+    float* fn = fused2_tables(a, 3 * f2_slot_rows(fy) * NXB, &s_sa, &s_sc);
+    fused2_body<PERIODIC, NXC>(a, fn, s_sa, s_sc, fy, blockIdx.x, blockIdx.y, zchunk, flip);
+}
+
+// Launch plan of the two-step kernel for a canonical nx x ny x nz cell:
+// the kernel variant (nxc: 128, 256 or 0 for the runtime row width), tile
+// height fy, block size, z chunk and grid.  The score estimates the useful
+// fraction of the work: rows computed once per tile (fy of fy + 2 for the
+// first step), planes computed once per chunk (zc of zc + 2), the fill of the
+// last wave of blocks and the warps resident per SM (two blocks of 320
+// threads measured best on rows of 128; one block per SM loses ~15 %).
+struct F2Plan {
+    bool ok;
+    int nxc, fy, threads, zchunk, bxy, nzc;
+    double score;
+};
+
+template <typename Occ>
+F2Plan f2_plan(int nx, int ny, int nz, int n_phases, int n_sm, int smem_max, Occ blocks_per_sm) {
+    F2Plan best{};
+    best.ok = false;
+    best.score = -1.0;
+    if (nx % 4 != 0 || nx < 4 || ny < 1 || nz < 1) return best;
+    const int nq = nx / 4;
+    const int nxc = nx == 128 ? 128 : (nx == 256 ? 256 : 0);
+    const int fy_lo = nxc ? 8 : 1;
+    const int fy_hi = nxc ? 8 : F2_MAX_THREADS / nq - 2;
+    for (int fy = fy_lo; fy <= fy_hi; ++fy) {
+        const int threads = (fy + 2) * nq;
+        if (threads > f2_bound_threads(nxc)) break;
+        const size_t smem = fused2_smem_bytes(nx, fy, n_phases);
+        if (smem > (size_t)smem_max) break;
+        const int nb = blocks_per_sm(nxc, threads, (size_t)smem);
+        if (nb < 1) continue;
+        const int bxy = (ny + fy - 1) / fy;
+        const double rows = (double)ny / (double)(bxy * (fy + 2));
+        const double occ = std::min(1.0, nb * threads / 640.0) * (nb >= 2 ? 1.0 : 0.85);
+        const long long slots = (long long)nb * n_sm;
+        for (int nzc = 1; nzc <= nz; ++nzc) {
+            const int zc = (nz + nzc - 1) / nzc;
+            if (nzc > 1 && zc < 4) break;
+            const int nchunks = (nz + zc - 1) / zc;
+            if (nchunks != nzc) continue;
+            const long long blocks = (long long)bxy * nchunks;
+            const double fill = (double)blocks / (double)(((blocks + slots - 1) / slots) * slots);
+            const double score = fill * zc / (zc + 2.0) * rows * occ;
+            if (score > best.score + 1e-9) {
+                best.ok = true;
+                best.score = score;
+                best.nxc = nxc;
+                best.fy = fy;
+                best.threads = threads;
+                best.zchunk = zc;
+                best.bxy = bxy;
+                best.nzc = nchunks;
+            }
+        }
+    }
+    return best;
 }
 
 // The single-solve step: blockIdx.x is the block within the plane,

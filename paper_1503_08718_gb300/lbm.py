@@ -49,7 +49,18 @@ class lbm_solve_opts(ctypes.Structure):
 class lbm_batch_info(ctypes.Structure):
     _fields_ = [("n_solves", ctypes.c_int32), ("n_converged", ctypes.c_int32),
                 ("total_updates", ctypes.c_int64), ("elapsed_ms", ctypes.c_double),
-                ("block_threads", ctypes.c_int32), ("status", ctypes.c_int32)]
+                ("block_threads", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("steps_per_launch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class lbm_launch_plan(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("pitch", ctypes.c_int32), ("steps_per_launch", ctypes.c_int32),
+                ("tile_rows", ctypes.c_int32), ("zchunk", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -112,6 +123,9 @@ _PROTOS = {
     "lbm_batch_result": (ctypes.c_int, [_ctx_p, ctypes.c_int, ctypes.POINTER(lbm_solve_info)]),
     "lbm_batch_get_temperature": (ctypes.c_int, [_ctx_p, ctypes.c_int,
                                                  ctypes.POINTER(ctypes.c_float)]),
+    "lbm_batch_set_initial": (ctypes.c_int, [_ctx_p, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
+    "lbm_batch_get_history": (ctypes.c_int, [_ctx_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "lbm_batch_last_error": (ctypes.c_char_p, [_ctx_p]),
     "lbm_batch_destroy": (None, [_ctx_p]),
     "lbm_nn_conv3d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
@@ -129,6 +143,7 @@ _PROTOS = {
     "lbm_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "lbm_create_with_workspace": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(_ctx_p)]),
+    "lbm_get_launch_plan": (ctypes.c_int, [_ctx_p, ctypes.POINTER(lbm_launch_plan)]),
     "lbm_state_bytes": (ctypes.c_size_t, [_ctx_p]),
     "lbm_get_state": (ctypes.c_int, [_ctx_p, ctypes.c_void_p, ctypes.c_size_t]),
     "lbm_set_state": (ctypes.c_int, [_ctx_p, ctypes.c_void_p, ctypes.c_size_t]),
@@ -287,6 +302,12 @@ def lbm_braid_voxelize_noalloc(nx: int, ny: int, nz: int, g_rad: float, A: float
     return st, used.value, frac.value, msg.value.decode()
 
 
+def lbm_get_launch_plan(ctx):
+    p = lbm_launch_plan()
+    st = load().lbm_get_launch_plan(ctx, ctypes.byref(p))
+    return st, p
+
+
 def lbm_state_bytes(ctx) -> int:
     return int(load().lbm_state_bytes(ctx))
 
@@ -339,6 +360,21 @@ def lbm_batch_result(b, i: int, info: lbm_solve_info) -> int:
 def lbm_batch_get_temperature(b, i: int, out: np.ndarray) -> int:
     assert out.dtype == np.float32 and out.flags.c_contiguous
     return load().lbm_batch_get_temperature(b, i, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+
+
+def lbm_batch_set_initial(b, i: int, t_init) -> int:
+    if t_init is None:
+        return load().lbm_batch_set_initial(b, i, None)
+    t_init = np.ascontiguousarray(t_init, dtype=np.float32)
+    return load().lbm_batch_set_initial(b, i, t_init.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+
+
+def lbm_batch_get_history(b, i: int, max_entries: int = 4096):
+    """Returns (status, array (n, 5) of iteration, k_eff, R_T, R_Q, ms)."""
+    out = np.zeros((max_entries, 5), np.float64)
+    n = ctypes.c_int(0)
+    st = load().lbm_batch_get_history(b, i, _f64(out), max_entries, ctypes.byref(n))
+    return st, out[: n.value]
 
 
 def lbm_batch_last_error(b) -> str:
@@ -478,6 +514,11 @@ class Solver:
         self._ok(st)
         return h
 
+    def launch_plan(self) -> dict:
+        st, p = lbm_get_launch_plan(self.h)
+        self._ok(st)
+        return p.as_dict()
+
     def get_state(self) -> np.ndarray:
         out = np.empty(lbm_state_bytes(self.h), np.uint8)
         self._ok(lbm_get_state(self.h, out))
@@ -528,6 +569,16 @@ class Batch:
         out = np.empty(self.shapes[i], np.float32)
         self._ok(lbm_batch_get_temperature(self.h, i, out))
         return out
+
+    def set_initial(self, i, t_init):
+        if t_init is not None:
+            assert tuple(np.shape(t_init)) == tuple(self.shapes[i])
+        self._ok(lbm_batch_set_initial(self.h, i, t_init))
+
+    def history(self, i) -> np.ndarray:
+        st, h = lbm_batch_get_history(self.h, i)
+        self._ok(st)
+        return h
 
     def close(self):
         if getattr(self, "h", None):

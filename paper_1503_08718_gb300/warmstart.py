@@ -113,8 +113,15 @@ class WarmNet:
         self.hb.copy_(torch.from_numpy(np.asarray(hb, np.float32).reshape(-1)))
         self._sync_bf16()
 
-    def save(self, path: str):
-        arrs = {f"W{l}": w.cpu().numpy() for l, w in enumerate(self.W)}
+    def save(self, path: str, bf16: bool = False):
+        """Weights to an .npz file; bf16 keeps the convolution weights as the
+        BF16 bit patterns the layers compute with (half the size)."""
+        if bf16:
+            torch = self.torch
+            arrs = {f"W{l}": w.to(torch.bfloat16).view(torch.int16).cpu().numpy().view(np.uint16)
+                    for l, w in enumerate(self.W)}
+        else:
+            arrs = {f"W{l}": w.cpu().numpy() for l, w in enumerate(self.W)}
         arrs["chans"] = np.array(self.chans)
         arrs["train_height"] = np.array(self.train_height)
         arrs.update({f"b{l}": b.cpu().numpy() for l, b in enumerate(self.b)})
@@ -130,7 +137,10 @@ class WarmNet:
         if "train_height" in z:
             self.train_height = int(z["train_height"])
         for l in range(len(self.layers)):
-            self.W[l].copy_(torch.from_numpy(z[f"W{l}"]))
+            w = z[f"W{l}"]
+            if w.dtype == np.uint16:                 # BF16 bit patterns
+                w = (w.astype(np.uint32) << 16).view(np.float32)
+            self.W[l].copy_(torch.from_numpy(np.ascontiguousarray(w)))
             self.b[l].copy_(torch.from_numpy(z[f"b{l}"]))
         self.hw.copy_(torch.from_numpy(z["hw"]))
         self.hb.copy_(torch.from_numpy(z["hb"]))
@@ -355,9 +365,7 @@ def generate_cells(seeds, n=64, g_range=(20.0, 45.0), phi_range=(0.30, 0.60), A=
     library's batched solver (z axis, periodic laterals, FP32)."""
     phases, lams = [], []
     for s in seeds:
-        r = I.SplitMix64(10_000 + int(s))
-        g = g_range[0] + (g_range[1] - g_range[0]) * r.uniform()
-        phi = phi_range[0] + (phi_range[1] - phi_range[0]) * r.uniform()
+        g, phi = I.warm_cell_params(s, g_range, phi_range)
         with lbm.Solver(n, n, n, device) as S:
             S.set_geometry_braid(math.radians(g), I.braid_anchors(n, n, int(s), n_max=256), phi, A, B)
             phases.append(S.geometry())
@@ -423,9 +431,7 @@ def evaluate(net, seeds, shape=(128, 128, 256), tol=1e-8, rel=1e-4, max_iters=3_
     nx, ny, nz = shape
     rows = []
     for s in seeds:
-        r = I.SplitMix64(10_000 + int(s))
-        g = 20.0 + 25.0 * r.uniform()
-        phi = 0.30 + 0.30 * r.uniform()
+        g, phi = I.warm_cell_params(s)
         lam = I.braid_tensors(g)
         S = lbm.Solver(nx, ny, nz, device)
         S.set_geometry_braid(math.radians(g), I.braid_anchors(nx, ny, int(s), n_max=512), phi)
@@ -478,7 +484,8 @@ def main(argv=None):
     ap.add_argument("--eval-cells", type=int, default=10)
     ap.add_argument("--eval-shape", default="128,128,256")
     ap.add_argument("--weights", default=None, help="load instead of training")
-    ap.add_argument("--out", default=None, help="save the trained weights here")
+    ap.add_argument("--out", default=None, help="save the trained weights here (BF16)")
+    ap.add_argument("--skip-eval", action="store_true")
     a = ap.parse_args(argv)
     chans = tuple(int(c) for c in a.chans.split(","))
     net = WarmNet(seed=0, chans=chans)
@@ -495,7 +502,10 @@ def main(argv=None):
         summary.update(train_cells=a.train_cells, epochs=a.epochs, data_s=t1 - t0,
                        train_s=t2 - t1, mse_first=hist[0], mse_last=hist[-1])
         if a.out:
-            net.save(a.out)
+            net.save(a.out, bf16=True)
+    if a.skip_eval:
+        print(json.dumps(summary))
+        return
     shape = tuple(int(c) for c in a.eval_shape.split(","))
     rows = evaluate(net, range(5000, 5000 + a.eval_cells), shape=shape)
     summary["eval"] = rows

@@ -6,9 +6,12 @@ voxelised by the oracle's own voxeliser and iterated from the linear start
 (the initial field of the method's reading 11) in chunks of `chunk` steps;
 after each chunk the plane fluxes give k_eff and the spread R_Q (Eq. 22 and
 Fig. 8: all plane fluxes are equal at the steady state).  The run stops
-when R_Q <= rq_tol; the record keeps the iteration count, the final R_Q and
-the change of k_eff over the last chunk, and the SHA-256 of the phase map so
-that a consumer can check it voxelised the same cell.
+when R_Q <= rq_tol, or (--dk-tol, for cells too large to iterate that far on
+the host) when k_eff changed by at most dk_tol over the last chunk: the
+error decays geometrically, so what remains is a few times the last change.
+The record keeps the iteration count, the final R_Q and the change of k_eff
+over the last chunk, and the SHA-256 of the phase map so that a consumer can
+check it voxelised the same cell.
 
 Usage: python tests/golden/make_keff_reference.py [--only LABEL] [--threads N]
 Cells:
@@ -48,7 +51,7 @@ def cells():
                    n_anchors=256, axis=2, lateral=0)
 
 
-def solve(c, rq_tol, chunk, max_iters, log):
+def solve(c, rq_tol, dk_tol, chunk, max_iters, log):
     nx, ny, nz = c["shape"]
     anchors = I.braid_anchors(nx, ny, c["seed"], n_max=c["n_anchors"])
     phase, used, frac = O.braid_phase(nx, ny, nz, math.radians(c["g_deg"]), anchors, c["phi"])
@@ -62,12 +65,13 @@ def solve(c, rq_tol, chunk, max_iters, log):
         k, rq = L.k_eff()
         dk = None if k_prev is None else abs(k / k_prev - 1.0)
         log(f"{c['label']}: iter {L.iter} k {k:.12f} R_Q {rq:.3e} dk {dk}")
-        if rq <= rq_tol or L.iter >= max_iters:
+        if rq <= rq_tol or (dk is not None and dk <= dk_tol) or L.iter >= max_iters:
             break
         k_prev = k
     return dict(c, shape=list(c["shape"]), phase_sha256=hashlib.sha256(phase.tobytes()).hexdigest(),
                 yarns=used, yarn_fraction=frac, lattice_scale=s, k_star=k, iters=L.iter,
-                residual_Q=rq, dk_last_chunk=dk, converged=bool(rq <= rq_tol),
+                residual_Q=rq, dk_last_chunk=dk,
+                converged=bool(rq <= rq_tol or (dk is not None and dk <= dk_tol)),
                 seconds=time.time() - t0, threads=O.max_threads())
 
 
@@ -76,6 +80,8 @@ def main():
     ap.add_argument("--only", default=None)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--rq-tol", type=float, default=1e-10)
+    ap.add_argument("--dk-tol", type=float, default=0.0,
+                    help="also stop once k_eff changes by at most this (relative) over a chunk")
     ap.add_argument("--chunk", type=int, default=1000)
     ap.add_argument("--max-iters", type=int, default=2_000_000)
     a = ap.parse_args()
@@ -93,8 +99,9 @@ def main():
             continue
         if c["label"] in data["cells"] and data["cells"][c["label"]].get("converged"):
             continue
-        r = solve(c, a.rq_tol, a.chunk, a.max_iters, lambda m: print(m, flush=True))
+        r = solve(c, a.rq_tol, a.dk_tol, a.chunk, a.max_iters, lambda m: print(m, flush=True))
         r["rq_tol"] = a.rq_tol
+        r["dk_tol"] = a.dk_tol
         data["cells"][c["label"]] = r
         with open(OUT + ".tmp", "w") as fh:
             json.dump(data, fh, indent=1, sort_keys=True)

@@ -326,16 +326,27 @@ def test_history_records_every_check():
         assert row[1] == pytest.approx(ref.k_eff()[0], rel=K_TOL)
 
 
+FUSED_SHAPES = [
+    # rows of 128 and 256 nodes (the tuned kernel variants): one z chunk
+    # along z and from x, several z chunks, rows of two warps
+    (2, (128, 16, 24)), (0, (24, 128, 16)), (2, (128, 16, 80)), (2, (256, 8, 40)),
+    # any row width that is a multiple of 4 (the runtime-width variant):
+    # two rows per warp, rows straddling warps, rows of several warps, a
+    # last tile shorter than the others, one-quad rows (the x-wrap stays in
+    # the thread), and the other axes
+    (2, (64, 40, 30)), (2, (80, 24, 20)), (2, (96, 13, 22)), (2, (160, 14, 18)),
+    (2, (32, 9, 10)), (2, (4, 3, 7)), (2, (8, 5, 12)), (1, (20, 36, 44)), (0, (33, 48, 12)),
+]
+
+
 @pytest.mark.parametrize("lateral", [0, 1])
-@pytest.mark.parametrize("axis,shape", [(2, (128, 16, 24)), (0, (24, 128, 16)), (2, (128, 16, 80)),
-                                        (2, (256, 8, 40))])
+@pytest.mark.parametrize("axis,shape", FUSED_SHAPES)
 def test_fused_pairs_equal_single_steps_bit_for_bit(lateral, axis, shape):
     """Two steps fused in one kernel (temporal blocking) do each node's
     arithmetic exactly as two single steps: identical fields and k_eff,
-    through the graph loop and through lbm_advance.  Shapes (canonical rows
-    of 128 or 256 nodes, the layouts the fused kernel takes): one z chunk
-    along z and from x, several z chunks (128 x 16 x 80), and rows of two
-    warps (256 x 8 x 40)."""
+    through the graph loop and through lbm_advance, for every row width that
+    takes the fused kernel (the launch plan says it ran) and tile heights
+    that leave a shorter last tile."""
     rng = np.random.default_rng(31 + lateral + axis + shape[2])
     lam = np.stack([I.random_spd(rng) for _ in range(3)])
     phase = I.random_phase(rng, *shape, 3)
@@ -345,6 +356,10 @@ def test_fused_pairs_equal_single_steps_bit_for_bit(lateral, axis, shape):
         S.set_geometry(phase, 3)
         S.set_tensors(lam)
         info = S.solve(axis, lateral, S.opts(tol=0.0, max_iters=300, fuse=fuse))
+        plan = S.launch_plan()
+        assert plan["steps_per_launch"] == (2 if fuse else 1), plan
+        if fuse:
+            assert plan["nx"] % 4 == 0 and plan["tile_rows"] >= 1
         T1 = S.temperature()
         S.start(axis, lateral, S.opts(fuse=fuse))
         S.advance(37)
