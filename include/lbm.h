@@ -90,10 +90,13 @@ typedef struct {
     int32_t fuse;           /* 1 (default): FP32 plain steps run two at a time in one
                                kernel (temporal blocking) when the canonical rows hold a
                                multiple of 4 nodes (lbm_start orders the lateral axes to
-                               allow it); identical results; a batch's autotuner then
-                               also times single steps and keeps the faster.  2: as 1,
-                               but a batch uses two-step launches whenever every solve
-                               allows them.  0: single steps only */
+                               allow it) and the cell gives every SM at least one block
+                               of four warps; identical results; a batch's autotuner
+                               also times single steps and keeps the faster.  2: two
+                               steps per launch whenever the rows allow it, however
+                               small the cell (and in a batch whenever every solve
+                               allows it).  0: single steps only.  The layout does not
+                               depend on this field. */
     int32_t reserved;
     const float* t_init;    /* host, nx*ny*nz initial T field in the original axis
                                order, or NULL for the linear profile between walls */
@@ -354,6 +357,31 @@ void lbm_batch_destroy(lbm_batch* b);
 lbm_status lbm_nn_conv3d(const void* x, int cin, const void* w, const float* bias, void* y, int cout,
                          int n, int d, int h, int wdt, int ksize, int relu, int out_f32,
                          void* stream);
+
+/* The same 3x3x3 convolution (bias, leaky ReLU, BF16 or FP32 output) on the
+ * fifth-generation tensor cores: tcgen05.mma with the accumulator in tensor
+ * memory, one block per tile of 16 x 8 output voxels of a plane, the tile's
+ * halo staged once in shared memory and read by every tap's MMA through its
+ * own descriptor.  wk: K-major weights [27][cout][cin] (lbm_nn_weights_kmajor).
+ * Requires cin and cout multiples of 16, cout <= 256, h a multiple of 16 and
+ * w a multiple of 8 (lbm_nn_conv3d_tc_supported); else LBM_ERR_INVALID_ARG.
+ * Each block bounds its waits; a timeout is recorded for lbm_nn_tc_error. */
+lbm_status lbm_nn_conv3d_tc(const void* x, int cin, const void* wk, const float* bias, void* y, int cout,
+                            int n, int d, int h, int wdt, int relu, int out_f32, void* stream);
+
+/* 1 if lbm_nn_conv3d_tc takes these sizes, else 0.  Host-only. */
+int lbm_nn_conv3d_tc_supported(int cin, int cout, int n, int d, int h, int w);
+
+/* K-major weights for lbm_nn_conv3d_tc from w [27][cin][cout]: flip = 0 gives
+ * wk[tap][co][ci] = w[tap][ci][co] (the forward conv); flip = 1 gives
+ * wk[tap][ci][co] = w[26 - tap][ci][co], the weights of the data gradient's
+ * conv (input channels cout, output channels cin). */
+lbm_status lbm_nn_weights_kmajor(const void* w, void* wk, int cin, int cout, int flip, void* stream);
+
+/* First error recorded by a lbm_nn_conv3d_tc block since the last clear (0:
+ * none; 1: a bounded wait on the tensor core expired).  clear != 0 resets it.
+ * Synchronous. */
+lbm_status lbm_nn_tc_error(int* out, int clear);
 
 /* dw[tap][ci][co] += sum_v x[v + tap][ci] g[v][co] (FP32 accumulation into dw;
  * zero dw first).  Same layouts and padding as lbm_nn_conv3d. */

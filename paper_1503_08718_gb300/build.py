@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libmrtlbm.so")
-SOURCES = ["lbm_capi.cu", "lbm_voxel.cu", "lbm_batch.cu", "lbm_nn.cu"]
+SOURCES = ["lbm_capi.cu", "lbm_voxel.cu", "lbm_batch.cu", "lbm_nn.cu", "lbm_nn_tc.cu"]
 HEADERS = ["lbm_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

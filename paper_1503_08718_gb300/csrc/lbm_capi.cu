@@ -288,9 +288,9 @@ const void* f2_kernel(bool periodic, int nxc) {
     return periodic ? f2_kernel_ptr<true, 0>() : f2_kernel_ptr<false, 0>();
 }
 
-lbm::F2Plan f2_plan_for(const lbm_ctx* c, int nx, int ny, int nz, int n_phases, bool periodic) {
+lbm::F2Plan f2_plan_for(const lbm_ctx* c, int nx, int ny, int nz, int n_phases, bool periodic, bool force) {
     if (!c->fuse_ok) return lbm::F2Plan{};
-    return lbm::f2_plan(nx, ny, nz, n_phases, c->n_sm, c->f2_smem_max,
+    return lbm::f2_plan(nx, ny, nz, n_phases, c->n_sm, c->f2_smem_max, force,
                         [&](int nxc, int threads, size_t smem) {
                             int nb = 0;
                             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f2_kernel(periodic, nxc), threads,
@@ -736,17 +736,21 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
         L.n[i] = c->n[i];
         L.perm[i] = perms[axis][i];
     }
+    // (the order depends on the geometry only, not on opts.fuse, so that a
+    // solve with fused pairs and one without share the layout bit for bit)
     lbm::F2Plan f2{};
-    if (op.fuse && op.storage == LBM_STORE_F32) {
+    if (op.storage == LBM_STORE_F32) {
         const bool per = lateral == LBM_LATERAL_PERIODIC;
-        f2 = f2_plan_for(c, c->n[L.perm[0]], c->n[L.perm[1]], c->n[L.perm[2]], c->n_phases, per);
-        const lbm::F2Plan sw = f2_plan_for(c, c->n[L.perm[1]], c->n[L.perm[0]], c->n[L.perm[2]], c->n_phases, per);
-        if (sw.ok && (!f2.ok || sw.score > f2.score * 1.001)) {
+        const lbm::F2Plan a0 = f2_plan_for(c, c->n[L.perm[0]], c->n[L.perm[1]], c->n[L.perm[2]], c->n_phases, per, true);
+        const lbm::F2Plan a1 = f2_plan_for(c, c->n[L.perm[1]], c->n[L.perm[0]], c->n[L.perm[2]], c->n_phases, per, true);
+        if (a1.ok && (!a0.ok || a1.score > a0.score * 1.001)) {
             const int t = L.perm[0];
             L.perm[0] = L.perm[1];
             L.perm[1] = t;
-            f2 = sw;
         }
+        // fuse = 2 takes the two-step kernel even where it would not pay
+        if (op.fuse)
+            f2 = f2_plan_for(c, c->n[L.perm[0]], c->n[L.perm[1]], c->n[L.perm[2]], c->n_phases, per, op.fuse == 2);
     }
     L.NX = c->n[L.perm[0]];
     L.NY = c->n[L.perm[1]];

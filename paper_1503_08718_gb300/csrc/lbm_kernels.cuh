@@ -688,6 +688,9 @@ __device__ __forceinline__ void fused2_body(const StepArgs& a, float* fn, const 
                                             const int zchunk, const int flip) {
     const int NXB = NXC ? NXC : a.pitch;           // nodes per row (= nx = pitch)
     const int nq = NXB >> 2;                       // threads per row
+    // rows of whole warps: every branch on the row is warp-uniform, so a
+    // warp whose row has no work skips the step (shuffles included)
+    constexpr bool WR = NXC > 0 && NXC % 128 == 0;
     const int RS = f2_slot_rows(FY) * NXB;         // floats per ring plane
     // population offsets within a ring plane, for block row r at row r - 1:
     // population 3 keeps block rows 0 .. FY, population 4 rows 1 .. FY + 1
@@ -802,18 +805,19 @@ __device__ __forceinline__ void fused2_body(const StepArgs& a, float* fn, const 
             q5 = __ldg(reinterpret_cast<const float4*>(s + (i > 0 ? 5 * P - PL : 6 * P) + yrow + x));
             q6 = __ldg(reinterpret_cast<const float4*>(s + (i < nz - 1 ? 6 * P + PL : 5 * P) + yrow + x));
             phC = __ldg(reinterpret_cast<const unsigned*>(a.phase + (long long)i * PL + yrow + x));
-        } else {
+        } else if (!WR) {
             q0 = q1 = q2 = q3 = q4 = q5 = q6 = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         // ---- step n + 1 at plane j, tile rows ----
         const int own = (r - 1) * NXB + x;          // this thread's nodes in a ring plane
-        {
-            const bool second = tile_row && j >= z0 && j < z1;
+        const bool second = tile_row && j >= z0 && j < z1;
+        if (!WR || second) {
             const float* fs = fn + sj * RS + own;
             const float* fb = fn + sjm * RS + own;
             const float* fa = fn + sjp * RS + own;
-            float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = g0, c2 = g0, g3 = g0, g4 = g0, g5 = g0, g6 = g0;
-            if (second) {
+            float4 g0, c1, c2, g3, g4, g5, g6;
+            if (!WR && !second) g0 = c1 = c2 = g3 = g4 = g5 = g6 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (WR || second) {
                 g0 = *reinterpret_cast<const float4*>(fs);
                 c1 = *reinterpret_cast<const float4*>(fs + Q1);
                 c2 = *reinterpret_cast<const float4*>(fs + Q2);
@@ -830,7 +834,7 @@ __device__ __forceinline__ void fused2_body(const StepArgs& a, float* fn, const 
             // from the ring row
             float l1 = __shfl_sync(kFull, c1.w, (lane + 31) & 31);
             float r2 = __shfl_sync(kFull, c2.x, (lane + 1) & 31);
-            if (second) {
+            if (WR || second) {
                 if (!own_left) l1 = fs[Q1 - x + xm];
                 if (!own_right) r2 = fs[Q2 - x + xp];
                 if (!PERIODIC && x == 0) l1 = c2.x;                 // Eq. 24 at x = 0
@@ -844,12 +848,12 @@ __device__ __forceinline__ void fused2_body(const StepArgs& a, float* fn, const 
             }
         }
         // ---- step n at plane i into the ring ----
-        {
+        if (!WR || first) {
             if (i == 0) q5 = f4neg(q5);
             if (i == nz - 1) q6 = f4neg(q6);
             float l1 = __shfl_sync(kFull, q1.w, (lane + 31) & 31);
             float r2 = __shfl_sync(kFull, q2.x, (lane + 1) & 31);
-            if (first) {
+            if (WR || first) {
                 if (!own_left) l1 = __ldg(src + (long long)i * PL + P + yrow + xm);
                 if (!own_right) r2 = __ldg(src + (long long)i * PL + 2 * P + yrow + xp);
                 if (!PERIODIC && x == 0) l1 = q2.x;
@@ -903,8 +907,10 @@ struct F2Plan {
     double score;
 };
 
+// force: take the best valid plan even for a cell too small to profit (the
+// fused kernel on every shape, for tests and for choosing the layout).
 template <typename Occ>
-F2Plan f2_plan(int nx, int ny, int nz, int n_phases, int n_sm, int smem_max, Occ blocks_per_sm) {
+F2Plan f2_plan(int nx, int ny, int nz, int n_phases, int n_sm, int smem_max, bool force, Occ blocks_per_sm) {
     F2Plan best{};
     best.ok = false;
     best.score = -1.0;
@@ -916,6 +922,7 @@ F2Plan f2_plan(int nx, int ny, int nz, int n_phases, int n_sm, int smem_max, Occ
     for (int fy = fy_lo; fy <= fy_hi; ++fy) {
         const int threads = (fy + 2) * nq;
         if (threads > f2_bound_threads(nxc)) break;
+        if (threads < 128 && !force) continue;     // at least four warps per block
         const size_t smem = fused2_smem_bytes(nx, fy, n_phases);
         if (smem > (size_t)smem_max) break;
         const int nb = blocks_per_sm(nxc, threads, (size_t)smem);
@@ -930,6 +937,10 @@ F2Plan f2_plan(int nx, int ny, int nz, int n_phases, int n_sm, int smem_max, Occ
             const int nchunks = (nz + zc - 1) / zc;
             if (nchunks != nzc) continue;
             const long long blocks = (long long)bxy * nchunks;
+            // a cell too small to give every SM a block runs single steps:
+            // the two-step kernel's serial march through the planes would
+            // only add latency there
+            if (blocks < n_sm && !force) continue;
             const double fill = (double)blocks / (double)(((blocks + slots - 1) / slots) * slots);
             const double score = fill * zc / (zc + 2.0) * rows * occ;
             if (score > best.score + 1e-9) {

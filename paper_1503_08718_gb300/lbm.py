@@ -129,6 +129,10 @@ _PROTOS = {
     "lbm_batch_last_error": (ctypes.c_char_p, [_ctx_p]),
     "lbm_batch_destroy": (None, [_ctx_p]),
     "lbm_nn_conv3d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "lbm_nn_conv3d_tc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "lbm_nn_conv3d_tc_supported": (ctypes.c_int, [ctypes.c_int] * 6),
+    "lbm_nn_weights_kmajor": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "lbm_nn_tc_error": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     "lbm_nn_conv3d_wgrad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "lbm_nn_flip_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "lbm_nn_bias_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p]),
@@ -398,6 +402,18 @@ def _nn(name):
 
 lbm_nn_conv3d = _nn("lbm_nn_conv3d")
 lbm_nn_conv3d_wgrad = _nn("lbm_nn_conv3d_wgrad")
+lbm_nn_conv3d_tc = _nn("lbm_nn_conv3d_tc")
+lbm_nn_conv3d_tc_supported = _nn("lbm_nn_conv3d_tc_supported")
+lbm_nn_weights_kmajor = _nn("lbm_nn_weights_kmajor")
+
+
+def lbm_nn_tc_error(clear: bool = True) -> int:
+    """Error word of the tensor-core convolution (0: none); raises on a CUDA error."""
+    v = ctypes.c_int(0)
+    st = load().lbm_nn_tc_error(ctypes.byref(v), int(clear))
+    if st != LBM_OK:
+        raise LBMError(st, "reading the tensor-core convolution's error word failed")
+    return v.value
 lbm_nn_flip_weights = _nn("lbm_nn_flip_weights")
 lbm_nn_bias_grad = _nn("lbm_nn_bias_grad")
 lbm_nn_relu_mask = _nn("lbm_nn_relu_mask")

@@ -66,9 +66,13 @@ class WarmNet:
     """Parameters and optimiser state on the GPU; forward and backward passes
     over a batch of n cells of d x h x w (all multiples of 4)."""
 
-    def __init__(self, seed: int = 0, device: int = 0, chans=CHANS, train_height: int = 64):
+    def __init__(self, seed: int = 0, device: int = 0, chans=CHANS, train_height: int = 64,
+                 use_tc: bool = True):
         torch = _torch()
         self.torch = torch
+        # 3x3x3 convolutions on the tcgen05 tensor-core kernel wherever its
+        # size rules allow (rows of 16 x 8 voxels), else the mma.sync kernel
+        self.use_tc = bool(use_tc)
         # cell height (along z) of the training cells: the correction to the
         # linear profile scales with the wall-to-wall gradient, so predictions
         # for a cell of height d are rescaled by train_height / d
@@ -98,6 +102,28 @@ class WarmNet:
     def _sync_bf16(self):
         torch = self.torch
         self.Wb = [w.to(torch.bfloat16).contiguous() for w in self.W]
+        self._refresh_kmajor()
+
+    def _refresh_kmajor(self):
+        """K-major copies of the BF16 weights for the tensor-core kernel:
+        [27][cout][cin] for the forward conv, [27][cin][cout] with the taps
+        reversed for the data gradient."""
+        torch = self.torch
+        if not hasattr(self, "Wk"):
+            self.Wk = [torch.empty((27, co, ci), dtype=torch.bfloat16, device=self.dev)
+                       for ci, co in self.layers]
+            self.Wkf = [torch.empty((27, ci, co), dtype=torch.bfloat16, device=self.dev)
+                        for ci, co in self.layers]
+        s = self._stream()
+        for l, (ci, co) in enumerate(self.layers):
+            self._ok(lbm.lbm_nn_weights_kmajor(self.Wb[l].data_ptr(), self.Wk[l].data_ptr(), ci, co, 0, s),
+                     "k-major weights")
+            self._ok(lbm.lbm_nn_weights_kmajor(self.Wb[l].data_ptr(), self.Wkf[l].data_ptr(), ci, co, 1, s),
+                     "k-major flipped weights")
+
+    def _tc(self, cin, cout, vol):
+        n, d, h, w = vol
+        return self.use_tc and lbm.lbm_nn_conv3d_tc_supported(cin, cout, n, d, h, w) == 1
 
     def set_reference_params(self, params):
         """Loads weights given as [(w [cout, cin, 3, 3, 3], b), ..., head]."""
@@ -160,9 +186,14 @@ class WarmNet:
         n, d, h, w = vol
         cin, cout = self.layers[l]
         y = torch.empty((n * d * h * w, cout), dtype=torch.bfloat16, device=self.dev)
-        self._ok(lbm.lbm_nn_conv3d(x.data_ptr(), cin, self.Wb[l].data_ptr(), self.b[l].data_ptr(),
-                                   y.data_ptr(), cout, n, d, h, w, 3, int(relu), 0, self._stream()),
-                 f"conv layer {l}")
+        if self._tc(cin, cout, vol):
+            self._ok(lbm.lbm_nn_conv3d_tc(x.data_ptr(), cin, self.Wk[l].data_ptr(), self.b[l].data_ptr(),
+                                          y.data_ptr(), cout, n, d, h, w, int(relu), 0, self._stream()),
+                     f"conv layer {l} (tensor cores)")
+        else:
+            self._ok(lbm.lbm_nn_conv3d(x.data_ptr(), cin, self.Wb[l].data_ptr(), self.b[l].data_ptr(),
+                                       y.data_ptr(), cout, n, d, h, w, 3, int(relu), 0, self._stream()),
+                     f"conv layer {l}")
         return y
 
     def _pool(self, x, c, vol):
@@ -252,9 +283,13 @@ class WarmNet:
         self._ok(lbm.lbm_nn_bias_grad(g_out.data_ptr(), cout, V, self.gb[l].data_ptr(), s), "bgrad")
         if not need_dx:
             return None
+        dx = torch.empty((V, cin), dtype=torch.bfloat16, device=self.dev)
+        if self._tc(cout, cin, vol):
+            self._ok(lbm.lbm_nn_conv3d_tc(g_out.data_ptr(), cout, self.Wkf[l].data_ptr(), None, dx.data_ptr(),
+                                          cin, n, d, h, w, 0, 0, s), "dgrad (tensor cores)")
+            return dx
         wf = torch.empty((27, cout, cin), dtype=torch.bfloat16, device=self.dev)
         self._ok(lbm.lbm_nn_flip_weights(self.Wb[l].data_ptr(), wf.data_ptr(), cin, cout, 3, s), "flip")
-        dx = torch.empty((V, cin), dtype=torch.bfloat16, device=self.dev)
         self._ok(lbm.lbm_nn_conv3d(g_out.data_ptr(), cout, wf.data_ptr(), None, dx.data_ptr(), cin,
                                    n, d, h, w, 3, 0, 0, s), "dgrad")
         return dx
@@ -326,6 +361,7 @@ class WarmNet:
             self._ok(lbm.lbm_nn_adam(p.data_ptr(), g.data_ptr(), self.m[i].data_ptr(),
                                      self.v[i].data_ptr(), pb, p.numel(), lr, beta1, beta2, eps,
                                      self.t, s), "adam")
+        self._refresh_kmajor()
 
     # ---- helpers ---------------------------------------------------------
     def make_input(self, phases, lams, t_hot=1.0, t_cold=0.0):

@@ -351,7 +351,7 @@ def test_fused_pairs_equal_single_steps_bit_for_bit(lateral, axis, shape):
     lam = np.stack([I.random_spd(rng) for _ in range(3)])
     phase = I.random_phase(rng, *shape, 3)
     out = []
-    for fuse in (1, 0):
+    for fuse in (2, 0):               # 2: two steps per launch on any shape that allows it
         S = lbm.Solver(*shape)
         S.set_geometry(phase, 3)
         S.set_tensors(lam)
@@ -375,26 +375,28 @@ def test_fused_pairs_equal_single_steps_bit_for_bit(lateral, axis, shape):
 
 @pytest.mark.parametrize("lateral", [0, 1])
 def test_lateral_order_chosen_for_fused_pairs(lateral):
-    """Along y the canonical rows would hold nz = 24 nodes; with fused pairs on,
-    lbm_start orders the lateral axes the other way (rows of nx = 128).  The
-    relabelling is exact in arithmetic, so both runs follow the oracle; they
-    differ from each other only by FP32 summation order."""
+    """Along y the canonical rows could hold nx = 30 nodes (not a multiple of
+    4: no two-step kernel) or nz = 128; lbm_start orders the lateral axes so
+    that the rows hold 128 nodes, whether or not fused pairs are on.  The
+    relabelling is exact in arithmetic: the solve follows the oracle."""
     rng = np.random.default_rng(77 + lateral)
     lam = np.stack([I.random_spd(rng) for _ in range(3)])
-    shape = (128, 20, 24)
+    shape = (30, 20, 128)
     phase = I.random_phase(rng, *shape, 3)
     res = []
-    for fuse in (1, 0):
+    for fuse in (2, 0):
         S = lbm.Solver(*shape)
         S.set_geometry(phase, 3)
         S.set_tensors(lam)
         info = S.solve(1, lateral, S.opts(tol=0.0, max_iters=300, fuse=fuse))
+        plan = S.launch_plan()
+        assert plan["nx"] == 128 and plan["steps_per_launch"] == (2 if fuse else 1)
         res.append((S.temperature(), info.k_eff, info.lattice_scale))
     ref = _oracle(phase, lam, 1, lateral, res[0][2], 300)
     for T, k, _ in res:
         assert np.max(np.abs(T - ref.temperature())) <= T_TOL
         assert k == pytest.approx(ref.k_eff()[0], rel=K_TOL)
-    assert np.max(np.abs(res[0][0] - res[1][0])) <= 1e-6
+    assert np.array_equal(res[0][0], res[1][0]) and res[0][1] == res[1][1]
 
 
 @pytest.mark.parametrize("axis,lateral", [(2, 0), (0, 1)])
