@@ -362,20 +362,40 @@ lbm_status lbm_nn_conv3d(const void* x, int cin, const void* w, const float* bia
  * fifth-generation tensor cores: tcgen05.mma with the accumulator in tensor
  * memory, one block per tile of 16 x 8 output voxels of a plane, the tile's
  * halo staged once in shared memory and read by every tap's MMA through its
- * own descriptor.  wk: K-major weights [27][cout][cin] (lbm_nn_weights_kmajor).
+ * own descriptor, the taps' weight slabs streamed by cp.async.bulk through
+ * four shared-memory stages.  wk: the weight slabs lbm_nn_weights_kmajor
+ * writes (27 * cin * cout BF16).
  * Requires cin and cout multiples of 16, cout <= 256, h a multiple of 16 and
  * w a multiple of 8 (lbm_nn_conv3d_tc_supported); else LBM_ERR_INVALID_ARG.
  * Each block bounds its waits; a timeout is recorded for lbm_nn_tc_error. */
 lbm_status lbm_nn_conv3d_tc(const void* x, int cin, const void* wk, const float* bias, void* y, int cout,
                             int n, int d, int h, int wdt, int relu, int out_f32, void* stream);
 
+/* Weight gradient of the 3x3x3 convolution on the tcgen05 tensor cores,
+ * dw[tap][ci][co] += sum_v x[v + tap][ci] g[v][co] (FP32 atomics into dw;
+ * zero it first): per tap a GEMM over the voxels with both operands read
+ * channels-last (MN-major) from shared memory, the accumulators of a group
+ * of taps in tensor memory.  Same layouts and padding as lbm_nn_conv3d.
+ * Requires cin a multiple of 16, cout a multiple of 8 and at most 128, h a
+ * multiple of 16 and w of 8 (lbm_nn_conv3d_wgrad_tc_supported). */
+lbm_status lbm_nn_conv3d_wgrad_tc(const void* x, int cin, const void* g, int cout, float* dw, int n, int d,
+                                  int h, int wdt, void* stream);
+
+/* 1 if lbm_nn_conv3d_wgrad_tc takes these sizes, else 0.  Host-only. */
+int lbm_nn_conv3d_wgrad_tc_supported(int cin, int cout, int n, int d, int h, int w);
+
 /* 1 if lbm_nn_conv3d_tc takes these sizes, else 0.  Host-only. */
 int lbm_nn_conv3d_tc_supported(int cin, int cout, int n, int d, int h, int w);
 
-/* K-major weights for lbm_nn_conv3d_tc from w [27][cin][cout]: flip = 0 gives
- * wk[tap][co][ci] = w[tap][ci][co] (the forward conv); flip = 1 gives
- * wk[tap][ci][co] = w[26 - tap][ci][co], the weights of the data gradient's
- * conv (input channels cout, output channels cin). */
+/* Weight slabs for lbm_nn_conv3d_tc from w [27][cin][cout] (27 * cin * cout
+ * BF16 into wk).  The conv that uses them has K input and N output channels:
+ * flip = 0 gives the forward conv (K = cin, N = cout); flip = 1 the data
+ * gradient's conv (K = cout, N = cin, taps reversed: tap t uses
+ * w[26 - t]).  The K channels are split into groups of G = K if K <= 64, else
+ * 64, 32 or 16 (the largest that divides K); slab (tap, group) is
+ * [G/8][N][8] (input channel group*G + 8*k8 + e, output channel n), each slab
+ * contiguous, slabs in (tap, group) order: the image of one shared-memory
+ * weight stage, K-major core matrices of 8 x 8 elements. */
 lbm_status lbm_nn_weights_kmajor(const void* w, void* wk, int cin, int cout, int flip, void* stream);
 
 /* First error recorded by a lbm_nn_conv3d_tc block since the last clear (0:

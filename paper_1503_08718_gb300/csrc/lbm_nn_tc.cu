@@ -124,23 +124,39 @@ struct Vol {
     int n, d, h, w;
 };
 
-// Shared memory: halo [cg/8][3][18][10] x 16 B, then NSTAGE weight stages
-// [cg/8][N/8][8] x 16 B, then the mbarriers and the TMEM address.
+// Input channels per shared-memory halo (a channel group): the whole input
+// up to 64 channels, else groups of 64, 32 or 16.
+__host__ __device__ constexpr int cg_for(int cin) {
+    return cin <= 64 ? cin : (cin % 64 == 0 ? 64 : (cin % 32 == 0 ? 32 : 16));
+}
+
+// Shared memory of the forward kernel: halo [cg/8][3][18][10] x 16 B, then
+// NSTAGE weight stages [cg/8][N] x 16 B, then the mbarriers and the TMEM
+// address.
 __host__ __device__ constexpr size_t tc_smem_bytes(int cg, int n) {
-    return (size_t)HALO_VOX * cg * 2 + (size_t)NSTAGE * n * cg * 2 + 64;
+    return (size_t)HALO_VOX * cg * 2 + (size_t)NSTAGE * n * cg * 2 + 128;
 }
 
-// The bytes the kernel's descriptors can reach, whichever way the hardware
-// reads the two strides: the layout needs tc_smem_bytes; the launch rounds
-// the allocation up so that even the A operand walked with its strides
-// exchanged (15 x 8640 bytes across the tile's rows) stays inside it.
-__host__ __device__ constexpr size_t tc_smem_padded(int cg, int n) {
-    return tc_smem_bytes(cg, n) + (size_t)15 * HALO_VOX * 16;
+// Blocks an SM can hold are bounded by shared memory; make sure they never
+// ask for more than the SM's 512 tensor-memory columns together (a block
+// whose tcgen05.alloc cannot be served waits for another to free).
+size_t tmem_safe_smem(size_t smem, int cols) {
+    const int max_blocks = 512 / cols;
+    const size_t floor = (size_t)(227 * 1024) / (size_t)(max_blocks + 1) + 1;
+    return smem > floor ? smem : floor;
 }
 
+// Forward kernel, one tile per block.  Roles: thread 0 streams the weight
+// slabs of the taps (one cp.async.bulk per slab into a free stage, completion
+// counted on the stage's `full` mbarrier); thread 32 issues each tap's MMAs
+// once its slab is in and commits them to the stage's `empty` mbarrier, which
+// frees the stage for the producer.  All threads load the halo of a channel
+// group (cp.async) and run the epilogue.  The weights arrive pre-arranged
+// (lbm_nn_weights_kmajor): slab (tap, group) is [cg/8][N][8] BF16, exactly
+// the stage's shared-memory image.
 template <bool RELU, bool OUT_F32>
 __global__ void __launch_bounds__(THREADS) conv3_tc_kernel(const bf16* __restrict__ X, int Cin, int CG,
-                                                           const bf16* __restrict__ Wk,
+                                                           const bf16* __restrict__ Wu,
                                                            const float* __restrict__ bias,
                                                            void* __restrict__ Yv, int N, int tmem_cols,
                                                            Vol vol) {
@@ -149,12 +165,14 @@ __global__ void __launch_bounds__(THREADS) conv3_tc_kernel(const bf16* __restric
     const int CG8 = CG >> 3;
     unsigned char* halo = smem;
     unsigned char* wst = smem + (size_t)HALO_VOX * CG * 2;
-    const size_t wstage_bytes = (size_t)N * CG * 2;
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(wst + NSTAGE * wstage_bytes);
-    unsigned* tmem_slot = reinterpret_cast<unsigned*>(bars + NSTAGE);
+    const unsigned slab = (unsigned)N * CG * 2;          // bytes of one weight slab
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(wst + NSTAGE * (size_t)slab);
+    unsigned long long* empty = full + NSTAGE;
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(empty + NSTAGE);
+    __shared__ volatile int s_fail;
+    __shared__ volatile int s_consumed;             // slabs the MMA thread has waited for
     const unsigned halo_s = smem_u32(halo), wst_s = smem_u32(wst);
 
-    // tile coordinates
     const int tiles_x = vol.w / TILE_X, tiles_y = vol.h / TILE_Y;
     int b = blockIdx.x;
     const int tx = b % tiles_x; b /= tiles_x;
@@ -162,9 +180,16 @@ __global__ void __launch_bounds__(THREADS) conv3_tc_kernel(const bf16* __restric
     const int z0 = b % vol.d;
     const int n0 = b / vol.d;
     const int x0 = tx * TILE_X, y0 = ty * TILE_Y;
+    const int ngroups = Cin / CG;
+    const int total = 27 * ngroups;                 // weight slabs / MMA batches, group-major
 
     if (tid == 0) {
-        for (int s = 0; s < NSTAGE; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        s_fail = 0;
+        s_consumed = 0;
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -179,35 +204,36 @@ __global__ void __launch_bounds__(THREADS) conv3_tc_kernel(const bf16* __restric
     const unsigned tmem = *tmem_slot;
     const uint32_t idesc = instr_desc(N);
     const unsigned lbo_a = HALO_VOX * 16, sbo_a = HX * 16;
-    const unsigned lbo_b = (unsigned)(N / 8) * 128, sbo_b = 128;
+    const unsigned lbo_b = (unsigned)N * 16, sbo_b = 128;
 
-    // Waits on the mbarriers are done by thread 0 alone (bounded); it
-    // publishes a timeout through s_fail, which every thread reads after the
-    // next __syncthreads, so all threads leave the loops together.
-    __shared__ int s_fail;
-    if (tid == 0) s_fail = 0;
-    int issued = 0;                                 // MMA batches committed (one per tap)
-    const int ngroups = Cin / CG;
-    auto wait_batch = [&](int T) {                  // thread 0: batch T's MMAs are done
-        if (tid == 0 && !s_fail &&
-            !mbar_wait(smem_u32(&bars[T % NSTAGE]), (unsigned)((T / NSTAGE) & 1)))
+    // producer: slab T into stage T % NSTAGE once the MMAs that last read it
+    // are done (batch T - NSTAGE committed to `empty`)
+    auto produce = [&](int T) {
+        const int s = T % NSTAGE;
+        if (T >= NSTAGE && !mbar_wait(smem_u32(&empty[s]), (unsigned)(((T / NSTAGE) - 1) & 1))) {
             s_fail = 1;
-    };
-    auto load_weights = [&](int g, int t, int stage) {
-        const bf16* wsrc = Wk + (long long)t * N * Cin + g * CG;
-        const unsigned dst0 = wst_s + stage * (unsigned)wstage_bytes;
-        for (int i = tid; i < N * CG8; i += THREADS) {
-            const int co = i / CG8, c8 = i - co * CG8;
-            cp16(dst0 + (unsigned)(((c8 * (N / 8) + (co >> 3)) * 8 + (co & 7)) * 16),
-                 wsrc + (long long)co * Cin + c8 * 8, 16u);
+            return;
         }
+        const unsigned fb = smem_u32(&full[s]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(slab) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                wst_s + (unsigned)s * slab),
+            "l"(Wu + (size_t)((T % 27) * ngroups + T / 27) * (slab / 2)), "r"(slab), "r"(fb)
+            : "memory");
     };
+    int next = 0;                                   // next slab the producer issues
     for (int g = 0; g < ngroups; ++g) {
-        // the MMAs of the previous group read the halo and both stages
-        if (g > 0) wait_batch(issued - 1);
+        const int T0 = g * 27;
+        // the halo is rewritten: the previous group's MMAs must be done
+        if (g > 0 && tid == 32 && !s_fail &&
+            !mbar_wait(smem_u32(&empty[(T0 - 1) % NSTAGE]), (unsigned)(((T0 - 1) / NSTAGE) & 1)))
+            s_fail = 1;
         __syncthreads();
         if (s_fail) break;
-        // halo of this channel group, and the weights of its first tap
+        // the first slabs of the group start while the halo loads
+        if (tid == 0)
+            for (; next < T0 + NSTAGE && next < total && !s_fail; ++next) produce(next);
         for (int i = tid; i < HALO_VOX * CG8; i += THREADS) {
             const int hv = i / CG8, c8 = i - hv * CG8;
             const int xh = hv % HX, yh = (hv / HX) % HY, zz = hv / (HX * HY);
@@ -220,51 +246,55 @@ __global__ void __launch_bounds__(THREADS) conv3_tc_kernel(const bf16* __restric
             cp16(halo_s + (unsigned)((((c8 * HZ + zz) * HY + yh) * HX + xh) * 16),
                  X + v * Cin + g * CG + c8 * 8, in ? 16u : 0u);
         }
-        load_weights(g, 0, issued % NSTAGE);
         cp_commit();
-        for (int t = 0; t < 27; ++t) {
-            const int stage = issued % NSTAGE;
-            cp_wait_all();                          // this thread's copies of tap t (and halo)
-            fence_proxy_async();                    // visible to the tensor core's async proxy
-            __syncthreads();
-            if (s_fail) break;
-            if (tid == 0) {
+        cp_wait_all();
+        fence_proxy_async();
+        __syncthreads();
+        if (s_fail) break;
+        if (tid == 0) {
+            // the rest of the group's slabs, each as soon as its stage frees
+            for (; next < T0 + 27 && !s_fail; ++next) produce(next);
+        } else if (tid == 32) {
+            for (int t = 0; t < 27 && !s_fail; ++t) {
+                const int T = T0 + t, s = T % NSTAGE;
+                if (!mbar_wait(smem_u32(&full[s]), (unsigned)((T / NSTAGE) & 1))) {
+                    s_fail = 1;
+                    break;
+                }
+                s_consumed = T + 1;
                 fence_after();
                 const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
                 const unsigned a0 = halo_s + (unsigned)(((dz * HY + dy) * HX + dx) * 16);
-                const unsigned b0 = wst_s + stage * (unsigned)wstage_bytes;
+                const unsigned b0 = wst_s + (unsigned)s * slab;
                 for (int ks = 0; ks < CG / 16; ++ks) {
                     const uint64_t ad = smem_desc(a0 + 2u * ks * lbo_a, lbo_a, sbo_a);
                     const uint64_t bd = smem_desc(b0 + 2u * ks * lbo_b, lbo_b, sbo_b);
-                    mma_bf16(tmem, ad, bd, idesc, (g > 0 || t > 0 || ks > 0) ? 1u : 0u);
+                    mma_bf16(tmem, ad, bd, idesc, (T > 0 || ks > 0) ? 1u : 0u);
                 }
-                mma_commit(smem_u32(&bars[stage]));
-            }
-            ++issued;
-            // the next tap's weights go to the other stage once the MMAs that
-            // last read it (batch issued - NSTAGE) are done
-            if (t + 1 < 27) {
-                if (issued >= NSTAGE) wait_batch(issued - NSTAGE);
-                __syncthreads();
-                if (s_fail) break;
-                load_weights(g, t + 1, issued % NSTAGE);
-                cp_commit();
+                mma_commit(smem_u32(&empty[s]));
             }
         }
-        if (s_fail) break;
+    }
+    // every MMA is done once the last batch's commit completes (a second
+    // bounded wait after a failure, before the tensor memory is freed)
+    if (tid == 32 && total > 0) {
+        const int T = total - 1;
+        if (!mbar_wait(smem_u32(&empty[T % NSTAGE]), (unsigned)((T / NSTAGE) & 1))) {
+            s_fail = 1;
+            mbar_wait(smem_u32(&empty[T % NSTAGE]), (unsigned)((T / NSTAGE) & 1));
+        }
     }
     cp_wait_all();
-    // every MMA is done once the last batch's barrier completes (a second
-    // bounded wait after a timeout, before the tensor memory is freed)
-    if (issued > 0 && tid == 0) {
-        const int T = issued - 1;
-        if (!mbar_wait(smem_u32(&bars[T % NSTAGE]), (unsigned)((T / NSTAGE) & 1))) s_fail = 1;
-    }
     __syncthreads();
-    const bool failed = s_fail != 0;
+    // after a failure, the weight copies still in flight land before the
+    // block leaves (bounded)
+    if (tid == 0 && s_fail)
+        for (int T = s_consumed; T < next; ++T) mbar_wait(smem_u32(&full[T % NSTAGE]), (unsigned)((T / NSTAGE) & 1));
+    __syncthreads();
     fence_after();
+    const bool failed = s_fail != 0;
     if (failed) {
-        atomicCAS(&g_tc_error, 0u, 1u);
+        if (tid == 0) atomicCAS(&g_tc_error, 0u, 1u);
     } else {
         // epilogue: lane m of the accumulator is output voxel m of the tile
         const int m = warp * 32 + lane;
@@ -302,27 +332,172 @@ __global__ void __launch_bounds__(THREADS) conv3_tc_kernel(const bf16* __restric
                      : "memory");
 }
 
-// Wk[tap][co][ci] = W[tap][ci][co] (forward), or W[26 - tap][co][ci] with
-// the roles of ci and co swapped (the data gradient's conv: input channels
-// co, output channels ci): Wk[tap][ci][co] = W[26 - tap][ci][co].
-__global__ void kmajor_kernel(const bf16* __restrict__ W, bf16* __restrict__ Wk, int Cin, int Cout,
+// ---------------------------------------------------------------------------
+// Weight gradient on the tensor cores: dW[tap][ci][co] = sum_v X[v + tap][ci]
+// G[v][co].  Per tap a GEMM D[co][ci] (M = output channels, zero-padded to
+// 128; N = a group of at most 64 input channels; K = voxels).  Both operands
+// are channels-last in memory, so both enter the MMA MN-major: 16-byte rows
+// of 8 channels, one per voxel.  A block loops over tiles of 128 voxels (the
+// forward kernel's 16 x 8 tiles) and keeps one accumulator per tap of its
+// tap group in tensor memory (256 columns: 4 taps of 64 channels, 8 of 32);
+// per tile it stages the output-gradient tile G [co/8][128 voxels] and the
+// input halo (as in the forward kernel), and each tap's B operand is the halo
+// seen through its own descriptor.  At the end the accumulators are added
+// into dW (FP32 atomics, dW zeroed by the caller).
+// MN-major no-swizzle layout: core matrices of 8 K-rows x 16 bytes; the
+// descriptor's LBO is the stride between core matrices along K and its SBO
+// the stride along M (N).
+constexpr int WG_TMEM = 256;
+
+template <int CG>
+__global__ void __launch_bounds__(THREADS) conv3_wgrad_tc_kernel(const bf16* __restrict__ X, int Cin,
+                                                                 const bf16* __restrict__ G, int Cout,
+                                                                 float* __restrict__ dW, Vol vol,
+                                                                 int n_tiles) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int CG8 = CG / 8;
+    constexpr int TAPS = WG_TMEM / CG;             // accumulators per block
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* gs = smem;                      // [16][128] x 16 B (co blocks x voxels)
+    unsigned char* halo = smem + 16 * 128 * 16;    // [CG/8][3][18][10] x 16 B
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(halo + (size_t)HALO_VOX * CG * 2);
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(bar + 1);
+    __shared__ int s_fail;
+    const unsigned gs_s = smem_u32(gs), halo_s = smem_u32(halo);
+    const int Cout8 = Cout / 8;
+    const int tap0 = blockIdx.y * TAPS;
+    const int ntap = min(TAPS, 27 - tap0);
+    const int g = blockIdx.z;                      // input channel group
+
+    // the padding rows of G (output channels Cout .. 127) stay zero
+    for (int i = tid; i < (16 - Cout8) * 128; i += THREADS)
+        *reinterpret_cast<uint4*>(gs + (size_t)(Cout8 * 128 + i) * 16) = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        s_fail = 0;
+        mbar_init(smem_u32(bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(WG_TMEM)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = *tmem_slot;
+    // both operands MN-major (bits 15, 16), M = 128, N = CG
+    const uint32_t idesc = instr_desc(CG) | (1u << 15) | (1u << 16);
+    const int tiles_x = vol.w / TILE_X, tiles_y = vol.h / TILE_Y;
+    int done = 0;                                  // tiles whose MMAs were committed
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        int b = tile;
+        const int tx = b % tiles_x; b /= tiles_x;
+        const int ty = b % tiles_y; b /= tiles_y;
+        const int z0 = b % vol.d;
+        const int n0 = b / vol.d;
+        const int x0 = tx * TILE_X, y0 = ty * TILE_Y;
+        // the previous tile's MMAs read the shared tiles
+        if (done > 0 && tid == 0 && !s_fail &&
+            !mbar_wait(smem_u32(bar), (unsigned)((done - 1) & 1)))
+            s_fail = 1;
+        __syncthreads();
+        if (s_fail) break;
+        for (int i = tid; i < 128 * Cout8; i += THREADS) {
+            const int v = i / Cout8, c8 = i - v * Cout8;
+            const long long gv = (((long long)n0 * vol.d + z0) * vol.h + y0 + v / TILE_X) * vol.w + x0 + v % TILE_X;
+            cp16(gs_s + (unsigned)((c8 * 128 + v) * 16), G + gv * Cout + c8 * 8, 16u);
+        }
+        for (int i = tid; i < HALO_VOX * CG8; i += THREADS) {
+            const int hv = i / CG8, c8 = i - hv * CG8;
+            const int xh = hv % HX, yh = (hv / HX) % HY, zz = hv / (HX * HY);
+            const int z = z0 + zz - 1;
+            int y = y0 + yh - 1, x = x0 + xh - 1;
+            y = y < 0 ? y + vol.h : (y >= vol.h ? y - vol.h : y);
+            x = x < 0 ? x + vol.w : (x >= vol.w ? x - vol.w : x);
+            const bool in = z >= 0 && z < vol.d;
+            const long long v = (((long long)n0 * vol.d + (in ? z : 0)) * vol.h + y) * vol.w + x;
+            cp16(halo_s + (unsigned)((((c8 * HZ + zz) * HY + yh) * HX + xh) * 16),
+                 X + v * Cin + g * CG + c8 * 8, in ? 16u : 0u);
+        }
+        cp_commit();
+        cp_wait_all();
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            for (int k = 0; k < ntap; ++k) {
+                const int t = tap0 + k;
+                const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+                for (int ks = 0; ks < 128 / 16; ++ks) {
+                    // K step ks: voxel rows 2ks and 2ks + 1 of the tile
+                    const uint64_t ad = smem_desc(gs_s + 2u * ks * 128u, 128u, 128u * 16u);
+                    const uint64_t bd = smem_desc(
+                        halo_s + (unsigned)(((dz * HY + dy + 2 * ks) * HX + dx) * 16), HX * 16, HALO_VOX * 16);
+                    mma_bf16(tmem + (unsigned)(k * CG), ad, bd, idesc, (done > 0 || ks > 0) ? 1u : 0u);
+                }
+            }
+            mma_commit(smem_u32(bar));
+        }
+        ++done;
+    }
+    if (done > 0 && tid == 0 && !mbar_wait(smem_u32(bar), (unsigned)((done - 1) & 1))) s_fail = 1;
+    if (done > 0 && tid == 0 && s_fail) mbar_wait(smem_u32(bar), (unsigned)((done - 1) & 1));
+    __syncthreads();
+    fence_after();
+    if (s_fail) {
+        atomicCAS(&g_tc_error, 0u, 1u);
+    } else if (done > 0) {
+        // lane = output channel co (warp w: 32w .. 32w + 31), columns = ci
+        const int co = warp * 32 + lane;
+        const unsigned trow = tmem + ((unsigned)(warp * 32) << 16);
+        for (int k = 0; k < ntap; ++k) {
+            const int t = tap0 + k;
+            for (int c0 = 0; c0 < CG; c0 += 16) {
+                float acc[16];
+                tmem_ld16(trow + (unsigned)(k * CG + c0), acc);
+                if (co < Cout) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        atomicAdd(dW + ((long long)t * Cin + g * CG + c0 + i) * Cout + co, acc[i]);
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(WG_TMEM)
+                     : "memory");
+}
+
+__host__ __device__ constexpr size_t wg_smem_bytes(int cg) {
+    return (size_t)16 * 128 * 16 + (size_t)HALO_VOX * cg * 2 + 64;
+}
+
+// Weight slabs for the forward kernel from W [27][cin][cout].  The conv that
+// uses them has input channels K and output channels N: K = cin, N = cout
+// for the forward conv (flip 0); K = cout, N = cin with the taps reversed for
+// the data gradient's conv (flip 1).  Slab (tap, group g) holds the group's
+// CG = cg_for(K) input channels as [CG/8][N][8]: element
+// (k8, n, e) = weight of input channel g CG + 8 k8 + e, output channel n.
+__global__ void kmajor_kernel(const bf16* __restrict__ W, bf16* __restrict__ Wu, int Cin, int Cout,
                               int flip) {
-    const long long total = 27LL * Cin * Cout;
+    const int K = flip ? Cout : Cin, N = flip ? Cin : Cout;
+    const int CG = cg_for(K), G = K / CG;
+    const long long total = 27LL * K * N;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
-        if (!flip) {
-            const int ci = (int)(i % Cin);
-            const long long r = i / Cin;
-            const int co = (int)(r % Cout);
-            const int tap = (int)(r / Cout);
-            Wk[i] = W[((long long)tap * Cin + ci) * Cout + co];
-        } else {
-            const int co = (int)(i % Cout);
-            const long long r = i / Cout;
-            const int ci = (int)(r % Cin);
-            const int tap = (int)(r / Cin);
-            Wk[i] = W[((long long)(26 - tap) * Cin + ci) * Cout + co];
-        }
+        const int e = (int)(i & 7);
+        long long r = i >> 3;
+        const int n = (int)(r % N); r /= N;
+        const int k8 = (int)(r % (CG / 8)); r /= CG / 8;
+        const int g = (int)(r % G);
+        const int tap = (int)(r / G);
+        const int k = g * CG + 8 * k8 + e;                 // input channel of the conv
+        Wu[i] = flip ? W[((long long)(26 - tap) * Cin + n) * Cout + k]
+                     : W[((long long)tap * Cin + k) * Cout + n];
     }
 }
 
@@ -340,19 +515,18 @@ int lbm_nn_conv3d_tc_supported(int cin, int cout, int n, int d, int h, int w) {
     if (cin < 16 || cin % 16 || cout < 16 || cout % 16 || cout > 256) return 0;
     if (n < 1 || d < 1 || h < TILE_Y || w < TILE_X || h % TILE_Y || w % TILE_X) return 0;
     if ((long long)n * d * h * w >= (1LL << 40)) return 0;
-    const int cg = cin <= 64 ? cin : (cin % 64 == 0 ? 64 : (cin % 32 == 0 ? 32 : 16));
-    return tc_smem_padded(cg, cout) + 256 <= 227 * 1024 ? 1 : 0;   // static shared memory too
+    return tc_smem_bytes(cg_for(cin), cout) + 256 <= 227 * 1024 ? 1 : 0;   // static shared memory too
 }
 
 lbm_status lbm_nn_conv3d_tc(const void* x, int cin, const void* wk, const float* bias, void* y, int cout,
                             int n, int d, int h, int wdt, int relu, int out_f32, void* stream) {
     if (!x || !wk || !y || !lbm_nn_conv3d_tc_supported(cin, cout, n, d, h, wdt)) return LBM_ERR_INVALID_ARG;
-    const int cg = cin <= 64 ? cin : (cin % 64 == 0 ? 64 : (cin % 32 == 0 ? 32 : 16));
-    const size_t smem = tc_smem_padded(cg, cout);
+    const int cg = cg_for(cin);
+    const int cols = tmem_cols_for(cout);
+    const size_t smem = tmem_safe_smem(tc_smem_bytes(cg, cout), cols);
     const Vol vol{n, d, h, wdt};
     const long long blocks = (long long)(wdt / TILE_X) * (h / TILE_Y) * d * n;
     if (blocks > 0x7fffffffLL) return LBM_ERR_INVALID_ARG;
-    const int cols = tmem_cols_for(cout);
     cudaStream_t st = (cudaStream_t)stream;
     const bf16* X = static_cast<const bf16*>(x);
     const bf16* W = static_cast<const bf16*>(wk);
@@ -365,6 +539,45 @@ lbm_status lbm_nn_conv3d_tc(const void* x, int cin, const void* wk, const float*
     else if (!relu && !out_f32) go(conv3_tc_kernel<false, false>);
     else if (relu) go(conv3_tc_kernel<true, true>);
     else go(conv3_tc_kernel<false, true>);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+int lbm_nn_conv3d_wgrad_tc_supported(int cin, int cout, int n, int d, int h, int w) {
+    if (cin < 16 || cin % 16 || cout < 8 || cout % 8 || cout > 128) return 0;
+    if (n < 1 || d < 1 || h < TILE_Y || w < TILE_X || h % TILE_Y || w % TILE_X) return 0;
+    return (long long)n * d * h * w < (1LL << 40) ? 1 : 0;
+}
+
+lbm_status lbm_nn_conv3d_wgrad_tc(const void* x, int cin, const void* g, int cout, float* dw, int n, int d,
+                                  int h, int wdt, void* stream) {
+    if (!x || !g || !dw || !lbm_nn_conv3d_wgrad_tc_supported(cin, cout, n, d, h, wdt)) return LBM_ERR_INVALID_ARG;
+    const int cg = cin % 64 == 0 ? 64 : (cin % 32 == 0 ? 32 : 16);
+    const Vol vol{n, d, h, wdt};
+    const long long tiles = (long long)(wdt / TILE_X) * (h / TILE_Y) * d * n;
+    if (tiles > 0x7fffffffLL) return LBM_ERR_INVALID_ARG;
+    const int taps_per_block = WG_TMEM / cg;
+    const int tap_groups = (27 + taps_per_block - 1) / taps_per_block;
+    const int ci_groups = cin / cg;
+    int n_sm = 152;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, 0);
+    // about two blocks per SM in all, each looping over its share of the tiles
+    long long chunks = (2LL * n_sm + tap_groups * ci_groups - 1) / (tap_groups * ci_groups);
+    if (chunks > tiles) chunks = tiles;
+    if (chunks < 1) chunks = 1;
+    const dim3 grid((unsigned)chunks, (unsigned)tap_groups, (unsigned)ci_groups);
+    const size_t smem = tmem_safe_smem(wg_smem_bytes(cg), WG_TMEM);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bf16* X = static_cast<const bf16*>(x);
+    const bf16* G = static_cast<const bf16*>(g);
+    cudaError_t e = cudaSuccess;
+    auto go = [&](auto kern) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) kern<<<grid, THREADS, smem, st>>>(X, cin, G, cout, dw, vol, (int)tiles);
+    };
+    if (cg == 64) go(conv3_wgrad_tc_kernel<64>);
+    else if (cg == 32) go(conv3_wgrad_tc_kernel<32>);
+    else go(conv3_wgrad_tc_kernel<16>);
     if (e == cudaSuccess) e = cudaGetLastError();
     return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }

@@ -278,8 +278,12 @@ class WarmNet:
         self.gW[l].zero_()
         self.gb[l].zero_()
         s = self._stream()
-        self._ok(lbm.lbm_nn_conv3d_wgrad(x_in.data_ptr(), cin, g_out.data_ptr(), cout,
-                                         self.gW[l].data_ptr(), n, d, h, w, 3, s), "wgrad")
+        if self.use_tc and lbm.lbm_nn_conv3d_wgrad_tc_supported(cin, cout, n, d, h, w) == 1:
+            self._ok(lbm.lbm_nn_conv3d_wgrad_tc(x_in.data_ptr(), cin, g_out.data_ptr(), cout,
+                                                self.gW[l].data_ptr(), n, d, h, w, s), "wgrad (tensor cores)")
+        else:
+            self._ok(lbm.lbm_nn_conv3d_wgrad(x_in.data_ptr(), cin, g_out.data_ptr(), cout,
+                                             self.gW[l].data_ptr(), n, d, h, w, 3, s), "wgrad")
         self._ok(lbm.lbm_nn_bias_grad(g_out.data_ptr(), cout, V, self.gb[l].data_ptr(), s), "bgrad")
         if not need_dx:
             return None

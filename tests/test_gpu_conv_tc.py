@@ -153,3 +153,31 @@ def test_network_on_tensor_cores_matches_mma_sync(torch):
     assert l1 == pytest.approx(l0, rel=1e-2)
     cos = float(g1 @ g0 / (np.linalg.norm(g1) * np.linalg.norm(g0)))
     assert cos >= 0.999, cos
+
+
+@pytest.mark.parametrize("cin,cout,vol", [(16, 32, (1, 3, 16, 8)), (32, 64, (2, 2, 16, 16)),
+                                          (64, 64, (1, 4, 32, 8)), (96, 32, (1, 2, 16, 8)),
+                                          (128, 128, (1, 2, 16, 16)), (192, 64, (1, 2, 16, 8))])
+def test_tc_weight_gradient_matches_reference(torch, cin, cout, vol):
+    """dW of the tensor-core kernel (both operands MN-major, one accumulator
+    per tap in tensor memory) against reverse-mode differentiation of the
+    FP64 reference conv; FP32 accumulation, bound 1e-4 of the scale as for
+    the mma.sync weight gradient."""
+    import torch as T
+    n, d, h, w = vol
+    assert lbm.lbm_nn_conv3d_wgrad_tc_supported(cin, cout, n, d, h, w) == 1
+    rng = np.random.default_rng(7 * cin + cout)
+    x = _bf16_round(rng.standard_normal((n, d, h, w, cin)))
+    g = _bf16_round(rng.standard_normal((n, d, h, w, cout)))
+    W = T.zeros((cout, cin, 3, 3, 3), dtype=T.float64, requires_grad=True)
+    y = R.conv3(T.from_numpy(np.moveaxis(x, -1, 1)), W, None)
+    (y * T.from_numpy(np.moveaxis(g, -1, 1))).sum().backward()
+    ref = np.transpose(W.grad.numpy().reshape(cout, cin, 27), (2, 1, 0))
+    xg = torch.from_numpy(x.reshape(-1, cin)).to(torch.bfloat16).to("cuda")
+    gg = torch.from_numpy(g.reshape(-1, cout)).to(torch.bfloat16).to("cuda")
+    dw = torch.zeros((27, cin, cout), dtype=torch.float32, device="cuda")
+    assert lbm.lbm_nn_conv3d_wgrad_tc(xg.data_ptr(), cin, gg.data_ptr(), cout, dw.data_ptr(),
+                                      n, d, h, w, None) == lbm.LBM_OK
+    torch.cuda.synchronize()
+    assert lbm.lbm_nn_tc_error(True) == 0
+    assert np.max(np.abs(dw.cpu().numpy() - ref)) <= 1e-4 * np.max(np.abs(ref))
