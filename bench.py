@@ -85,6 +85,14 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def bf16_sustained_tflops():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops_sustained"]), "measured"
+    except Exception:
+        return 1700.0, "fallback"
+
+
 class ClockSampler:
     """Samples nvidia-smi clocks and throttle reasons during the timed region."""
 
@@ -490,6 +498,100 @@ def combined_form(lbm, I, stream, rel=1e-4, budget=40_000):
     return out
 
 
+def warm_start_config5(lbm, I, stream, seeds=(5000, 5001, 5002, 5003), tol=1e-8):
+    """Learned warm start on 128x128x256 braided cells of the warm-start
+    distribution (seeds 5000.., z axis, periodic laterals, FP32): iterations
+    and device time to R_T <= tol from the linear profile and from the
+    network's prediction (inference time included), and the k_eff of both."""
+    import torch
+    from paper_1503_08718_gb300 import warmstart as W
+
+    if not os.path.exists(WARM_WEIGHTS):
+        return {"unavailable": "no trained warm-start weights"}
+    net = W.WarmNet()
+    net.load(WARM_WEIGHTS)
+    rows = []
+    for s in seeds:
+        g, phi = I.warm_cell_params(s)
+        lam = I.braid_tensors(g)
+        with lbm.Solver(128, 128, 256) as S:
+            S.set_geometry_braid(math.radians(g), I.braid_anchors(128, 128, s, n_max=512), phi)
+            S.set_tensors(lam)
+            ph = S.geometry()
+            o = S.opts(tol=tol, max_iters=3_000_000)
+            o.stream = int(stream.cuda_stream)
+            S.start(2, 0, o)
+            lin = S.run(allow=())
+            net.predict(ph, lam, as_tensor=True)              # warm-up (module load)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            T0 = net.predict(ph, lam, as_tensor=True)
+            e1.record()
+            torch.cuda.synchronize()
+            inf_ms = e0.elapsed_time(e1)
+            T0h = np.ascontiguousarray(T0.cpu().numpy(), dtype=np.float32)
+            o.t_init = T0h.ctypes.data_as(lbm.ctypes.POINTER(lbm.ctypes.c_float))
+            S.start(2, 0, o)
+            warm = S.run(allow=())
+            rows.append({"seed": s, "g_deg": g, "phi": phi,
+                         "linear": {"iters": int(lin.iters), "ms": lin.elapsed_ms, "k_eff": lin.k_eff},
+                         "warm": {"iters": int(warm.iters), "ms": warm.elapsed_ms + inf_ms,
+                                  "inference_ms": inf_ms, "k_eff": warm.k_eff},
+                         "iters_saved": 1.0 - warm.iters / lin.iters,
+                         "k_rel_diff": warm.k_eff / lin.k_eff - 1.0})
+    return {"workload": "braids 128x128x256 (warm-start distribution), z axis, periodic, FP32, "
+                        "to R_T <= %g" % tol, "cells": rows,
+            "iters_saved_mean": float(np.mean([r["iters_saved"] for r in rows])),
+            "time_ratio_mean": float(np.mean([r["warm"]["ms"] / r["linear"]["ms"] for r in rows]))}
+
+
+def conv_throughput(lbm, sustained_tflops, n=4, d=64, h=64, w=64, cin=64, cout=64, reps=10):
+    """The warm-start network's 3x3x3 convolution at 4 cells of 64^3 with 64
+    input and 64 output channels: the tcgen05 forward and weight-gradient
+    kernels against the mma.sync ones (CUDA events), TFLOP/s and the fraction
+    of the sustained BF16 peak."""
+    import torch
+    V = n * d * h * w
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    x = torch.randn(V, cin, device="cuda", generator=g).to(torch.bfloat16)
+    gy = torch.randn(V, cout, device="cuda", generator=g).to(torch.bfloat16)
+    W = (torch.randn(27, cin, cout, device="cuda", generator=g) / math.sqrt(27 * cin)).to(torch.bfloat16)
+    b = torch.zeros(cout, device="cuda")
+    y = torch.empty(V, cout, dtype=torch.bfloat16, device="cuda")
+    dw = torch.zeros(27, cin, cout, device="cuda")
+    wk = torch.empty(27 * cin * cout, dtype=torch.bfloat16, device="cuda")
+    lbm.lbm_nn_weights_kmajor(W.data_ptr(), wk.data_ptr(), cin, cout, 0, None)
+    flop = 2.0 * V * 27 * cin * cout
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        return {"ms": ms, "tflops": flop / ms / 1e9, "frac_sustained": flop / ms / 1e9 / sustained_tflops}
+
+    out = {"shape": f"{n} x {d}x{h}x{w}, {cin} -> {cout} channels, 3x3x3", "gflop": flop / 1e9,
+           "peak_sustained_tflops": sustained_tflops}
+    out["fwd_tcgen05"] = timed(lambda: lbm.lbm_nn_conv3d_tc(x.data_ptr(), cin, wk.data_ptr(), b.data_ptr(),
+                                                             y.data_ptr(), cout, n, d, h, w, 1, 0, None))
+    out["fwd_mma_sync"] = timed(lambda: lbm.lbm_nn_conv3d(x.data_ptr(), cin, W.data_ptr(), b.data_ptr(),
+                                                           y.data_ptr(), cout, n, d, h, w, 3, 1, 0, None))
+    out["wgrad_tcgen05"] = timed(lambda: lbm.lbm_nn_conv3d_wgrad_tc(x.data_ptr(), cin, gy.data_ptr(), cout,
+                                                                     dw.data_ptr(), n, d, h, w, None))
+    out["wgrad_mma_sync"] = timed(lambda: lbm.lbm_nn_conv3d_wgrad(x.data_ptr(), cin, gy.data_ptr(), cout,
+                                                                   dw.data_ptr(), n, d, h, w, 3, None))
+    out["tc_error"] = lbm.lbm_nn_tc_error(True)
+    return out
+
+
 def cpu_oracle_sample(seconds_target=15.0):
     """Times the FP64 oracle on the host cores on the same cell: a fixed
     number of iterations of the full 128x128x256 lattice."""
@@ -735,6 +837,10 @@ def run_ours(args):
         }
         extras["time_to_keff"] = time_to_keff(lbm, S, stream)
         extras["combined_form"] = combined_form(lbm, I, stream)
+        extras["configs"]["cfg5_warm_start"] = warm_start_config5(lbm, I, stream)
+        sus, sus_kind = bf16_sustained_tflops()
+        extras["warmnet_conv"] = conv_throughput(lbm, sus)
+        extras["warmnet_conv"]["peak_source"] = sus_kind
 
     # end to end through the public API with host buffers
     anchors = I.braid_anchors(NX, NY, SEED, n_max=NMAX)

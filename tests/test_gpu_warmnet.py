@@ -156,25 +156,58 @@ def test_training_reduces_the_loss(torch):
 
 
 def test_warm_start_saves_iterations(torch):
-    """Trained on solver outputs of seeded 64^3 braided cells, the network's
-    prediction starts held-out cells closer to their steady state: fewer
-    iterations to R_T <= 1e-8, the same converged k_eff."""
-    from paper_1503_08718_gb300.warmstart import WarmNet, generate_cells, train
-    ph, lams, temps, _ = generate_cells(range(160), n=64)
-    net = WarmNet(seed=2)
-    train(net, ph, lams, temps, epochs=20, batch=4)
-    ph_t, lams_t, _, _ = generate_cells(range(900, 903), n=64)
-    saved = []
-    for i in range(3):
+    """The trained network shipped with the package (2000 seeded 64^3 braided
+    cells, 30 epochs) on held-out cells of the same distribution whose
+    converged FP64 oracle value k* is stored: from its prediction the solve
+    reaches k_eff within 1e-4 of k* in at least 30 % fewer iterations on
+    average than from the linear profile (and on no cell more), and the
+    converged k_eff (R_T <= 1e-8) is the linear start's and within 1e-4 of k*:
+    the lattice Boltzmann fixed point decides the answer, the network only
+    the path to it."""
+    import hashlib
+    import json
+    import os
+    from paper_1503_08718_gb300.warmstart import WarmNet
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    weights = os.path.join(root, "paper_1503_08718_gb300", "weights", "warmnet_braid64.npz")
+    with open(os.path.join(root, "tests", "golden", "keff_reference.json")) as fh:
+        refs = json.load(fh)["cells"]
+    net = WarmNet()
+    net.load(weights)
+    saved, checked = [], 0
+    for seed in (7000, 7001, 7002):
+        ref = refs.get(f"warm64_{seed}")
+        if not ref or not ref.get("converged"):
+            continue
+        g, phi = I.warm_cell_params(seed)
+        lam = I.braid_tensors(g)
         S = lbm.Solver(64, 64, 64)
-        S.set_geometry(ph_t[i], 5)
-        S.set_tensors(lams_t[i])
+        S.set_geometry_braid(math.radians(g), I.braid_anchors(64, 64, seed, n_max=256), phi)
+        S.set_tensors(lam)
+        ph = S.geometry()
+        assert hashlib.sha256(ph.tobytes()).hexdigest() == ref["phase_sha256"]
+        k_star = ref["k_star"]
+
+        def iters_to_band(info_hist):
+            err = np.abs(info_hist[:, 1] / k_star - 1.0)
+            bad = np.nonzero(err > 1e-4)[0]
+            first = 0 if bad.size == 0 else int(bad[-1]) + 1
+            assert first < len(info_hist)
+            return int(info_hist[first, 0])
+
         base = S.solve(2, 0, S.opts(tol=1e-8, max_iters=2_000_000), allow=())
-        T0 = np.ascontiguousarray(net.predict(ph_t[i], lams_t[i]), dtype=np.float32)
+        n_lin = iters_to_band(S.history())
+        T0 = np.ascontiguousarray(net.predict(ph, lam), dtype=np.float32)
         o = S.opts(tol=1e-8, max_iters=2_000_000)
         o.t_init = T0.ctypes.data_as(lbm.ctypes.POINTER(lbm.ctypes.c_float))
         warm = S.solve(2, 0, o, allow=())
-        assert warm.k_eff == pytest.approx(base.k_eff, rel=2e-4)
-        saved.append(1.0 - warm.iters / base.iters)
-    # a few hundred training cells already take 5-20 % of the iterations off
-    assert np.mean(saved) > 0.03, saved
+        n_warm = iters_to_band(S.history())
+        assert warm.k_eff == pytest.approx(base.k_eff, rel=2e-5)
+        assert warm.k_eff == pytest.approx(k_star, rel=1e-4)
+        assert n_warm <= n_lin
+        saved.append(1.0 - n_warm / n_lin)
+        checked += 1
+        S.close()
+    assert checked >= 2, "fewer than two held-out cells have a stored oracle k*"
+    assert np.mean(saved) >= 0.30, saved
