@@ -384,6 +384,14 @@ lbm_status lbm_nn_conv3d_wgrad_tc(const void* x, int cin, const void* g, int cou
 /* 1 if lbm_nn_conv3d_wgrad_tc takes these sizes, else 0.  Host-only. */
 int lbm_nn_conv3d_wgrad_tc_supported(int cin, int cout, int n, int d, int h, int w);
 
+/* lbm_nn_conv3d_tc with an explicit launch configuration: tz output planes
+ * per block (1 or 2: the planes share every weight slab) and ns weight stages
+ * (2, 4 or 6); 0 lets the library choose, as lbm_nn_conv3d_tc does.
+ * LBM_ERR_INVALID_ARG if the sizes or the configuration do not fit (d must
+ * be a multiple of tz; tz accumulators must fit 256 tensor-memory columns). */
+lbm_status lbm_nn_conv3d_tc_cfg(const void* x, int cin, const void* wk, const float* bias, void* y, int cout,
+                                int n, int d, int h, int wdt, int relu, int out_f32, int tz, int ns, void* stream);
+
 /* 1 if lbm_nn_conv3d_tc takes these sizes, else 0.  Host-only. */
 int lbm_nn_conv3d_tc_supported(int cin, int cout, int n, int d, int h, int w);
 

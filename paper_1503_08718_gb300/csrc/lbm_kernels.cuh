@@ -624,6 +624,7 @@ constexpr int F2_MAX_THREADS = 640;
 // (runtime row width); the launch bounds keep every variant at or below 96
 // registers so that two 320-thread blocks fit an SM.
 __host__ __device__ constexpr int f2_bound_threads(int nxc) { return nxc == 128 ? 320 : F2_MAX_THREADS; }
+__host__ __device__ constexpr int f2_fixed_fy(int nxc) { return 8; }   // tile rows of the tuned variants
 __host__ __device__ constexpr int f2_bound_blocks(int nxc) { return nxc == 128 ? 2 : 1; }
 
 // A ring plane keeps, per population, only the rows the second step reads:
@@ -684,8 +685,11 @@ __device__ __forceinline__ float* fused2_tables(const StepArgs& a, int ring_floa
 // The caller has loaded the B tables (fused2_tables) but not yet synchronised.
 template <bool PERIODIC, int NXC>
 __device__ __forceinline__ void fused2_body(const StepArgs& a, float* fn, const float4* s_sa,
-                                            const float2* s_sc, const int FY, const int by, const int bz,
+                                            const float2* s_sc, const int fy_arg, const int by, const int bz,
                                             const int zchunk, const int flip) {
+    // the tuned row widths have a fixed tile height: every ring offset below
+    // is then a compile-time constant
+    const int FY = NXC ? f2_fixed_fy(NXC) : fy_arg;
     const int NXB = NXC ? NXC : a.pitch;           // nodes per row (= nx = pitch)
     const int nq = NXB >> 2;                       // threads per row
     // rows of whole warps: every branch on the row is warp-uniform, so a
@@ -917,8 +921,8 @@ F2Plan f2_plan(int nx, int ny, int nz, int n_phases, int n_sm, int smem_max, boo
     if (nx % 4 != 0 || nx < 4 || ny < 1 || nz < 1) return best;
     const int nq = nx / 4;
     const int nxc = nx == 128 ? 128 : (nx == 256 ? 256 : 0);
-    const int fy_lo = nxc ? 8 : 1;
-    const int fy_hi = nxc ? 8 : F2_MAX_THREADS / nq - 2;
+    const int fy_lo = nxc ? f2_fixed_fy(nxc) : 1;
+    const int fy_hi = nxc ? f2_fixed_fy(nxc) : F2_MAX_THREADS / nq - 2;
     for (int fy = fy_lo; fy <= fy_hi; ++fy) {
         const int threads = (fy + 2) * nq;
         if (threads > f2_bound_threads(nxc)) break;

@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "lbm.h"
 
@@ -37,7 +38,6 @@ constexpr int TILE_Y = 16, TILE_X = 8;             // 128 output voxels per bloc
 constexpr int HZ = 3, HY = TILE_Y + 2, HX = TILE_X + 2;
 constexpr int HALO_VOX = HZ * HY * HX;             // 540
 constexpr int THREADS = 128;
-constexpr int NSTAGE = 2;                          // weight stages
 constexpr unsigned kSpinLimit = 1u << 22;          // bounded mbarrier waits
 
 __device__ unsigned int g_tc_error = 0u;           // first error code of any block
@@ -130,11 +130,11 @@ __host__ __device__ constexpr int cg_for(int cin) {
     return cin <= 64 ? cin : (cin % 64 == 0 ? 64 : (cin % 32 == 0 ? 32 : 16));
 }
 
-// Shared memory of the forward kernel: halo [cg/8][3][18][10] x 16 B, then
-// NSTAGE weight stages [cg/8][N] x 16 B, then the mbarriers and the TMEM
-// address.
-__host__ __device__ constexpr size_t tc_smem_bytes(int cg, int n) {
-    return (size_t)HALO_VOX * cg * 2 + (size_t)NSTAGE * n * cg * 2 + 128;
+// Shared memory of the forward kernel for tz output planes per block and ns
+// weight stages: halo [cg/8][tz + 2][18][10] x 16 B, then the stages
+// [cg/8][N] x 16 B each, then the mbarriers and the TMEM address.
+__host__ __device__ constexpr size_t tc_smem_bytes(int cg, int n, int tz, int ns) {
+    return (size_t)(tz + 2) * HY * HX * cg * 2 + (size_t)ns * n * cg * 2 + 256;
 }
 
 // Blocks an SM can hold are bounded by shared memory; make sure they never
@@ -146,7 +146,9 @@ size_t tmem_safe_smem(size_t smem, int cols) {
     return smem > floor ? smem : floor;
 }
 
-// Forward kernel, one tile per block.  Roles: thread 0 streams the weight
+// Forward kernel, TZ tiles per block (TZ consecutive z planes of the same 16
+// x 8 rows: TZ accumulators of N columns that share every weight slab).
+// Roles: thread 0 streams the weight
 // slabs of the taps (one cp.async.bulk per slab into a free stage, completion
 // counted on the stage's `full` mbarrier); thread 32 issues each tap's MMAs
 // once its slab is in and commits them to the stage's `empty` mbarrier, which
@@ -154,7 +156,7 @@ size_t tmem_safe_smem(size_t smem, int cols) {
 // group (cp.async) and run the epilogue.  The weights arrive pre-arranged
 // (lbm_nn_weights_kmajor): slab (tap, group) is [cg/8][N][8] BF16, exactly
 // the stage's shared-memory image.
-template <bool RELU, bool OUT_F32>
+template <bool RELU, bool OUT_F32, int TZ, int NS>
 __global__ void __launch_bounds__(THREADS) conv3_tc_kernel(const bf16* __restrict__ X, int Cin, int CG,
                                                            const bf16* __restrict__ Wu,
                                                            const float* __restrict__ bias,
@@ -164,7 +166,10 @@ __global__ void __launch_bounds__(THREADS) conv3_tc_kernel(const bf16* __restric
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int CG8 = CG >> 3;
     unsigned char* halo = smem;
-    unsigned char* wst = smem + (size_t)HALO_VOX * CG * 2;
+    constexpr int NSTAGE = NS;
+    constexpr int PZ = TZ + 2;                      // halo planes
+    constexpr int PVOX = PZ * HY * HX;              // halo voxels
+    unsigned char* wst = smem + (size_t)PVOX * CG * 2;
     const unsigned slab = (unsigned)N * CG * 2;          // bytes of one weight slab
     unsigned long long* full = reinterpret_cast<unsigned long long*>(wst + NSTAGE * (size_t)slab);
     unsigned long long* empty = full + NSTAGE;
@@ -177,8 +182,9 @@ __global__ void __launch_bounds__(THREADS) conv3_tc_kernel(const bf16* __restric
     int b = blockIdx.x;
     const int tx = b % tiles_x; b /= tiles_x;
     const int ty = b % tiles_y; b /= tiles_y;
-    const int z0 = b % vol.d;
-    const int n0 = b / vol.d;
+    const int zt = vol.d / TZ;                      // z tiles per cell
+    const int z0 = (b % zt) * TZ;
+    const int n0 = b / zt;
     const int x0 = tx * TILE_X, y0 = ty * TILE_Y;
     const int ngroups = Cin / CG;
     const int total = 27 * ngroups;                 // weight slabs / MMA batches, group-major
@@ -203,7 +209,7 @@ __global__ void __launch_bounds__(THREADS) conv3_tc_kernel(const bf16* __restric
     fence_after();
     const unsigned tmem = *tmem_slot;
     const uint32_t idesc = instr_desc(N);
-    const unsigned lbo_a = HALO_VOX * 16, sbo_a = HX * 16;
+    const unsigned lbo_a = PVOX * 16, sbo_a = HX * 16;
     const unsigned lbo_b = (unsigned)N * 16, sbo_b = 128;
 
     // producer: slab T into stage T % NSTAGE once the MMAs that last read it
@@ -234,7 +240,7 @@ __global__ void __launch_bounds__(THREADS) conv3_tc_kernel(const bf16* __restric
         // the first slabs of the group start while the halo loads
         if (tid == 0)
             for (; next < T0 + NSTAGE && next < total && !s_fail; ++next) produce(next);
-        for (int i = tid; i < HALO_VOX * CG8; i += THREADS) {
+        for (int i = tid; i < PVOX * CG8; i += THREADS) {
             const int hv = i / CG8, c8 = i - hv * CG8;
             const int xh = hv % HX, yh = (hv / HX) % HY, zz = hv / (HX * HY);
             const int z = z0 + zz - 1;
@@ -243,7 +249,7 @@ __global__ void __launch_bounds__(THREADS) conv3_tc_kernel(const bf16* __restric
             x = x < 0 ? x + vol.w : (x >= vol.w ? x - vol.w : x);
             const bool in = z >= 0 && z < vol.d;
             const long long v = (((long long)n0 * vol.d + (in ? z : 0)) * vol.h + y) * vol.w + x;
-            cp16(halo_s + (unsigned)((((c8 * HZ + zz) * HY + yh) * HX + xh) * 16),
+            cp16(halo_s + (unsigned)((((c8 * PZ + zz) * HY + yh) * HX + xh) * 16),
                  X + v * Cin + g * CG + c8 * 8, in ? 16u : 0u);
         }
         cp_commit();
@@ -264,12 +270,15 @@ __global__ void __launch_bounds__(THREADS) conv3_tc_kernel(const bf16* __restric
                 s_consumed = T + 1;
                 fence_after();
                 const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-                const unsigned a0 = halo_s + (unsigned)(((dz * HY + dy) * HX + dx) * 16);
                 const unsigned b0 = wst_s + (unsigned)s * slab;
-                for (int ks = 0; ks < CG / 16; ++ks) {
-                    const uint64_t ad = smem_desc(a0 + 2u * ks * lbo_a, lbo_a, sbo_a);
-                    const uint64_t bd = smem_desc(b0 + 2u * ks * lbo_b, lbo_b, sbo_b);
-                    mma_bf16(tmem, ad, bd, idesc, (T > 0 || ks > 0) ? 1u : 0u);
+#pragma unroll
+                for (int tz = 0; tz < TZ; ++tz) {
+                    const unsigned a0 = halo_s + (unsigned)((((tz + dz) * HY + dy) * HX + dx) * 16);
+                    for (int ks = 0; ks < CG / 16; ++ks) {
+                        const uint64_t ad = smem_desc(a0 + 2u * ks * lbo_a, lbo_a, sbo_a);
+                        const uint64_t bd = smem_desc(b0 + 2u * ks * lbo_b, lbo_b, sbo_b);
+                        mma_bf16(tmem + (unsigned)(tz * N), ad, bd, idesc, (T > 0 || ks > 0) ? 1u : 0u);
+                    }
                 }
                 mma_commit(smem_u32(&empty[s]));
             }
@@ -296,12 +305,13 @@ __global__ void __launch_bounds__(THREADS) conv3_tc_kernel(const bf16* __restric
     if (failed) {
         if (tid == 0) atomicCAS(&g_tc_error, 0u, 1u);
     } else {
-        // epilogue: lane m of the accumulator is output voxel m of the tile
+        // epilogue: lane m of accumulator tz is output voxel m of tile tz
         const int m = warp * 32 + lane;
         const int yy = m / TILE_X, xx = m % TILE_X;
-        const long long v = (((long long)n0 * vol.d + z0) * vol.h + y0 + yy) * vol.w + x0 + xx;
-        const unsigned trow = tmem + ((unsigned)(warp * 32) << 16);
+        for (int tz = 0; tz < TZ; ++tz)
         for (int c0 = 0; c0 < N; c0 += 16) {
+            const long long v = (((long long)n0 * vol.d + z0 + tz) * vol.h + y0 + yy) * vol.w + x0 + xx;
+            const unsigned trow = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(tz * N);
             float acc[16];
             tmem_ld16(trow + (unsigned)c0, acc);
 #pragma unroll
@@ -507,6 +517,33 @@ int tmem_cols_for(int n) {
     return c;
 }
 
+// Launch configuration of the forward kernel: z planes per block (tz) and
+// weight stages (ns).  Two planes share every weight slab (half the weight
+// traffic per output voxel, twice the MMA work per slab); more stages keep
+// more slabs in flight.  The first that fits two blocks per SM, else one.
+struct TcCfg {
+    int tz, ns;
+    size_t smem;
+};
+
+TcCfg tc_cfg(int cin, int cout, int d, int tz_req, int ns_req) {
+    const int cg = cg_for(cin);
+    const int cols_per_tile = tmem_cols_for(cout);
+    TcCfg best{0, 0, 0};
+    const int tzs[2] = {2, 1};
+    const int nss[3] = {6, 4, 2};
+    for (int pass = 0; pass < 2 && !best.tz; ++pass)          // pass 0: two blocks per SM
+        for (int tz : tzs)
+            for (int ns : nss) {
+                if (best.tz || (tz_req && tz != tz_req) || (ns_req && ns != ns_req)) continue;
+                if (d % tz || tz * cols_per_tile > 256) continue;
+                const size_t sm = tc_smem_bytes(cg, cout, tz, ns);
+                const size_t lim = pass == 0 ? (size_t)113 * 1024 : (size_t)226 * 1024;
+                if (sm <= lim) best = TcCfg{tz, ns, sm};
+            }
+    return best;
+}
+
 }  // namespace
 
 extern "C" {
@@ -515,32 +552,58 @@ int lbm_nn_conv3d_tc_supported(int cin, int cout, int n, int d, int h, int w) {
     if (cin < 16 || cin % 16 || cout < 16 || cout % 16 || cout > 256) return 0;
     if (n < 1 || d < 1 || h < TILE_Y || w < TILE_X || h % TILE_Y || w % TILE_X) return 0;
     if ((long long)n * d * h * w >= (1LL << 40)) return 0;
-    return tc_smem_bytes(cg_for(cin), cout) + 256 <= 227 * 1024 ? 1 : 0;   // static shared memory too
+    return tc_cfg(cin, cout, d, 0, 0).tz ? 1 : 0;
 }
 
-lbm_status lbm_nn_conv3d_tc(const void* x, int cin, const void* wk, const float* bias, void* y, int cout,
-                            int n, int d, int h, int wdt, int relu, int out_f32, void* stream) {
+lbm_status lbm_nn_conv3d_tc_cfg(const void* x, int cin, const void* wk, const float* bias, void* y, int cout,
+                                int n, int d, int h, int wdt, int relu, int out_f32, int tz, int ns, void* stream) {
     if (!x || !wk || !y || !lbm_nn_conv3d_tc_supported(cin, cout, n, d, h, wdt)) return LBM_ERR_INVALID_ARG;
+    const TcCfg cf = tc_cfg(cin, cout, d, tz, ns);
+    if (!cf.tz) return LBM_ERR_INVALID_ARG;
     const int cg = cg_for(cin);
-    const int cols = tmem_cols_for(cout);
-    const size_t smem = tmem_safe_smem(tc_smem_bytes(cg, cout), cols);
+    const int cols = tmem_cols_for(cf.tz * tmem_cols_for(cout));
+    const size_t smem = tmem_safe_smem(cf.smem, cols);
     const Vol vol{n, d, h, wdt};
-    const long long blocks = (long long)(wdt / TILE_X) * (h / TILE_Y) * d * n;
+    const long long blocks = (long long)(wdt / TILE_X) * (h / TILE_Y) * (d / cf.tz) * n;
     if (blocks > 0x7fffffffLL) return LBM_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const bf16* X = static_cast<const bf16*>(x);
     const bf16* W = static_cast<const bf16*>(wk);
+    const int tstride = tmem_cols_for(cout);          // accumulator columns per plane
     cudaError_t e = cudaSuccess;
     auto go = [&](auto kern) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess) kern<<<(unsigned)blocks, THREADS, smem, st>>>(X, cin, cg, W, bias, y, cout, cols, vol);
     };
-    if (relu && !out_f32) go(conv3_tc_kernel<true, false>);
-    else if (!relu && !out_f32) go(conv3_tc_kernel<false, false>);
-    else if (relu) go(conv3_tc_kernel<true, true>);
-    else go(conv3_tc_kernel<false, true>);
+    (void)tstride;
+    auto pick = [&](auto tzc, auto nsc) {
+        constexpr int TZ = decltype(tzc)::value, NS = decltype(nsc)::value;
+        if (relu && !out_f32) go(conv3_tc_kernel<true, false, TZ, NS>);
+        else if (!relu && !out_f32) go(conv3_tc_kernel<false, false, TZ, NS>);
+        else if (relu) go(conv3_tc_kernel<true, true, TZ, NS>);
+        else go(conv3_tc_kernel<false, true, TZ, NS>);
+    };
+    using I1 = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>;
+    using S2 = std::integral_constant<int, 2>;
+    using S4 = std::integral_constant<int, 4>;
+    using S6 = std::integral_constant<int, 6>;
+    if (cf.tz == 2) {
+        if (cf.ns == 6) pick(I2{}, S6{});
+        else if (cf.ns == 4) pick(I2{}, S4{});
+        else pick(I2{}, S2{});
+    } else {
+        if (cf.ns == 6) pick(I1{}, S6{});
+        else if (cf.ns == 4) pick(I1{}, S4{});
+        else pick(I1{}, S2{});
+    }
     if (e == cudaSuccess) e = cudaGetLastError();
     return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+lbm_status lbm_nn_conv3d_tc(const void* x, int cin, const void* wk, const float* bias, void* y, int cout,
+                            int n, int d, int h, int wdt, int relu, int out_f32, void* stream) {
+    return lbm_nn_conv3d_tc_cfg(x, cin, wk, bias, y, cout, n, d, h, wdt, relu, out_f32, 0, 0, stream);
 }
 
 int lbm_nn_conv3d_wgrad_tc_supported(int cin, int cout, int n, int d, int h, int w) {

@@ -131,6 +131,7 @@ _PROTOS = {
     "lbm_nn_conv3d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "lbm_nn_conv3d_tc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "lbm_nn_conv3d_tc_supported": (ctypes.c_int, [ctypes.c_int] * 6),
+    "lbm_nn_conv3d_tc_cfg": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "lbm_nn_conv3d_wgrad_tc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "lbm_nn_conv3d_wgrad_tc_supported": (ctypes.c_int, [ctypes.c_int] * 6),
     "lbm_nn_weights_kmajor": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
@@ -406,6 +407,7 @@ lbm_nn_conv3d = _nn("lbm_nn_conv3d")
 lbm_nn_conv3d_wgrad = _nn("lbm_nn_conv3d_wgrad")
 lbm_nn_conv3d_tc = _nn("lbm_nn_conv3d_tc")
 lbm_nn_conv3d_tc_supported = _nn("lbm_nn_conv3d_tc_supported")
+lbm_nn_conv3d_tc_cfg = _nn("lbm_nn_conv3d_tc_cfg")
 lbm_nn_conv3d_wgrad_tc = _nn("lbm_nn_conv3d_wgrad_tc")
 lbm_nn_conv3d_wgrad_tc_supported = _nn("lbm_nn_conv3d_wgrad_tc_supported")
 lbm_nn_weights_kmajor = _nn("lbm_nn_weights_kmajor")

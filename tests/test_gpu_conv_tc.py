@@ -88,6 +88,28 @@ def test_tc_conv_forward_matches_reference_and_mma_sync(torch, cin, cout, vol):
     assert lbm.lbm_nn_tc_error(True) == 0
 
 
+@pytest.mark.parametrize("tz,ns", [(1, 2), (1, 4), (1, 6), (2, 2), (2, 4), (2, 6)])
+@pytest.mark.parametrize("cin,cout", [(64, 64), (32, 128), (128, 64)])
+def test_tc_conv_every_launch_configuration(torch, cin, cout, tz, ns):
+    """Every kernel variant (output planes per block x weight stages) against
+    the FP64 reference."""
+    vol = (1, 4, 16, 16)
+    n, d, h, w = vol
+    x, wt, b = _case(cin, cout, vol, 3 * tz + ns)
+    ref = R.conv3_np(x, wt, b)
+    xg, wg, bg = _dev(torch, x, wt, b)
+    wk = torch.empty((27, cout, cin), dtype=torch.bfloat16, device="cuda")
+    assert lbm.lbm_nn_weights_kmajor(wg.data_ptr(), wk.data_ptr(), cin, cout, 0, None) == lbm.LBM_OK
+    y = torch.empty((n * d * h * w, cout), dtype=torch.float32, device="cuda")
+    st = lbm.lbm_nn_conv3d_tc_cfg(xg.data_ptr(), cin, wk.data_ptr(), bg.data_ptr(), y.data_ptr(), cout,
+                                  n, d, h, w, 0, 1, tz, ns, None)
+    assert st == lbm.LBM_OK
+    torch.cuda.synchronize()
+    assert lbm.lbm_nn_tc_error(True) == 0
+    got = y.cpu().numpy().reshape(ref.shape)
+    assert np.max(np.abs(got - ref)) <= 1e-3 * np.max(np.abs(ref))
+
+
 @pytest.mark.parametrize("cin,cout", [(32, 64), (64, 32)])
 def test_tc_data_gradient_weights(torch, cin, cout):
     """With the flipped K-major weights the tensor-core conv of the output
