@@ -385,8 +385,8 @@ lbm_status lbm_nn_conv3d_wgrad_tc(const void* x, int cin, const void* g, int cou
 int lbm_nn_conv3d_wgrad_tc_supported(int cin, int cout, int n, int d, int h, int w);
 
 /* lbm_nn_conv3d_tc with an explicit launch configuration: tz output planes
- * per block (1 or 2: the planes share every weight slab) and ns weight stages
- * (2, 4 or 6); 0 lets the library choose, as lbm_nn_conv3d_tc does.
+ * per block (1, 2 or 4: the planes share every weight slab) and ns weight
+ * stages (2 or 4); 0 lets the library choose, as lbm_nn_conv3d_tc does.
  * LBM_ERR_INVALID_ARG if the sizes or the configuration do not fit (d must
  * be a multiple of tz; tz accumulators must fit 256 tensor-memory columns). */
 lbm_status lbm_nn_conv3d_tc_cfg(const void* x, int cin, const void* wk, const float* bias, void* y, int cout,
@@ -399,8 +399,8 @@ int lbm_nn_conv3d_tc_supported(int cin, int cout, int n, int d, int h, int w);
  * BF16 into wk).  The conv that uses them has K input and N output channels:
  * flip = 0 gives the forward conv (K = cin, N = cout); flip = 1 the data
  * gradient's conv (K = cout, N = cin, taps reversed: tap t uses
- * w[26 - t]).  The K channels are split into groups of G = K if K <= 64, else
- * 64, 32 or 16 (the largest that divides K); slab (tap, group) is
+ * w[26 - t]).  The K channels are split into groups of G = 32 if 32 divides
+ * K, else 16; slab (tap, group) is
  * [G/8][N][8] (input channel group*G + 8*k8 + e, output channel n), each slab
  * contiguous, slabs in (tap, group) order: the image of one shared-memory
  * weight stage, K-major core matrices of 8 x 8 elements. */

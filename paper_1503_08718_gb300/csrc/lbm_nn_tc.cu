@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <algorithm>
 #include <type_traits>
 
 #include "lbm.h"
@@ -124,10 +125,11 @@ struct Vol {
     int n, d, h, w;
 };
 
-// Input channels per shared-memory halo (a channel group): the whole input
-// up to 64 channels, else groups of 64, 32 or 16.
+// Input channels per shared-memory halo (a channel group): at most 32, so
+// that the halo of two planes (46 KB) leaves room for four blocks per SM;
+// groups of 32 or 16.
 __host__ __device__ constexpr int cg_for(int cin) {
-    return cin <= 64 ? cin : (cin % 64 == 0 ? 64 : (cin % 32 == 0 ? 32 : 16));
+    return cin % 32 == 0 ? 32 : 16;
 }
 
 // Shared memory of the forward kernel for tz output planes per block and ns
@@ -529,19 +531,21 @@ struct TcCfg {
 TcCfg tc_cfg(int cin, int cout, int d, int tz_req, int ns_req) {
     const int cg = cg_for(cin);
     const int cols_per_tile = tmem_cols_for(cout);
-    TcCfg best{0, 0, 0};
-    const int tzs[2] = {2, 1};
-    const int nss[3] = {6, 4, 2};
-    for (int pass = 0; pass < 2 && !best.tz; ++pass)          // pass 0: two blocks per SM
-        for (int tz : tzs)
-            for (int ns : nss) {
-                if (best.tz || (tz_req && tz != tz_req) || (ns_req && ns != ns_req)) continue;
-                if (d % tz || tz * cols_per_tile > 256) continue;
-                const size_t sm = tc_smem_bytes(cg, cout, tz, ns);
-                const size_t lim = pass == 0 ? (size_t)113 * 1024 : (size_t)226 * 1024;
-                if (sm <= lim) best = TcCfg{tz, ns, sm};
-            }
-    return best;
+    // measured on the network's layers: resident blocks hide the load
+    // latency better than deeper weight pipelines (two stages), and two
+    // planes sharing each weight slab pay while N <= 64 (four planes gain
+    // nothing more)
+    const int tz_pref = cols_per_tile <= 64 ? 2 : 1;
+    for (int tz : {4, 2, 1}) {
+        if (tz_req ? tz != tz_req : tz > tz_pref) continue;
+        if (d % tz || tz * cols_per_tile > 256) continue;
+        for (int ns : {2, 4}) {
+            if (ns_req ? ns != ns_req : ns != 2) continue;
+            const size_t sm = tc_smem_bytes(cg, cout, tz, ns);
+            if (sm <= (size_t)226 * 1024) return TcCfg{tz, ns, sm};
+        }
+    }
+    return TcCfg{0, 0, 0};
 }
 
 }  // namespace
@@ -585,16 +589,17 @@ lbm_status lbm_nn_conv3d_tc_cfg(const void* x, int cin, const void* wk, const fl
     };
     using I1 = std::integral_constant<int, 1>;
     using I2 = std::integral_constant<int, 2>;
+    using I4 = std::integral_constant<int, 4>;
     using S2 = std::integral_constant<int, 2>;
     using S4 = std::integral_constant<int, 4>;
-    using S6 = std::integral_constant<int, 6>;
-    if (cf.tz == 2) {
-        if (cf.ns == 6) pick(I2{}, S6{});
-        else if (cf.ns == 4) pick(I2{}, S4{});
+    if (cf.tz == 4) {
+        if (cf.ns == 4) pick(I4{}, S4{});
+        else pick(I4{}, S2{});
+    } else if (cf.tz == 2) {
+        if (cf.ns == 4) pick(I2{}, S4{});
         else pick(I2{}, S2{});
     } else {
-        if (cf.ns == 6) pick(I1{}, S6{});
-        else if (cf.ns == 4) pick(I1{}, S4{});
+        if (cf.ns == 4) pick(I1{}, S4{});
         else pick(I1{}, S2{});
     }
     if (e == cudaSuccess) e = cudaGetLastError();

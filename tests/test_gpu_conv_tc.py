@@ -88,13 +88,18 @@ def test_tc_conv_forward_matches_reference_and_mma_sync(torch, cin, cout, vol):
     assert lbm.lbm_nn_tc_error(True) == 0
 
 
-@pytest.mark.parametrize("tz,ns", [(1, 2), (1, 4), (1, 6), (2, 2), (2, 4), (2, 6)])
+@pytest.mark.parametrize("tz,ns", [(1, 2), (1, 4), (2, 2), (2, 4), (4, 2), (4, 4)])
 @pytest.mark.parametrize("cin,cout", [(64, 64), (32, 128), (128, 64)])
 def test_tc_conv_every_launch_configuration(torch, cin, cout, tz, ns):
     """Every kernel variant (output planes per block x weight stages) against
     the FP64 reference."""
     vol = (1, 4, 16, 16)
     n, d, h, w = vol
+    cols = 32
+    while cols < cout:
+        cols *= 2
+    if tz * cols > 256:
+        pytest.skip("the accumulators of this many planes exceed 256 tensor-memory columns")
     x, wt, b = _case(cin, cout, vol, 3 * tz + ns)
     ref = R.conv3_np(x, wt, b)
     xg, wg, bg = _dev(torch, x, wt, b)
