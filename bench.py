@@ -18,6 +18,13 @@ resident.  `e2e`: the same metric through the public C ABI with pinned host
 buffers: upload the phase map and tensors, solve ITERS iterations from the
 linear start, download the temperature field, every step.
 
+Outside the timed region (--legs, default all): per-config lines (the 32^3
+layered cell, the bench cell's six solves, the 192-solve batched sweep, the
+256x256x512 precision cell with its oracle error), time to k_eff within 1e-4
+of the FP64 oracle's converged value, the combined batched + warm-started +
+BF16 form against plain FP32, the learned warm start on 128x128x256 cells
+and the tensor-core convolution's throughput.
+
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload.
 """
@@ -827,7 +834,10 @@ def run_ours(args):
                               "k_eff_rel_vs_f32": (i16.k_eff - info.k_eff) / info.k_eff}
 
     extras = {}
-    if not args.no_extras:
+    legs = set() if args.no_extras else set(args.legs.split(","))
+    if "all" in legs:
+        legs = {"configs", "time_to_keff", "combined", "cfg5", "conv"}
+    if "configs" in legs:
         extras["configs"] = {
             "cfg1_layered32": config1_layered(lbm, I, stream),
             "cfg2_bench_cell_all_solves": config2_all_solves(lbm, S, stream, n_vox),
@@ -835,9 +845,13 @@ def run_ours(args):
             "cfg4_braid256x256x512": config4_precision(lbm, I, stream, peak,
                                                        with_oracle=not args.skip_cpu),
         }
+    if "time_to_keff" in legs:
         extras["time_to_keff"] = time_to_keff(lbm, S, stream)
+    if "combined" in legs:
         extras["combined_form"] = combined_form(lbm, I, stream)
-        extras["configs"]["cfg5_warm_start"] = warm_start_config5(lbm, I, stream)
+    if "cfg5" in legs:
+        extras.setdefault("configs", {})["cfg5_warm_start"] = warm_start_config5(lbm, I, stream)
+    if "conv" in legs:
         sus, sus_kind = bf16_sustained_tflops()
         extras["warmnet_conv"] = conv_throughput(lbm, sus)
         extras["warmnet_conv"]["peak_source"] = sus_kind
@@ -936,7 +950,10 @@ def main():
     ap.add_argument("--no-variants", action="store_true",
                     help="omit the BF16/FP16 storage variants of the step")
     ap.add_argument("--no-extras", action="store_true",
-                    help="omit the time-to-k_eff runs and the batched sweep")
+                    help="omit every leg outside the timed region")
+    ap.add_argument("--legs", default="all",
+                    help="comma list of the legs outside the timed region: configs, time_to_keff, "
+                         "combined, cfg5, conv (default all)")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline leg")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--oracle-extras", action="store_true",

@@ -22,6 +22,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lbm.h"
 #include "lbm_kernels.cuh"
 
@@ -410,6 +412,10 @@ lbm_status lbm_batch_solve(lbm_batch* b, lbm_lateral lateral, const lbm_solve_op
         return bfail(b, LBM_ERR_INVALID_ARG,
                      "invalid options (walls, even check_every <= 4096, storage, tau_max; no t_init)");
     BCUDA(b, cudaSetDevice(b->device));
+    nvtxRangePushA("lbm_batch_solve");
+    struct PopOnExit {
+        ~PopOnExit() { nvtxRangePop(); }
+    } pop_on_exit;
     free_device(b);
     b->opts = op;
     b->fmt = op.storage;

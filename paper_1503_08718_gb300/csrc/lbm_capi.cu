@@ -16,6 +16,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lbm.h"
 #include "lbm_kernels.cuh"
 
@@ -96,6 +98,13 @@ struct lbm_ctx {
 namespace {
 
 constexpr int kHistCap = 1 << 16;          // checks kept in the history ring
+
+// NVTX range for the duration of a scope (visible to Nsight tools; the
+// header-only NVTX library costs nothing when no tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 lbm_status fail(lbm_ctx* c, lbm_status st, const char* fmt, ...) {
     char buf[512];
@@ -699,6 +708,7 @@ lbm_status lbm_set_tensors(lbm_ctx* c, const double* lambda, int n_phases) {
 
 lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_solve_opts* o) {
     CHECK_CTX(c);
+    NvtxRange nvtx("lbm_start");
     if (!c->have_geometry || !c->have_tensors)
         return fail(c, LBM_ERR_STATE, "set geometry and tensors before starting a solve");
     if (axis < LBM_AXIS_X || axis > LBM_AXIS_Z) return fail(c, LBM_ERR_INVALID_ARG, "bad axis");
@@ -881,6 +891,7 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
 
 lbm_status lbm_advance(lbm_ctx* c, int64_t n_steps) {
     CHECK_CTX(c);
+    NvtxRange nvtx("lbm_advance");
     if (!c->started) return fail(c, LBM_ERR_STATE, "call lbm_start first");
     if (n_steps < 0) return fail(c, LBM_ERR_INVALID_ARG, "n_steps must be >= 0");
     if (n_steps == 0) return LBM_OK;
@@ -906,6 +917,7 @@ lbm_status lbm_advance(lbm_ctx* c, int64_t n_steps) {
 
 lbm_status lbm_check(lbm_ctx* c, lbm_solve_info* info) {
     CHECK_CTX(c);
+    NvtxRange nvtx("lbm_check");
     if (!c->started) return fail(c, LBM_ERR_STATE, "call lbm_start first");
     CUDA_TRY(c, cudaSetDevice(c->device));
     CUDA_TRY(c, cudaEventRecord(c->ev0, c->stream));
@@ -924,6 +936,7 @@ lbm_status lbm_check(lbm_ctx* c, lbm_solve_info* info) {
 
 lbm_status lbm_run(lbm_ctx* c, lbm_solve_info* info) {
     CHECK_CTX(c);
+    NvtxRange nvtx("lbm_run");
     if (!c->started) return fail(c, LBM_ERR_STATE, "call lbm_start first");
     CUDA_TRY(c, cudaSetDevice(c->device));
     const int K = c->opts.check_every;
