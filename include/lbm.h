@@ -530,6 +530,18 @@ lbm_status lbm_braid_unit_cell(double phi_f, int n_f, double d_f, double gamma_r
  * uint8, original order) to host_out (caller-owned). */
 lbm_status lbm_get_geometry(lbm_ctx* c, uint8_t* host_out);
 
+/* No counterpart in the paper (a stand-in for a memory checker).  1 if this
+ * library was built with bounds checks (LBM_DEBUG): every global and ring
+ * access of the step kernels is checked against its buffer, an access outside
+ * records a code (and touches the buffer's first element instead), and the
+ * solver calls that synchronise (lbm_check, lbm_run, lbm_solve,
+ * lbm_batch_solve) then fail with LBM_ERR_INTERNAL.  0 for the normal build. */
+int lbm_debug_build(void);
+
+/* The recorded bounds-check code of the context kernels (0: none; always 0
+ * in the normal build); clear != 0 resets it.  Synchronous. */
+lbm_status lbm_debug_error(unsigned* out, int clear);
+
 /* No counterpart in the paper.  Message of the last failed call on this
  * context (context-owned string, valid until the next call).  NULL-safe. */
 const char* lbm_last_error(const lbm_ctx* c);

@@ -831,6 +831,13 @@ lbm_status lbm_batch_solve(lbm_batch* b, lbm_lateral lateral, const lbm_solve_op
     }
     float ms = 0.f;
     BCUDA(b, cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+#ifdef LBM_DEBUG
+    {
+        unsigned code = 0;
+        BCUDA(b, cudaMemcpyFromSymbol(&code, lbm::g_lbm_debug, sizeof code));
+        if (code) return bfail(b, LBM_ERR_INTERNAL, "bounds check %u failed in a batched step kernel", code);
+    }
+#endif
     long long updates = 0;
     int converged = 0;
     for (int s = 0; s < n_solves; ++s) {

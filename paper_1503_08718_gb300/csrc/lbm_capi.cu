@@ -432,11 +432,26 @@ void fill_info(const lbm_ctx* c, lbm_solve_info* info, double ms) {
     info->checks = (int32_t)c->h_ctl->checks;
 }
 
+// The bounds-check word of this translation unit's kernels (bounds-checked
+// builds only): a recorded code fails the call with LBM_ERR_INTERNAL.
+lbm_status debug_word(lbm_ctx* c) {
+#ifdef LBM_DEBUG
+    unsigned code = 0;
+    CUDA_TRY(c, cudaMemcpyFromSymbol(&code, lbm::g_lbm_debug, sizeof code));
+    if (code) return fail(c, LBM_ERR_INTERNAL, "bounds check %u failed in a step kernel", code);
+#else
+    (void)c;
+#endif
+    return LBM_OK;
+}
+
 lbm_status read_ctl(lbm_ctx* c, cudaStream_t st) {
     CUDA_TRY(c, cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(c, cudaMemcpyAsync(c->Q_host.data(), c->d_Q, sizeof(double) * c->L.NZ,
                                 cudaMemcpyDeviceToHost, st));
     CUDA_TRY(c, cudaStreamSynchronize(st));
+    const lbm_status dbg = debug_word(c);
+    if (dbg != LBM_OK) return dbg;
     c->k_eff = c->h_ctl->k_eff;
     c->have_k = c->h_ctl->checks > 0;
     return LBM_OK;
@@ -1177,6 +1192,29 @@ lbm_status lbm_set_state(lbm_ctx* c, const void* host_in, size_t bytes) {
     CUDA_TRY(c, cudaMemsetAsync(c->d_plane_cnt, 0, sizeof(int) * c->L.NZ, st));
     lbm_status s2 = read_ctl(c, st);
     if (s2 != LBM_OK) return s2;
+    return LBM_OK;
+}
+
+int lbm_debug_build(void) {
+#ifdef LBM_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+lbm_status lbm_debug_error(unsigned* out, int clear) {
+    if (!out) return LBM_ERR_INVALID_ARG;
+    *out = 0;
+#ifdef LBM_DEBUG
+    if (cudaMemcpyFromSymbol(out, lbm::g_lbm_debug, sizeof *out) != cudaSuccess) return LBM_ERR_CUDA;
+    if (clear) {
+        const unsigned z = 0;
+        if (cudaMemcpyToSymbol(lbm::g_lbm_debug, &z, sizeof z) != cudaSuccess) return LBM_ERR_CUDA;
+    }
+#else
+    (void)clear;
+#endif
     return LBM_OK;
 }
 

@@ -42,6 +42,29 @@
 
 namespace lbm {
 
+// Bounds-checked build (-DLBM_DEBUG, `build.build(debug=True)`): every
+// global and ring access of the step kernels is checked against its buffer;
+// an access outside records its code in the device word g_lbm_debug (one per
+// translation unit) and goes to the buffer's first element instead.  The host
+// calls turn a recorded code into LBM_ERR_INTERNAL.  This stands in for a
+// memory checker: the index arithmetic of every launch is checked while the
+// parity tests run.  Without LBM_DEBUG the checks compile to nothing.
+#ifdef LBM_DEBUG
+static __device__ unsigned int g_lbm_debug = 0u;
+template <typename T>
+__device__ __forceinline__ T* dbg_ptr(T* p, T* base, long long count, int width, unsigned code) {
+    const long long i = p - base;
+    if (i < 0 || i + width > count) {
+        atomicCAS(&g_lbm_debug, 0u, code);
+        return base;
+    }
+    return p;
+}
+#define LBM_CK(p, base, count, width, code) ::lbm::dbg_ptr((p), (base), (long long)(count), (width), (code))
+#else
+#define LBM_CK(p, base, count, width, code) (p)
+#endif
+
 constexpr int kThreads = 256;        // threads per step block
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -453,15 +476,15 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
     Raw c0 = S::zero(), c1 = c0, c2 = c0, c3 = c0, c4 = c0, c5 = c0, c6 = c0;
     uint2 ph = make_uint2(0u, 0u);
     if (active) {
-        c0 = S::load(src + row + x0);
-        c1 = S::load(src + P + row + x0);
-        c2 = S::load(src + 2 * P + row + x0);
-        c3 = S::load(src + o3 + x0);
-        c4 = S::load(src + o4 + x0);
-        c5 = S::load(src + o5 + x0);
-        c6 = S::load(src + o6 + x0);
-        if (V == 8) ph = __ldg(reinterpret_cast<const uint2*>(a.phase + row + x0));
-        else ph.x = __ldg(reinterpret_cast<const unsigned*>(a.phase + row + x0));
+        c0 = S::load(LBM_CK(src + row + x0, src, 7 * P, V, 1u));
+        c1 = S::load(LBM_CK(src + P + row + x0, src, 7 * P, V, 1u));
+        c2 = S::load(LBM_CK(src + 2 * P + row + x0, src, 7 * P, V, 1u));
+        c3 = S::load(LBM_CK(src + o3 + x0, src, 7 * P, V, 1u));
+        c4 = S::load(LBM_CK(src + o4 + x0, src, 7 * P, V, 1u));
+        c5 = S::load(LBM_CK(src + o5 + x0, src, 7 * P, V, 1u));
+        c6 = S::load(LBM_CK(src + o6 + x0, src, 7 * P, V, 1u));
+        if (V == 8) ph = __ldg(reinterpret_cast<const uint2*>(LBM_CK(a.phase + row + x0, a.phase, P, V, 2u)));
+        else ph.x = __ldg(reinterpret_cast<const unsigned*>(LBM_CK(a.phase + row + x0, a.phase, P, V, 2u)));
     }
     // Frame changes (all exact): a population pulled from plane z' carries
     // w_i R_src(z'); it is re-expressed relative to R_dst(z) of this node.
@@ -475,15 +498,16 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
     const float right2 = __shfl_down_sync(kFull, S::get(c2, 0), 1);
     float f1_0, f2_last;
     if (lane > 0 && qx > 0) f1_0 = left1;
-    else if (qx > 0) f1_0 = active ? S::scalar(src + P + row + x0 - 1) : 0.f;
-    else f1_0 = PERIODIC ? (active ? S::scalar(src + P + row + a.nx - 1) : 0.f) : S::get(c2, 0);
+    else if (qx > 0) f1_0 = active ? S::scalar(LBM_CK(src + P + row + x0 - 1, src, 7 * P, 1, 3u)) : 0.f;
+    else f1_0 = PERIODIC ? (active ? S::scalar(LBM_CK(src + P + row + a.nx - 1, src, 7 * P, 1, 3u)) : 0.f)
+                         : S::get(c2, 0);
     // the last real voxel of the row sits in the row's last vector, at e_last
     const int e_last = (RAGGED && qx == nq - 1) ? a.nx - 1 - x0 : V;
     float edge2 = 0.f;
     if (qx < nq - 1) {
-        f2_last = (lane < 31) ? right2 : (active ? S::scalar(src + 2 * P + row + x0 + V) : 0.f);
+        f2_last = (lane < 31) ? right2 : (active ? S::scalar(LBM_CK(src + 2 * P + row + x0 + V, src, 7 * P, 1, 3u)) : 0.f);
     } else {
-        edge2 = PERIODIC ? (active ? S::scalar(src + 2 * P + row) : 0.f) : S::get(c1, V - 1);
+        edge2 = PERIODIC ? (active ? S::scalar(LBM_CK(src + 2 * P + row, src, 7 * P, 1, 3u)) : 0.f) : S::get(c1, V - 1);
         f2_last = RAGGED ? 0.f : edge2;
         if (RAGGED && !PERIODIC) edge2 = 0.f;
     }
@@ -497,7 +521,7 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
     if (CHECK) {
 #pragma unroll
         for (int v4 = 0; v4 < V / 4; ++v4) {
-            const float4 q4 = active ? *reinterpret_cast<const float4*>(a.tsnap + row + x0 + 4 * v4)
+            const float4 q4 = active ? *reinterpret_cast<const float4*>(LBM_CK(a.tsnap + row + x0 + 4 * v4, a.tsnap, P, 4, 4u))
                                      : make_float4(0.f, 0.f, 0.f, 0.f);
             thp[4 * v4] = q4.x; thp[4 * v4 + 1] = q4.y; thp[4 * v4 + 2] = q4.z; thp[4 * v4 + 3] = q4.w;
         }
@@ -552,11 +576,12 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
             key = seed ^ (unsigned)((row + x0) >> 1) * 0x85ebca6bu;
         }
 #pragma unroll
-        for (int i = 0; i < 7; ++i) S::store(dst + i * P, o[i], key + 0x9E3779B9u * (unsigned)i);
+        for (int i = 0; i < 7; ++i)
+            S::store(LBM_CK(dst + i * P, reinterpret_cast<T*>(a.dst), 7 * P, V, 5u), o[i], key + 0x9E3779B9u * (unsigned)i);
         if (CHECK) {
 #pragma unroll
             for (int v4 = 0; v4 < V / 4; ++v4)
-                st4(a.tsnap + row + x0 + 4 * v4,
+                st4(LBM_CK(a.tsnap + row + x0 + 4 * v4, a.tsnap, P, 4, 4u),
                     make_float4(thv[4 * v4], thv[4 * v4 + 1], thv[4 * v4 + 2], thv[4 * v4 + 3]));
         }
     }
@@ -589,7 +614,7 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
                 const long long base = (long long)z * a.blocks_per_plane + bx;
                 const long long plane_all = (long long)a.nz * a.blocks_per_plane;
 #pragma unroll
-                for (int m = 0; m < 4; ++m) ck.part[m * plane_all + base] = v[m];
+                for (int m = 0; m < 4; ++m) *LBM_CK(ck.part + m * plane_all + base, ck.part, 4 * plane_all, 1, 6u) = v[m];
                 // the last block of this plane to finish closes the plane
                 __threadfence();
                 const int ticket = atomicAdd(&ck.plane_cnt[z], 1);
@@ -800,15 +825,18 @@ __device__ __forceinline__ void fused2_body(const StepArgs& a, float* fn, const 
         unsigned phC = 0u;
         if (first) {
             const float* s = src + (long long)i * PL;
-            q0 = __ldg(reinterpret_cast<const float4*>(s + yrow + x));
-            q1 = __ldg(reinterpret_cast<const float4*>(s + P + yrow + x));
-            q2 = __ldg(reinterpret_cast<const float4*>(s + 2 * P + yrow + x));
-            q3 = __ldg(reinterpret_cast<const float4*>(s + o3 + x));
-            q4 = __ldg(reinterpret_cast<const float4*>(s + o4 + x));
+            q0 = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + yrow + x, src, 7 * P, 4, 11u)));
+            q1 = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + P + yrow + x, src, 7 * P, 4, 11u)));
+            q2 = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + 2 * P + yrow + x, src, 7 * P, 4, 11u)));
+            q3 = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + o3 + x, src, 7 * P, 4, 11u)));
+            q4 = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + o4 + x, src, 7 * P, 4, 11u)));
             // the walls (Eq. 23) read the own node's opposite population
-            q5 = __ldg(reinterpret_cast<const float4*>(s + (i > 0 ? 5 * P - PL : 6 * P) + yrow + x));
-            q6 = __ldg(reinterpret_cast<const float4*>(s + (i < nz - 1 ? 6 * P + PL : 5 * P) + yrow + x));
-            phC = __ldg(reinterpret_cast<const unsigned*>(a.phase + (long long)i * PL + yrow + x));
+            q5 = __ldg(reinterpret_cast<const float4*>(
+                LBM_CK(s + (i > 0 ? 5 * P - PL : 6 * P) + yrow + x, src, 7 * P, 4, 11u)));
+            q6 = __ldg(reinterpret_cast<const float4*>(
+                LBM_CK(s + (i < nz - 1 ? 6 * P + PL : 5 * P) + yrow + x, src, 7 * P, 4, 11u)));
+            phC = __ldg(reinterpret_cast<const unsigned*>(
+                LBM_CK(a.phase + (long long)i * PL + yrow + x, a.phase, P, 4, 12u)));
         } else if (!WR) {
             q0 = q1 = q2 = q3 = q4 = q5 = q6 = make_float4(0.f, 0.f, 0.f, 0.f);
         }
@@ -822,25 +850,27 @@ __device__ __forceinline__ void fused2_body(const StepArgs& a, float* fn, const 
             float4 g0, c1, c2, g3, g4, g5, g6;
             if (!WR && !second) g0 = c1 = c2 = g3 = g4 = g5 = g6 = make_float4(0.f, 0.f, 0.f, 0.f);
             if (WR || second) {
-                g0 = *reinterpret_cast<const float4*>(fs);
-                c1 = *reinterpret_cast<const float4*>(fs + Q1);
-                c2 = *reinterpret_cast<const float4*>(fs + Q2);
-                g3 = (PERIODIC || !ylo) ? *reinterpret_cast<const float4*>(fs + Q3 - NXB)
-                                        : *reinterpret_cast<const float4*>(fs + Q4);
-                g4 = (PERIODIC || !yhi) ? *reinterpret_cast<const float4*>(fs + Q4 + NXB)
-                                        : *reinterpret_cast<const float4*>(fs + Q3);
-                g5 = j > 0 ? *reinterpret_cast<const float4*>(fb + Q5)
-                           : f4neg(*reinterpret_cast<const float4*>(fs + Q6));
-                g6 = j < nz - 1 ? *reinterpret_cast<const float4*>(fa + Q6)
-                                : f4neg(*reinterpret_cast<const float4*>(fs + Q5));
+                const float* rb = fn;
+                const int RN = 3 * RS;
+                g0 = *reinterpret_cast<const float4*>(LBM_CK(fs, rb, RN, 4, 15u));
+                c1 = *reinterpret_cast<const float4*>(LBM_CK(fs + Q1, rb, RN, 4, 15u));
+                c2 = *reinterpret_cast<const float4*>(LBM_CK(fs + Q2, rb, RN, 4, 15u));
+                g3 = (PERIODIC || !ylo) ? *reinterpret_cast<const float4*>(LBM_CK(fs + Q3 - NXB, rb, RN, 4, 15u))
+                                        : *reinterpret_cast<const float4*>(LBM_CK(fs + Q4, rb, RN, 4, 15u));
+                g4 = (PERIODIC || !yhi) ? *reinterpret_cast<const float4*>(LBM_CK(fs + Q4 + NXB, rb, RN, 4, 15u))
+                                        : *reinterpret_cast<const float4*>(LBM_CK(fs + Q3, rb, RN, 4, 15u));
+                g5 = j > 0 ? *reinterpret_cast<const float4*>(LBM_CK(fb + Q5, rb, RN, 4, 15u))
+                           : f4neg(*reinterpret_cast<const float4*>(LBM_CK(fs + Q6, rb, RN, 4, 15u)));
+                g6 = j < nz - 1 ? *reinterpret_cast<const float4*>(LBM_CK(fa + Q6, rb, RN, 4, 15u))
+                                : f4neg(*reinterpret_cast<const float4*>(LBM_CK(fs + Q5, rb, RN, 4, 15u)));
             }
             // x-neighbours: from the next lane (every lane takes part), else
             // from the ring row
             float l1 = __shfl_sync(kFull, c1.w, (lane + 31) & 31);
             float r2 = __shfl_sync(kFull, c2.x, (lane + 1) & 31);
             if (WR || second) {
-                if (!own_left) l1 = fs[Q1 - x + xm];
-                if (!own_right) r2 = fs[Q2 - x + xp];
+                if (!own_left) l1 = *LBM_CK(fs + Q1 - x + xm, (const float*)fn, 3 * RS, 1, 15u);
+                if (!own_right) r2 = *LBM_CK(fs + Q2 - x + xp, (const float*)fn, 3 * RS, 1, 15u);
                 if (!PERIODIC && x == 0) l1 = c2.x;                 // Eq. 24 at x = 0
                 if (!PERIODIC && x + 4 == NXB) r2 = c1.w;           // and at x = nx - 1
                 const float4 g1 = make_float4(l1, c1.x, c1.y, c1.z);
@@ -848,7 +878,7 @@ __device__ __forceinline__ void fused2_body(const StepArgs& a, float* fn, const 
                 const Quad7 o = collide_quad(g0, g1, g2, g3, g4, g5, g6, phA, s_sa, s_sc, kn1.kT, kn1.kJ);
                 float* d = dst + (long long)j * PL + yrow + x;
 #pragma unroll
-                for (int p = 0; p < 7; ++p) *reinterpret_cast<float4*>(d + p * P) = o.o[p];
+                for (int p = 0; p < 7; ++p) *reinterpret_cast<float4*>(LBM_CK(d + p * P, dst, 7 * P, 4, 14u)) = o.o[p];
             }
         }
         // ---- step n at plane i into the ring ----
@@ -858,26 +888,27 @@ __device__ __forceinline__ void fused2_body(const StepArgs& a, float* fn, const 
             float l1 = __shfl_sync(kFull, q1.w, (lane + 31) & 31);
             float r2 = __shfl_sync(kFull, q2.x, (lane + 1) & 31);
             if (WR || first) {
-                if (!own_left) l1 = __ldg(src + (long long)i * PL + P + yrow + xm);
-                if (!own_right) r2 = __ldg(src + (long long)i * PL + 2 * P + yrow + xp);
+                if (!own_left) l1 = __ldg(LBM_CK(src + (long long)i * PL + P + yrow + xm, src, 7 * P, 1, 13u));
+                if (!own_right) r2 = __ldg(LBM_CK(src + (long long)i * PL + 2 * P + yrow + xp, src, 7 * P, 1, 13u));
                 if (!PERIODIC && x == 0) l1 = q2.x;
                 if (!PERIODIC && x + 4 == NXB) r2 = q1.w;
                 const float4 g1 = make_float4(l1, q1.x, q1.y, q1.z);
                 const float4 g2 = make_float4(q2.y, q2.z, q2.w, r2);
                 const Quad7 o = collide_quad(q0, g1, g2, q3, q4, q5, q6, phC, s_sa, s_sc, kn.kT, kn.kJ);
                 float* w = fn + si * RS + own;       // block row 0 only writes population 3
+                const int RN = 3 * RS;
                 if (tile_row) {
-                    *reinterpret_cast<float4*>(w) = o.o[0];
-                    *reinterpret_cast<float4*>(w + Q1) = o.o[1];
-                    *reinterpret_cast<float4*>(w + Q2) = o.o[2];
-                    *reinterpret_cast<float4*>(w + Q3) = o.o[3];
-                    *reinterpret_cast<float4*>(w + Q4) = o.o[4];
-                    *reinterpret_cast<float4*>(w + Q5) = o.o[5];
-                    *reinterpret_cast<float4*>(w + Q6) = o.o[6];
+                    *reinterpret_cast<float4*>(LBM_CK(w, fn, RN, 4, 16u)) = o.o[0];
+                    *reinterpret_cast<float4*>(LBM_CK(w + Q1, fn, RN, 4, 16u)) = o.o[1];
+                    *reinterpret_cast<float4*>(LBM_CK(w + Q2, fn, RN, 4, 16u)) = o.o[2];
+                    *reinterpret_cast<float4*>(LBM_CK(w + Q3, fn, RN, 4, 16u)) = o.o[3];
+                    *reinterpret_cast<float4*>(LBM_CK(w + Q4, fn, RN, 4, 16u)) = o.o[4];
+                    *reinterpret_cast<float4*>(LBM_CK(w + Q5, fn, RN, 4, 16u)) = o.o[5];
+                    *reinterpret_cast<float4*>(LBM_CK(w + Q6, fn, RN, 4, 16u)) = o.o[6];
                 } else if (r == 0) {
-                    *reinterpret_cast<float4*>(w + Q3) = o.o[3];
+                    *reinterpret_cast<float4*>(LBM_CK(w + Q3, fn, RN, 4, 16u)) = o.o[3];
                 } else {                                 // r == fyb + 1
-                    *reinterpret_cast<float4*>(w + Q4) = o.o[4];
+                    *reinterpret_cast<float4*>(LBM_CK(w + Q4, fn, RN, 4, 16u)) = o.o[4];
                 }
             }
         }

@@ -16,7 +16,8 @@ import os
 import numpy as np
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "_build", "libmrtlbm.so")
+# LBM_LIBRARY selects another build of the library (the bounds-checked one)
+LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(PKG, "_build", "libmrtlbm.so")
 
 LBM_OK = 0
 LBM_ERR_INVALID_ARG = 1
@@ -151,6 +152,8 @@ _PROTOS = {
     "lbm_create_with_workspace": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(_ctx_p)]),
     "lbm_get_launch_plan": (ctypes.c_int, [_ctx_p, ctypes.POINTER(lbm_launch_plan)]),
+    "lbm_debug_build": (ctypes.c_int, []),
+    "lbm_debug_error": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint), ctypes.c_int]),
     "lbm_state_bytes": (ctypes.c_size_t, [_ctx_p]),
     "lbm_get_state": (ctypes.c_int, [_ctx_p, ctypes.c_void_p, ctypes.c_size_t]),
     "lbm_set_state": (ctypes.c_int, [_ctx_p, ctypes.c_void_p, ctypes.c_size_t]),
@@ -307,6 +310,17 @@ def lbm_braid_voxelize_noalloc(nx: int, ny: int, nz: int, g_rad: float, A: float
                                            d_phase, ctypes.byref(used), ctypes.byref(frac),
                                            stream, msg, len(msg))
     return st, used.value, frac.value, msg.value.decode()
+
+
+def lbm_debug_build() -> int:
+    return int(load().lbm_debug_build())
+
+
+def lbm_debug_error(clear: bool = True):
+    """Returns (status, recorded bounds-check code)."""
+    v = ctypes.c_uint(0)
+    st = load().lbm_debug_error(ctypes.byref(v), int(clear))
+    return st, v.value
 
 
 def lbm_get_launch_plan(ctx):
