@@ -36,8 +36,7 @@ namespace {
 using bf16 = __nv_bfloat16;
 
 constexpr int TILE_Y = 16, TILE_X = 8;             // 128 output voxels per block
-constexpr int HZ = 3, HY = TILE_Y + 2, HX = TILE_X + 2;
-constexpr int HALO_VOX = HZ * HY * HX;             // 540
+constexpr int HY = TILE_Y + 2, HX = TILE_X + 2;     // halo of a tile's plane
 constexpr int THREADS = 128;
 constexpr unsigned kSpinLimit = 1u << 22;          // bounded mbarrier waits
 
@@ -349,49 +348,69 @@ __global__ void __launch_bounds__(THREADS) conv3_tc_kernel(const bf16* __restric
 // G[v][co].  Per tap a GEMM D[co][ci] (M = output channels, zero-padded to
 // 128; N = a group of at most 64 input channels; K = voxels).  Both operands
 // are channels-last in memory, so both enter the MMA MN-major: 16-byte rows
-// of 8 channels, one per voxel.  A block loops over tiles of 128 voxels (the
-// forward kernel's 16 x 8 tiles) and keeps one accumulator per tap of its
-// tap group in tensor memory (256 columns: 4 taps of 64 channels, 8 of 32);
-// per tile it stages the output-gradient tile G [co/8][128 voxels] and the
-// input halo (as in the forward kernel), and each tap's B operand is the halo
-// seen through its own descriptor.  At the end the accumulators are added
-// into dW (FP32 atomics, dW zeroed by the caller).
+// of 8 channels, one per voxel.  A block owns one column of 16 x 8 tiles
+// (cell n0, rows y0..y0+15, voxels x0..x0+7) over a range of planes, a group
+// of taps and a group of CG input channels, and keeps one accumulator per tap
+// in tensor memory (512 columns: 8 taps of 64 channels, 16 of 32, 27 of 16);
+// each tap's B operand is the input halo seen through its own descriptor.
+// The halo lives in a ring of four planes ([CG/8][4 slots][18][10] x 16 B):
+// tile z reads planes z-1, z, z+1 and, while its MMAs run, the block loads
+// plane z+2 into the fourth slot together with the next output-gradient tile
+// (two G buffers), so each tile brings in one halo plane, not three.  Each G
+// buffer has its own mbarrier (tile k commits to bar[k & 1]), so a wait never
+// lags its barrier by more than one phase.  At the end the accumulators are
+// added into dW (FP32 atomics, dW zeroed by the caller).
 // MN-major no-swizzle layout: core matrices of 8 K-rows x 16 bytes; the
 // descriptor's LBO is the stride between core matrices along K and its SBO
 // the stride along M (N).
-constexpr int WG_TMEM = 256;
+constexpr int WGZ_TMEM = 512;
 
 template <int CG>
-__global__ void __launch_bounds__(THREADS) conv3_wgrad_tc_kernel(const bf16* __restrict__ X, int Cin,
-                                                                 const bf16* __restrict__ G, int Cout,
-                                                                 float* __restrict__ dW, Vol vol,
-                                                                 int n_tiles) {
+__global__ void __launch_bounds__(THREADS) conv3_wgrad_z_kernel(const bf16* __restrict__ X, int Cin,
+                                                                const bf16* __restrict__ G, int Cout,
+                                                                float* __restrict__ dW, Vol vol, int zchunk,
+                                                                int taps_per_block) {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int CG8 = CG / 8;
-    constexpr int TAPS = WG_TMEM / CG;             // accumulators per block
+    constexpr int RING = 4;
+    constexpr int PLANE = HY * HX;                 // halo voxels of one plane
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    unsigned char* gs = smem;                      // [16][128] x 16 B (co blocks x voxels)
-    unsigned char* halo = smem + 16 * 128 * 16;    // [CG/8][3][18][10] x 16 B
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(halo + (size_t)HALO_VOX * CG * 2);
-    unsigned* tmem_slot = reinterpret_cast<unsigned*>(bar + 1);
-    __shared__ int s_fail;
-    const unsigned gs_s = smem_u32(gs), halo_s = smem_u32(halo);
+    unsigned char* ring = smem;                    // [CG/8][4][18][10] x 16 B
+    unsigned char* gs = ring + (size_t)RING * PLANE * CG * 2;   // 2 x [16][128] x 16 B
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(gs + 2 * 16 * 128 * 16);
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(bar + 2);
+    __shared__ volatile int s_fail;
+    const unsigned ring_s = smem_u32(ring), gs_s = smem_u32(gs);
     const int Cout8 = Cout / 8;
-    const int tap0 = blockIdx.y * TAPS;
-    const int ntap = min(TAPS, 27 - tap0);
-    const int g = blockIdx.z;                      // input channel group
+    const int tap0 = blockIdx.y * taps_per_block;
+    const int ntap = min(taps_per_block, 27 - tap0);
+    const int g = blockIdx.z;
 
-    // the padding rows of G (output channels Cout .. 127) stay zero
-    for (int i = tid; i < (16 - Cout8) * 128; i += THREADS)
-        *reinterpret_cast<uint4*>(gs + (size_t)(Cout8 * 128 + i) * 16) = make_uint4(0u, 0u, 0u, 0u);
+    const int tiles_x = vol.w / TILE_X, tiles_y = vol.h / TILE_Y;
+    const int zchunks = (vol.d + zchunk - 1) / zchunk;
+    int b = blockIdx.x;
+    const int zc = b % zchunks; b /= zchunks;
+    const int tx = b % tiles_x; b /= tiles_x;
+    const int ty = b % tiles_y; b /= tiles_y;
+    const int n0 = b;
+    const int x0 = tx * TILE_X, y0 = ty * TILE_Y;
+    const int zb = zc * zchunk, ze = min(zb + zchunk, vol.d);
+
+    // the padding rows of G (output channels Cout .. 127) stay zero in both buffers
+    for (int i = tid; i < 2 * (16 - Cout8) * 128; i += THREADS) {
+        const int buf = i / ((16 - Cout8) * 128), r = i % ((16 - Cout8) * 128);
+        *reinterpret_cast<uint4*>(gs + (size_t)buf * 16 * 128 * 16 + (size_t)(Cout8 * 128 + r) * 16) =
+            make_uint4(0u, 0u, 0u, 0u);
+    }
     if (tid == 0) {
         s_fail = 0;
-        mbar_init(smem_u32(bar), 1);
+        mbar_init(smem_u32(&bar[0]), 1);
+        mbar_init(smem_u32(&bar[1]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(WG_TMEM)
+                     "r"(WGZ_TMEM)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -399,76 +418,96 @@ __global__ void __launch_bounds__(THREADS) conv3_wgrad_tc_kernel(const bf16* __r
     __syncthreads();
     fence_after();
     const unsigned tmem = *tmem_slot;
-    // both operands MN-major (bits 15, 16), M = 128, N = CG
-    const uint32_t idesc = instr_desc(CG) | (1u << 15) | (1u << 16);
-    const int tiles_x = vol.w / TILE_X, tiles_y = vol.h / TILE_Y;
-    int done = 0;                                  // tiles whose MMAs were committed
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        int b = tile;
-        const int tx = b % tiles_x; b /= tiles_x;
-        const int ty = b % tiles_y; b /= tiles_y;
-        const int z0 = b % vol.d;
-        const int n0 = b / vol.d;
-        const int x0 = tx * TILE_X, y0 = ty * TILE_Y;
-        // the previous tile's MMAs read the shared tiles
-        if (done > 0 && tid == 0 && !s_fail &&
-            !mbar_wait(smem_u32(bar), (unsigned)((done - 1) & 1)))
-            s_fail = 1;
-        __syncthreads();
-        if (s_fail) break;
-        for (int i = tid; i < 128 * Cout8; i += THREADS) {
-            const int v = i / Cout8, c8 = i - v * Cout8;
-            const long long gv = (((long long)n0 * vol.d + z0) * vol.h + y0 + v / TILE_X) * vol.w + x0 + v % TILE_X;
-            cp16(gs_s + (unsigned)((c8 * 128 + v) * 16), G + gv * Cout + c8 * 8, 16u);
-        }
-        for (int i = tid; i < HALO_VOX * CG8; i += THREADS) {
+    const uint32_t idesc = instr_desc(CG) | (1u << 15) | (1u << 16);   // both operands MN-major
+
+    // halo plane z (any z; outside the cell: zeros) into its ring slot
+    auto load_plane = [&](int z) {
+        const int slot = (z + RING) % RING;
+        const bool in = z >= 0 && z < vol.d;
+        for (int i = tid; i < PLANE * CG8; i += THREADS) {
             const int hv = i / CG8, c8 = i - hv * CG8;
-            const int xh = hv % HX, yh = (hv / HX) % HY, zz = hv / (HX * HY);
-            const int z = z0 + zz - 1;
+            const int xh = hv % HX, yh = hv / HX;
             int y = y0 + yh - 1, x = x0 + xh - 1;
             y = y < 0 ? y + vol.h : (y >= vol.h ? y - vol.h : y);
             x = x < 0 ? x + vol.w : (x >= vol.w ? x - vol.w : x);
-            const bool in = z >= 0 && z < vol.d;
             const long long v = (((long long)n0 * vol.d + (in ? z : 0)) * vol.h + y) * vol.w + x;
-            cp16(halo_s + (unsigned)((((c8 * HZ + zz) * HY + yh) * HX + xh) * 16),
+            cp16(ring_s + (unsigned)((((c8 * RING + slot) * HY + yh) * HX + xh) * 16),
                  X + v * Cin + g * CG + c8 * 8, in ? 16u : 0u);
         }
-        cp_commit();
+    };
+    auto load_g = [&](int z, int buf) {
+        for (int i = tid; i < 128 * Cout8; i += THREADS) {
+            const int v = i / Cout8, c8 = i - v * Cout8;
+            const long long gv = (((long long)n0 * vol.d + z) * vol.h + y0 + v / TILE_X) * vol.w + x0 + v % TILE_X;
+            cp16(gs_s + (unsigned)(buf * 16 * 128 * 16 + (c8 * 128 + v) * 16), G + gv * Cout + c8 * 8, 16u);
+        }
+    };
+    auto wait_tile = [&](int k) {                  // thread 0: tile k's MMAs are done
+        if (tid == 0 && !s_fail && !mbar_wait(smem_u32(&bar[k & 1]), (unsigned)((k >> 1) & 1))) s_fail = 1;
+    };
+
+    const int ntiles = ze - zb;
+    load_plane(zb - 1);
+    load_plane(zb);
+    load_plane(zb + 1);
+    load_g(zb, 0);
+    cp_commit();
+    int issued = 0;
+    for (int k = 0; k < ntiles; ++k) {
+        const int z = zb + k;
         cp_wait_all();
         fence_proxy_async();
         __syncthreads();
+        if (s_fail) break;
         if (tid == 0) {
             fence_after();
-            for (int k = 0; k < ntap; ++k) {
-                const int t = tap0 + k;
+            const unsigned gbuf = gs_s + (unsigned)((k & 1) * 16 * 128 * 16);
+            for (int j = 0; j < ntap; ++j) {
+                const int t = tap0 + j;
                 const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+                const int slot = (z + dz - 1 + RING) % RING;
                 for (int ks = 0; ks < 128 / 16; ++ks) {
-                    // K step ks: voxel rows 2ks and 2ks + 1 of the tile
-                    const uint64_t ad = smem_desc(gs_s + 2u * ks * 128u, 128u, 128u * 16u);
+                    // A: output gradient [co][voxels] (LBO = K step of 8 voxels, SBO = 8 channels)
+                    const uint64_t ad = smem_desc(gbuf + 2u * ks * 128u, 128u, 128u * 16u);
+                    // B: halo [ci][voxels] of the tap (LBO = next voxel row, SBO = next 8 channels)
                     const uint64_t bd = smem_desc(
-                        halo_s + (unsigned)(((dz * HY + dy + 2 * ks) * HX + dx) * 16), HX * 16, HALO_VOX * 16);
-                    mma_bf16(tmem + (unsigned)(k * CG), ad, bd, idesc, (done > 0 || ks > 0) ? 1u : 0u);
+                        ring_s + (unsigned)(((slot * HY + dy + 2 * ks) * HX + dx) * 16), HX * 16,
+                        RING * PLANE * 16);
+                    mma_bf16(tmem + (unsigned)(j * CG), ad, bd, idesc, (k > 0 || ks > 0) ? 1u : 0u);
                 }
             }
-            mma_commit(smem_u32(bar));
+            mma_commit(smem_u32(&bar[k & 1]));
         }
-        ++done;
+        issued = k + 1;
+        if (k + 1 < ntiles) {
+            // plane z + 2 replaces plane z - 2 and G buffer (k + 1) & 1 held
+            // tile k - 1: both wait for tile k - 1's MMAs
+            if (k >= 1) wait_tile(k - 1);
+            __syncthreads();
+            if (s_fail) break;
+            load_plane(z + 2);
+            load_g(z + 1, (k + 1) & 1);
+            cp_commit();
+        }
     }
-    if (done > 0 && tid == 0 && !mbar_wait(smem_u32(bar), (unsigned)((done - 1) & 1))) s_fail = 1;
-    if (done > 0 && tid == 0 && s_fail) mbar_wait(smem_u32(bar), (unsigned)((done - 1) & 1));
+    cp_wait_all();
+    if (issued > 0) {
+        wait_tile(issued - 1);
+        if (tid == 0 && s_fail) mbar_wait(smem_u32(&bar[(issued - 1) & 1]), (unsigned)(((issued - 1) >> 1) & 1));
+    }
     __syncthreads();
     fence_after();
     if (s_fail) {
-        atomicCAS(&g_tc_error, 0u, 1u);
-    } else if (done > 0) {
+        if (tid == 0) atomicCAS(&g_tc_error, 0u, 1u);
+    } else if (issued > 0) {
         // lane = output channel co (warp w: 32w .. 32w + 31), columns = ci
         const int co = warp * 32 + lane;
         const unsigned trow = tmem + ((unsigned)(warp * 32) << 16);
-        for (int k = 0; k < ntap; ++k) {
-            const int t = tap0 + k;
+        for (int j = 0; j < ntap; ++j) {
+            const int t = tap0 + j;
             for (int c0 = 0; c0 < CG; c0 += 16) {
                 float acc[16];
-                tmem_ld16(trow + (unsigned)(k * CG + c0), acc);
+                tmem_ld16(trow + (unsigned)(j * CG + c0), acc);
                 if (co < Cout) {
 #pragma unroll
                     for (int i = 0; i < 16; ++i)
@@ -480,12 +519,12 @@ __global__ void __launch_bounds__(THREADS) conv3_wgrad_tc_kernel(const bf16* __r
     fence_before();
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(WG_TMEM)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(WGZ_TMEM)
                      : "memory");
 }
 
-__host__ __device__ constexpr size_t wg_smem_bytes(int cg) {
-    return (size_t)16 * 128 * 16 + (size_t)HALO_VOX * cg * 2 + 64;
+__host__ __device__ constexpr size_t wgz_smem_bytes(int cg) {
+    return (size_t)4 * HY * HX * cg * 2 + (size_t)2 * 16 * 128 * 16 + 64;
 }
 
 // Weight slabs for the forward kernel from W [27][cin][cout].  The conv that
@@ -622,30 +661,32 @@ lbm_status lbm_nn_conv3d_wgrad_tc(const void* x, int cin, const void* g, int cou
     if (!x || !g || !dw || !lbm_nn_conv3d_wgrad_tc_supported(cin, cout, n, d, h, wdt)) return LBM_ERR_INVALID_ARG;
     const int cg = cin % 64 == 0 ? 64 : (cin % 32 == 0 ? 32 : 16);
     const Vol vol{n, d, h, wdt};
-    const long long tiles = (long long)(wdt / TILE_X) * (h / TILE_Y) * d * n;
-    if (tiles > 0x7fffffffLL) return LBM_ERR_INVALID_ARG;
-    const int taps_per_block = WG_TMEM / cg;
+    const int taps_per_block = std::min(27, WGZ_TMEM / cg);
     const int tap_groups = (27 + taps_per_block - 1) / taps_per_block;
     const int ci_groups = cin / cg;
     int n_sm = 152;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, 0);
-    // about two blocks per SM in all, each looping over its share of the tiles
-    long long chunks = (2LL * n_sm + tap_groups * ci_groups - 1) / (tap_groups * ci_groups);
-    if (chunks > tiles) chunks = tiles;
-    if (chunks < 1) chunks = 1;
-    const dim3 grid((unsigned)chunks, (unsigned)tap_groups, (unsigned)ci_groups);
-    const size_t smem = tmem_safe_smem(wg_smem_bytes(cg), WG_TMEM);
+    // columns of tiles; z split into chunks until there are about two waves
+    // of blocks (one block per SM: all 512 TMEM columns)
+    const long long columns = (long long)(wdt / TILE_X) * (h / TILE_Y) * n;
+    const long long per_z = columns * tap_groups * ci_groups;
+    int zchunk = d;
+    while (zchunk > 4 && per_z * ((d + zchunk - 1) / zchunk) < 2LL * n_sm) zchunk = (zchunk + 1) / 2;
+    const long long gx = columns * ((d + zchunk - 1) / zchunk);
+    if (gx > 0x7fffffffLL) return LBM_ERR_INVALID_ARG;
+    const dim3 grid((unsigned)gx, (unsigned)tap_groups, (unsigned)ci_groups);
+    const size_t smem = tmem_safe_smem(wgz_smem_bytes(cg), WGZ_TMEM);
     cudaStream_t st = (cudaStream_t)stream;
     const bf16* X = static_cast<const bf16*>(x);
     const bf16* G = static_cast<const bf16*>(g);
     cudaError_t e = cudaSuccess;
     auto go = [&](auto kern) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) kern<<<grid, THREADS, smem, st>>>(X, cin, G, cout, dw, vol, (int)tiles);
+        if (e == cudaSuccess) kern<<<grid, THREADS, smem, st>>>(X, cin, G, cout, dw, vol, zchunk, taps_per_block);
     };
-    if (cg == 64) go(conv3_wgrad_tc_kernel<64>);
-    else if (cg == 32) go(conv3_wgrad_tc_kernel<32>);
-    else go(conv3_wgrad_tc_kernel<16>);
+    if (cg == 64) go(conv3_wgrad_z_kernel<64>);
+    else if (cg == 32) go(conv3_wgrad_z_kernel<32>);
+    else go(conv3_wgrad_z_kernel<16>);
     if (e == cudaSuccess) e = cudaGetLastError();
     return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }

@@ -201,3 +201,34 @@ def test_batch_errors():
     B.add(np.zeros((4, 4, 4), np.uint8), I.isotropic(1.0)[None], 2)
     with pytest.raises(lbm.LBMError):
         B.solve(0, lbm.Solver.opts(check_every=5))
+
+
+def test_sweep_cells_batched_at_full_size_match_oracle():
+    """Config 3 in the launch configuration the bench times: the first four
+    cells of the seeded sweep (uneven sizes between 64^3 and 160x160x320)
+    along x, y and z in one batch with the autotuned plan, 20 iterations from
+    the linear start, every solve against the FP64 oracle on every voxel."""
+    import math
+
+    cells = I.braid_sweep_cells(4)
+    B = lbm.Batch()
+    solves = []
+    for c in cells:
+        with lbm.Solver(c["nx"], c["ny"], c["nz"]) as V:
+            V.set_geometry_braid(math.radians(c["g_deg"]),
+                                 I.braid_anchors(c["nx"], c["ny"], c["seed"], n_max=256), c["phi"])
+            ph = V.geometry()
+        lam = I.braid_tensors(c["g_deg"])
+        for axis in (0, 1, 2):
+            B.add(ph, lam, axis)
+            solves.append((ph, lam, axis))
+    info = B.solve(0, lbm.Solver.opts(tol=0.0, max_iters=20, check_every=20))
+    assert info.n_solves == 12
+    for i, (ph, lam, axis) in enumerate(solves):
+        r = B.result(i)
+        ref = O.Lattice(ph, lam, r.lattice_scale, axis, 0)
+        ref.init_linear()
+        ref.step(20)
+        assert np.max(np.abs(B.temperature(i) - ref.temperature())) <= 1e-5
+        assert r.k_eff == pytest.approx(ref.k_eff()[0], rel=1e-5)
+    B.close()
