@@ -10,8 +10,9 @@ collide-stream iterations in check intervals of K = 100 (each interval ends
 with an FP64 plane-flux / residual check and the k_eff finalize), launched as
 one CUDA graph with a device-side while condition.  FP32 plain iterations run
 two per launch (temporal blocking, identical results; --no-fuse: one).
-Metric: GLUPS (giga lattice updates per second).  The f buffers (2 x 117 MB) exceed the 129 MB
-L2, so no flush is needed between steps.
+Metric: GLUPS (giga lattice updates per second).  Each step is timed by its own
+CUDA events; between steps a 256 MB write (outside the timed region) evicts
+the 129 MB L2.
 
 `value`: device time (CUDA events on the solver's stream) with the state
 resident.  `e2e`: the same metric through the public C ABI with pinned host
@@ -48,13 +49,16 @@ NX, NY, NZ = 128, 128, 256
 G_DEG, PHI, SEED, NMAX = 30.0, 0.45, 42, 128
 K = 100
 ITERS = 1000
-BYTES_PER_LUP = {"f32": 57, "bf16": 29, "f16": 29}   # 7 values read + 7 written + 1 B phase id
+# the state is four stored fields per node (th and jhat / 2; the seven
+# populations follow from them exactly): 4 values read + 4 written + 1 B
+# phase id per update (a seven-population state would move 57 B in FP32)
+BYTES_PER_LUP = {"f32": 33, "bf16": 17, "f16": 17}
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
 # capture of this workload (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by (kernel, storage) and stamped with the SHA-256 prefix of the
 # kernel source it was taken on; a stamp that no longer matches the source
 # reports null instead of a stale figure.
-TRAFFIC = {("fused2", "f32"): (186.38e6, "f58b822989b3e90b")}   # mean of 3 launches
+TRAFFIC = {}
 KERNEL_SOURCE = os.path.join(ROOT, "paper_1503_08718_gb300", "csrc", "lbm_kernels.cuh")
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 WORKLOAD = (f"braid {NX}x{NY}x{NZ} g=30deg phi=0.45 seed=42, dT along z, periodic laterals, "
@@ -308,7 +312,7 @@ def config4_precision(lbm, I, stream, peak, with_oracle, iters=2000, n_check=20)
     """The 256x256x512 braid (35 deg, yarn fraction 0.50, seed 7), every axis,
     periodic laterals, FP32 / BF16 / FP16 storage: GLUPS over `iters`
     iterations, the dominant kernel's average launch time and roofline
-    fraction (57 or 29 B per update), and the k_eff error against the FP64
+    fraction (33 or 17 B per update), and the k_eff error against the FP64
     oracle after n_check iterations from the linear start."""
     n = (256, 256, 512)
     n_vox = n[0] * n[1] * n[2]
@@ -749,17 +753,24 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    # each step is bracketed by its own events; between steps (outside the
+    # timed region) a 256 MB write evicts the L2, so no step starts on data
+    # the previous one left there
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
     with ClockSampler(dev) as clk:
-        ev0.record(stream)
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 255)
+            evs[k][0].record(stream)
             info = one_step()
-        ev1.record(stream)
+            evs[k][1].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-    ms = ev0.elapsed_time(ev1)
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    del flush
     if ws > 1:
         torch.distributed.barrier()
     ms = replicas.max_over_ranks(ms, device=f"cuda:{dev}")
@@ -775,10 +786,10 @@ def run_ours(args):
     launches_per_step = (iters // K) * launches_per_interval + 2   # + permute, init
     # roofline of the dominant kernel: the fused two-step kernel in FP32,
     # else the single step.  Algorithmic bytes per launch follow the
-    # per-update figure (57 B/LUP FP32, 29 B/LUP 16-bit: 7 values read, 7
+    # per-update figure (33 B/LUP FP32, 17 B/LUP 16-bit: 4 fields read, 4
     # written, 1 B phase id) times the updates one launch performs
     # (voxels x 2 for the two-step kernel).  A two-step launch moves the state
-    # through HBM once (57 B per voxel for two updates), so its `frac` exceeds
+    # through HBM once (33 B per voxel for two updates), so its `frac` exceeds
     # 1 by construction; `frac_moved` divides the bytes it actually has to
     # move by the same time (its bandwidth efficiency).  Its average launch
     # time is measured with CUDA events on the solver's stream over a run of
@@ -899,7 +910,7 @@ def run_ours(args):
                        "storage": args.storage, "fuse": bool(args.fuse),
                        "launch": args.launch,
                        "yarns": used, "yarn_fraction": round(frac, 6),
-                       "l2": "inputs larger than L2 (f buffers 2 x 117 MB)",
+                       "l2": "flushed between steps (256 MB write outside the timed region)",
                        "parallelism": f"replicas{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,

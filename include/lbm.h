@@ -206,9 +206,10 @@ lbm_status lbm_get_temperature(lbm_ctx* c, float* host_out);
 lbm_status lbm_get_history(lbm_ctx* c, double* host_out, int max_entries, int* n_out);
 
 /* No counterpart in the paper (checkpoint and resume of the iteration).
- * Bytes of a snapshot of the current solve: its distributions, reference
- * frames, residual snapshot, control block, check history and last plane
- * fluxes.  0 without a started solve (or for NULL / a poisoned context). */
+ * Bytes of a snapshot of the current solve: its distributions (four stored
+ * fields per node, th = T - R(z) and jhat / 2, from which the seven
+ * post-collision populations follow exactly), reference frames, residual
+ * snapshot, control block, check history and last plane fluxes.  0 without a started solve (or for NULL / a poisoned context). */
 size_t lbm_state_bytes(const lbm_ctx* c);
 
 /* No counterpart in the paper.  Writes the snapshot of the current solve

@@ -304,8 +304,8 @@ Plan plan_solve(const Layout& L, int n_phases, size_t esize, int bpp, size_t bas
     Plan p;
     const size_t cells = (size_t)L.pitch * L.NY * L.NZ;
     size_t o = base;
-    p.off_f[0] = o; o = align256(o + 7 * cells * esize);
-    p.off_f[1] = o; o = align256(o + 7 * cells * esize);
+    p.off_f[0] = o; o = align256(o + lbm::kFields * cells * esize);
+    p.off_f[1] = o; o = align256(o + lbm::kFields * cells * esize);
     p.off_phase = o; o = align256(o + cells);
     p.off_tsnap = o; o = align256(o + cells * sizeof(float));
     p.off_ref = o; o = align256(o + 5 * (size_t)L.NZ * sizeof(float));

@@ -382,7 +382,7 @@ size_t ws_solve_bytes(int NX, int NY, int NZ, int storage) {
     const size_t pitch = (size_t)((NX + V - 1) / V * V);
     const size_t cells = pitch * NY * NZ;
     const size_t bpp = ((pitch / V) * NY + lbm::kThreads - 1) / lbm::kThreads;
-    return 2 * ws_round(7 * cells * esize) + ws_round(cells) + ws_round(sizeof(float) * cells) +
+    return 2 * ws_round(lbm::kFields * cells * esize) + ws_round(cells) + ws_round(sizeof(float) * cells) +
            ws_round(sizeof(float) * 5 * NZ) + ws_round(sizeof(int) * NZ) + ws_round(sizeof(float4) * 2 * 255) +
            ws_round(sizeof(double) * 4 * NZ * bpp) + ws_round(sizeof(double) * 3 * NZ);
 }
@@ -805,8 +805,8 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
     const long long cells = (long long)L.pitch * L.NY * L.NZ;
     lbm_status st;
     size_t cur = c->ws_static;              // workspace cursor (unused without a workspace)
-    if ((st = solve_buf(c, &cur, &c->d_f[0], (size_t)(7 * cells) * esize, &c->cap_f[0])) != LBM_OK) return st;
-    if ((st = solve_buf(c, &cur, &c->d_f[1], (size_t)(7 * cells) * esize, &c->cap_f[1])) != LBM_OK) return st;
+    if ((st = solve_buf(c, &cur, &c->d_f[0], (size_t)(lbm::kFields * cells) * esize, &c->cap_f[0])) != LBM_OK) return st;
+    if ((st = solve_buf(c, &cur, &c->d_f[1], (size_t)(lbm::kFields * cells) * esize, &c->cap_f[1])) != LBM_OK) return st;
     if ((st = solve_buf(c, &cur, &c->d_phase_c, (size_t)cells, &c->cap_phase_c)) != LBM_OK) return st;
     if ((st = solve_buf(c, &cur, &c->d_tsnap, (size_t)cells, &c->cap_tsnap)) != LBM_OK) return st;
     if ((st = solve_buf(c, &cur, &c->d_ref, (size_t)5 * L.NZ, &c->cap_ref)) != LBM_OK) return st;
@@ -1089,7 +1089,7 @@ lbm_status lbm_get_history(lbm_ctx* c, double* host_out, int max_entries, int* n
 namespace {
 
 struct StateHeader {
-    char magic[8];                         // "MRTLBMS1"
+    char magic[8];                         // "MRTLBMS2": four stored fields per node
     int32_t n[3], axis, lateral, fmt, NX, NY, NZ, pitch, check_every, pad;
     double s, t_hot, t_cold;
     int64_t f_bytes, cells;
@@ -1098,7 +1098,7 @@ struct StateHeader {
 size_t state_bytes(const lbm_ctx* c) {
     const size_t esize = c->fmt == LBM_STORE_F32 ? 4 : 2;
     const size_t cells = (size_t)c->pstride;
-    return sizeof(StateHeader) + 7 * cells * esize + sizeof(float) * 5 * (size_t)c->L.NZ +
+    return sizeof(StateHeader) + lbm::kFields * cells * esize + sizeof(float) * 5 * (size_t)c->L.NZ +
            sizeof(float) * cells + sizeof(Ctl) + sizeof(double) * 4 * kHistCap +
            sizeof(double) * (size_t)c->L.NZ;
 }
@@ -1106,7 +1106,7 @@ size_t state_bytes(const lbm_ctx* c) {
 StateHeader state_header(const lbm_ctx* c) {
     StateHeader h;
     std::memset(&h, 0, sizeof h);
-    std::memcpy(h.magic, "MRTLBMS1", 8);
+    std::memcpy(h.magic, "MRTLBMS2", 8);
     for (int i = 0; i < 3; ++i) h.n[i] = c->n[i];
     h.axis = c->axis;
     h.lateral = c->lateral;
@@ -1120,7 +1120,7 @@ StateHeader state_header(const lbm_ctx* c) {
     h.t_hot = c->opts.t_hot;
     h.t_cold = c->opts.t_cold;
     h.cells = c->pstride;
-    h.f_bytes = 7 * c->pstride * (c->fmt == LBM_STORE_F32 ? 4 : 2);
+    h.f_bytes = lbm::kFields * c->pstride * (c->fmt == LBM_STORE_F32 ? 4 : 2);
     return h;
 }
 

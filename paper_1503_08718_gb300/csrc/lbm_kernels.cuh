@@ -1,19 +1,28 @@
 // Device kernels of the D3Q7 MRT lattice Boltzmann hot path for sm_103a.
 //
-// Storage: structure of arrays f[i][z][y][x] (population-major), FP32, BF16 or
-// FP16, two buffers (pull scheme: read the previous post-collision state,
-// write the next one).  The Dirichlet axis is always the slowest index z; the
-// host lays the cell out that way.  Rows are padded to a multiple of V voxels
-// (pitch) so that every thread moves one aligned 16-byte vector per
-// population (V = 4 FP32 or 8 16-bit values).
-// Values are stored as deviations g_i = f_i - w_i R(z), w_0 = 1/4,
-// w_1..6 = 1/8 (Eq. 6 with gamma = 1/8), from a per-plane reference
-// temperature R(z): the plane mean of T at the previous check, quantised to a
-// power-of-two grid so that every frame-change constant w_i (R(z') - R(z)) is
-// exact in FP32.  The map is linear, so the frame changes nothing in exact
-// arithmetic; in FP32 the stored values are small (non-equilibrium parts and
-// in-plane temperature variation), which shrinks the rounding of the stored
-// state and with it the FP32 error of the converged fixed point.
+// Storage: the post-collision state of every node lies in a four-dimensional
+// subspace (see the collision below: fhat_0 = T / 4, fhat_{2k-1,2k} = T / 8 +-
+// jhat_k / 2), so the state is stored as four fields per node, th = T - R(z)
+// and m = jhat / 2, not seven populations: structure of arrays
+// [field][z][y][x], FP32, BF16 or FP16, two buffers (pull scheme: read the
+// previous post-collision state, write the next one).  A node rebuilds each
+// population it pulls from its source node's fields (f_{2k-1} = th / 8 + m_k,
+// f_{2k} = th / 8 - m_k, f_0 = th / 4); the scalings by 1/8 and 1/4 are exact,
+// so in FP32 the pulled values are the very populations a seven-field state
+// would have stored, while a step moves 16 instead of 28 bytes per node.  The
+// Dirichlet axis is always the slowest index z; the host lays the cell out
+// that way.  Rows are padded to a multiple of V voxels (pitch) so that every
+// thread moves one aligned 16-byte vector per field (V = 4 FP32 or 8 16-bit
+// values).
+// The temperature is stored as the deviation th = T - R(z) from a per-plane
+// reference temperature R(z) (populations g_i = f_i - w_i R(z), w_0 = 1/4,
+// w_1..6 = 1/8, Eq. 6 with gamma = 1/8): the plane mean of T at the previous
+// check, quantised to a power-of-two grid so that every frame-change constant
+// w_i (R(z') - R(z)) is exact in FP32.  The map is linear, so the frame
+// changes nothing in exact arithmetic; in FP32 the stored values are small
+// (non-equilibrium parts and in-plane temperature variation), which shrinks
+// the rounding of the stored state and with it the FP32 error of the
+// converged fixed point.
 //
 // Collision (Eq. 5, 8-13).  With tau_0 = tau_4 = tau_5 = tau_6 = 1 the
 // moments 0, 4, 5, 6 leave the collision at equilibrium and the flux moment
@@ -66,6 +75,7 @@ __device__ __forceinline__ T* dbg_ptr(T* p, T* base, long long count, int width,
 #endif
 
 constexpr int kThreads = 256;        // threads per step block
+constexpr int kFields = 4;           // stored fields per node: th, m_x, m_y, m_z
 constexpr unsigned kFull = 0xffffffffu;
 
 struct Ctl {
@@ -107,14 +117,14 @@ struct CheckArgs {
 };
 
 struct StepArgs {
-    const void* __restrict__ src;    // 7 populations, post-collision state n-1
-    void* __restrict__ dst;          // 7 populations, post-collision state n
+    const void* __restrict__ src;    // fields th, m_x, m_y, m_z of post-collision state n-1
+    void* __restrict__ dst;          // the fields of post-collision state n
     const uint8_t* __restrict__ phase;  // [nz][ny][pitch], padded with 0
     const float4* __restrict__ sb;   // 2 float4 per phase: (xx, yy, zz, yz), (xz, xy, -, -)
     float* __restrict__ tsnap;       // T - T_ref at the previous check, [nz][ny][pitch]
     const float* __restrict__ rsrc;  // reference R(z) of the src state, [nz]
     const float* __restrict__ rdst;  // reference R(z) of the dst state, [nz]
-    long long pstride;               // elements per population = pitch * ny * nz
+    long long pstride;               // elements per field = pitch * ny * nz
     int nx, ny, nz, pitch, n_phases;
     int quads_per_plane;             // (pitch / V) * ny vectors per plane
     int blocks_per_plane;
@@ -277,12 +287,13 @@ __device__ void close_plane(const StepArgs& a, int z) {
 
 // The collision of one node (Eq. 5, 8-13 in the reduced form above) from its
 // seven pulled values relative to R_src, with the frame constants kT, kJ and
-// the phase's table entry (sa, sc) = B (BTAB) or S_b; returns the seven
-// post-collision values relative to R_dst, th = T - R_dst and q_z, the flux
-// along z (Eq. 16).  Every step kernel uses this one function.
+// the phase's table entry (sa, sc) = B (BTAB) or S_b; returns the fields the
+// state stores, th = T - R_dst and m = jhat / 2, and q_z, the flux along z
+// (Eq. 16).  Every step kernel uses this one function.
 struct Collided {
-    float o[7];
-    float th, qz;
+    float th;
+    float m[3];
+    float qz;
 };
 
 // host side of the table: the entry of one phase from S_b (FP64, 3x3 row-major)
@@ -309,28 +320,26 @@ __device__ __forceinline__ Collided collide_node(float g0, float g1, float g2, f
     const float ax = fmaf(sa.x, jx, fmaf(sc.y, jy, sc.x * jz));
     const float ay = fmaf(sc.y, jx, fmaf(sa.y, jy, sa.w * jz));
     const float az = fmaf(sc.x, jx, fmaf(sa.w, jy, sa.z * jz));
-    const float t8 = 0.125f * c.th;
-    c.o[0] = 0.25f * c.th;
     if (BTAB) {                          // a = B j = jhat / 2
-        c.o[1] = t8 + ax;
-        c.o[2] = t8 - ax;
-        c.o[3] = t8 + ay;
-        c.o[4] = t8 - ay;
-        c.o[5] = t8 + az;
-        c.o[6] = t8 - az;
+        c.m[0] = ax;
+        c.m[1] = ay;
+        c.m[2] = az;
         c.qz = fmaf(0.5f, jz, az);      // j_z / 2 + (B j)_z
     } else {                             // a = S_b j, jhat = j - a
-        const float hx = jx - ax, hy = jy - ay, hz = jz - az;
-        c.o[1] = fmaf(0.5f, hx, t8);
-        c.o[2] = fmaf(-0.5f, hx, t8);
-        c.o[3] = fmaf(0.5f, hy, t8);
-        c.o[4] = fmaf(-0.5f, hy, t8);
-        c.o[5] = fmaf(0.5f, hz, t8);
-        c.o[6] = fmaf(-0.5f, hz, t8);
+        c.m[0] = 0.5f * (jx - ax);
+        c.m[1] = 0.5f * (jy - ay);
+        c.m[2] = 0.5f * (jz - az);
         c.qz = fmaf(-0.5f, az, jz);     // (j_z + jhat_z) / 2
     }
     return c;
 }
+
+// A post-collision population from the stored fields of the node it leaves:
+// f_{2k-1} = th / 8 + m_k (pull_p) and f_{2k} = th / 8 - m_k (pull_m), the
+// rest population f_0 = th / 4.  The scalings are exact, so each value is
+// the population the collision would have stored, rounded once.
+__device__ __forceinline__ float pull_p(float th, float m) { return fmaf(0.125f, th, m); }
+__device__ __forceinline__ float pull_m(float th, float m) { return fmaf(0.125f, th, -m); }
 
 // Frame constants of plane z for a step from frame R_src to R_dst (see the
 // step kernel): kT is added to the sum of the pulled values, kJ to j_z.
@@ -355,8 +364,8 @@ __device__ __forceinline__ PlaneK plane_consts(const float* rsrc, const float* r
 }
 
 // Storage policies.  FP32 moves 4 voxels per thread as one float4 per
-// population; BF16 and FP16 move 8 voxels per thread as one uint4 (eight
-// 16-bit values) per population, converted to FP32 for the collision and
+// field; BF16 and FP16 move 8 voxels per thread as one uint4 (eight 16-bit
+// values) per field, converted to FP32 for the collision and
 // rounded back stochastically (cvt.rs: the rounding direction is drawn with
 // probability proportional to the distance to each neighbour, so the stored
 // value is unbiased and updates below half an ulp are not lost on average).
@@ -438,6 +447,9 @@ template <> struct Pol<2> : Pol16<2> {};
 // the adjacent lanes (warp shuffles) except at warp and row boundaries, where
 // a scalar load or a face rule supplies them.  RAGGED: nx is not a multiple
 // of V, so the last vector of a row holds padding.
+// A node pulls f_i from its neighbour at -e_i, rebuilt from that node's
+// stored fields: th and m_x of the x-neighbours, th and m_y of the
+// y-neighbours, th and m_z of the z-neighbours, th of the own node.
 template <int FMT, bool PERIODIC, bool CHECK, bool RAGGED, int THREADS>
 __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const int z,
                                           const unsigned rseed) {
@@ -457,32 +469,35 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
     const int x0 = qx * V;
     const int lane = threadIdx.x & 31;
     const long long P = a.pstride;
+    const long long PL = (long long)a.ny * a.pitch;
     const T* __restrict__ src = reinterpret_cast<const T*>(a.src);
+    constexpr int NF = kFields;
 
     const long long row = ((long long)z * a.ny + y) * a.pitch;
-    // y-neighbour rows: periodic wrap (Eq. 25) or bounce-back into the own node (Eq. 24)
+    // y-neighbour rows: periodic wrap (Eq. 25), or the own node at an
+    // adiabatic face (bounce-back, Eq. 24: m_y enters with the other sign)
     const bool ylo = (y == 0), yhi = (y == a.ny - 1);
     const bool zlo = (z == 0), zhi = (z == a.nz - 1);
-    const long long rym = PERIODIC ? ((long long)z * a.ny + (ylo ? a.ny - 1 : y - 1)) * a.pitch
-                                   : (ylo ? row + 4 * P : row - a.pitch + 3 * P);
-    const long long ryp = PERIODIC ? ((long long)z * a.ny + (yhi ? 0 : y + 1)) * a.pitch
-                                   : (yhi ? row + 3 * P : row + a.pitch + 4 * P);
-    const long long o3 = PERIODIC ? rym + 3 * P : rym;
-    const long long o4 = PERIODIC ? ryp + 4 * P : ryp;
-    // z-neighbour rows; the walls (Eq. 23) read the own node's opposite population
-    const long long o5 = zlo ? row + 6 * P : row - (long long)a.ny * a.pitch + 5 * P;
-    const long long o6 = zhi ? row + 5 * P : row + (long long)a.ny * a.pitch + 6 * P;
+    const long long rym = ylo ? (PERIODIC ? row + (long long)(a.ny - 1) * a.pitch : row) : row - a.pitch;
+    const long long ryp = yhi ? (PERIODIC ? row - (long long)(a.ny - 1) * a.pitch : row) : row + a.pitch;
+    // z-neighbour planes; the walls (Eq. 23) use the own node, th with the
+    // other sign (anti-bounce-back)
+    const long long rzm = zlo ? row : row - PL;
+    const long long rzp = zhi ? row : row + PL;
 
-    Raw c0 = S::zero(), c1 = c0, c2 = c0, c3 = c0, c4 = c0, c5 = c0, c6 = c0;
+    Raw cT = S::zero(), cX = cT, mT = cT, mY = cT, pT = cT, pY = cT, dT = cT, dZ = cT, uT = cT, uZ = cT;
     uint2 ph = make_uint2(0u, 0u);
     if (active) {
-        c0 = S::load(LBM_CK(src + row + x0, src, 7 * P, V, 1u));
-        c1 = S::load(LBM_CK(src + P + row + x0, src, 7 * P, V, 1u));
-        c2 = S::load(LBM_CK(src + 2 * P + row + x0, src, 7 * P, V, 1u));
-        c3 = S::load(LBM_CK(src + o3 + x0, src, 7 * P, V, 1u));
-        c4 = S::load(LBM_CK(src + o4 + x0, src, 7 * P, V, 1u));
-        c5 = S::load(LBM_CK(src + o5 + x0, src, 7 * P, V, 1u));
-        c6 = S::load(LBM_CK(src + o6 + x0, src, 7 * P, V, 1u));
+        cT = S::load(LBM_CK(src + row + x0, src, NF * P, V, 1u));
+        cX = S::load(LBM_CK(src + P + row + x0, src, NF * P, V, 1u));
+        mT = S::load(LBM_CK(src + rym + x0, src, NF * P, V, 1u));
+        mY = S::load(LBM_CK(src + 2 * P + rym + x0, src, NF * P, V, 1u));
+        pT = S::load(LBM_CK(src + ryp + x0, src, NF * P, V, 1u));
+        pY = S::load(LBM_CK(src + 2 * P + ryp + x0, src, NF * P, V, 1u));
+        dT = S::load(LBM_CK(src + rzm + x0, src, NF * P, V, 1u));
+        dZ = S::load(LBM_CK(src + 3 * P + rzm + x0, src, NF * P, V, 1u));
+        uT = S::load(LBM_CK(src + rzp + x0, src, NF * P, V, 1u));
+        uZ = S::load(LBM_CK(src + 3 * P + rzp + x0, src, NF * P, V, 1u));
         if (V == 8) ph = __ldg(reinterpret_cast<const uint2*>(LBM_CK(a.phase + row + x0, a.phase, P, V, 2u)));
         else ph.x = __ldg(reinterpret_cast<const unsigned*>(LBM_CK(a.phase + row + x0, a.phase, P, V, 2u)));
     }
@@ -491,25 +506,48 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
     const PlaneK pk = plane_consts(a.rsrc, a.rdst, z, a.nz, a.eps_hot, a.eps_cold);
     const float kT = pk.kT, kJ = pk.kJ;
     const float rd = a.rdst[z];
-    if (zlo) c5 = S::neg(c5);
-    if (zhi) c6 = S::neg(c6);
-    // x-neighbours: f1 comes from x - 1, f2 from x + 1.
-    const float left1 = __shfl_up_sync(kFull, S::get(c1, V - 1), 1);
-    const float right2 = __shfl_down_sync(kFull, S::get(c2, 0), 1);
-    float f1_0, f2_last;
-    if (lane > 0 && qx > 0) f1_0 = left1;
-    else if (qx > 0) f1_0 = active ? S::scalar(LBM_CK(src + P + row + x0 - 1, src, 7 * P, 1, 3u)) : 0.f;
-    else f1_0 = PERIODIC ? (active ? S::scalar(LBM_CK(src + P + row + a.nx - 1, src, 7 * P, 1, 3u)) : 0.f)
-                         : S::get(c2, 0);
+    if (zlo) dT = S::neg(dT);
+    if (zhi) uT = S::neg(uT);
+    if (!PERIODIC && ylo) mY = S::neg(mY);
+    if (!PERIODIC && yhi) pY = S::neg(pY);
+    // x-neighbours: f1 comes from x - 1, f2 from x + 1 (th and m_x of each)
+    const float lT = __shfl_up_sync(kFull, S::get(cT, V - 1), 1);
+    const float lX = __shfl_up_sync(kFull, S::get(cX, V - 1), 1);
+    const float rT = __shfl_down_sync(kFull, S::get(cT, 0), 1);
+    const float rX = __shfl_down_sync(kFull, S::get(cX, 0), 1);
+    float TL, XL, TR, XR;
+    if (lane > 0 && qx > 0) {
+        TL = lT;
+        XL = lX;
+    } else if (qx > 0 || PERIODIC) {
+        const long long xl = qx > 0 ? row + x0 - 1 : row + a.nx - 1;
+        TL = active ? S::scalar(LBM_CK(src + xl, src, NF * P, 1, 3u)) : 0.f;
+        XL = active ? S::scalar(LBM_CK(src + P + xl, src, NF * P, 1, 3u)) : 0.f;
+    } else {                                      // Eq. 24 at x = 0: f1 = f2 of the own node
+        TL = S::get(cT, 0);
+        XL = -S::get(cX, 0);
+    }
     // the last real voxel of the row sits in the row's last vector, at e_last
     const int e_last = (RAGGED && qx == nq - 1) ? a.nx - 1 - x0 : V;
-    float edge2 = 0.f;
+    float eT = 0.f, eX = 0.f;
     if (qx < nq - 1) {
-        f2_last = (lane < 31) ? right2 : (active ? S::scalar(LBM_CK(src + 2 * P + row + x0 + V, src, 7 * P, 1, 3u)) : 0.f);
+        if (lane < 31) {
+            TR = rT;
+            XR = rX;
+        } else {
+            TR = active ? S::scalar(LBM_CK(src + row + x0 + V, src, NF * P, 1, 3u)) : 0.f;
+            XR = active ? S::scalar(LBM_CK(src + P + row + x0 + V, src, NF * P, 1, 3u)) : 0.f;
+        }
     } else {
-        edge2 = PERIODIC ? (active ? S::scalar(LBM_CK(src + 2 * P + row, src, 7 * P, 1, 3u)) : 0.f) : S::get(c1, V - 1);
-        f2_last = RAGGED ? 0.f : edge2;
-        if (RAGGED && !PERIODIC) edge2 = 0.f;
+        if (PERIODIC) {                           // the row's first node
+            eT = active ? S::scalar(LBM_CK(src + row, src, NF * P, 1, 3u)) : 0.f;
+            eX = active ? S::scalar(LBM_CK(src + P + row, src, NF * P, 1, 3u)) : 0.f;
+        } else {                                  // Eq. 24 at x = nx - 1: f2 = f1 of the own node
+            eT = S::get(cT, V - 1);
+            eX = -S::get(cX, V - 1);
+        }
+        TR = RAGGED ? 0.f : eT;
+        XR = RAGGED ? 0.f : eX;
     }
 
     const int n_real = active ? min(V, a.nx - x0) : 0;
@@ -528,23 +566,25 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
     }
     const float dref = (float)((double)rd - a.t_ref);
     const float tref = (float)a.t_ref;
-    float o[7][V];
+    float o[NF][V];
 #pragma unroll
     for (int k = 0; k < V; ++k) {
-        const float g0 = S::get(c0, k);
-        const float g1 = k == 0 ? f1_0 : S::get(c1, k - 1);
-        float g2 = k == V - 1 ? f2_last : S::get(c2, k + 1);
-        if (RAGGED && k == e_last) g2 = PERIODIC ? edge2 : S::get(c1, k);
-        const float g3 = S::get(c3, k), g4 = S::get(c4, k);
-        const float g5 = S::get(c5, k), g6 = S::get(c6, k);
+        const float g0 = 0.25f * S::get(cT, k);
+        const float g1 = k == 0 ? pull_p(TL, XL) : pull_p(S::get(cT, k - 1), S::get(cX, k - 1));
+        float g2 = k == V - 1 ? pull_m(TR, XR) : pull_m(S::get(cT, k + 1), S::get(cX, k + 1));
+        if (RAGGED && k == e_last) g2 = PERIODIC ? pull_m(eT, eX) : pull_p(S::get(cT, k), S::get(cX, k));
+        const float g3 = pull_p(S::get(mT, k), S::get(mY, k)), g4 = pull_m(S::get(pT, k), S::get(pY, k));
+        const float g5 = pull_p(S::get(dT, k), S::get(dZ, k)), g6 = pull_m(S::get(uT, k), S::get(uZ, k));
         const int p = (k < 4 ? (ph.x >> (8 * k)) : (ph.y >> (8 * (k - 4)))) & 0xff;
         const float4 sa = s_sb[2 * p];
         const float4 sc = s_sb[2 * p + 1];
         const Collided cc = collide_node<FMT == 0>(g0, g1, g2, g3, g4, g5, g6, sa, sc, kT, kJ);
         const float th = cc.th;
         const bool real = RAGGED ? k < n_real : active;   // n_real is 0 for inactive threads
-#pragma unroll
-        for (int i = 0; i < 7; ++i) o[i][k] = cc.o[i];
+        o[0][k] = th;
+        o[1][k] = cc.m[0];
+        o[2][k] = cc.m[1];
+        o[3][k] = cc.m[2];
         if (CHECK) {
             const float tdev = th + dref;                    // T - T_ref
             thv[k] = tdev;
@@ -562,22 +602,22 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
         for (int k = 0; k < V; ++k)
             if (k >= n_real) {
 #pragma unroll
-                for (int i = 0; i < 7; ++i) o[i][k] = 0.f;
+                for (int i = 0; i < NF; ++i) o[i][k] = 0.f;
                 if (CHECK) thv[k] = 0.f;
             }
     }
     if (active) {
         T* __restrict__ dst = reinterpret_cast<T*>(a.dst) + row + x0;
         // random bits for stochastic rounding: a hash of the element's
-        // position and population, salted by the iteration and the launch
+        // position and field, salted by the iteration and the launch
         unsigned key = 0u;
         if (FMT != 0) {
             const unsigned seed = hash32((unsigned)__ldcg(&a.ck.ctl->iter) * 0x9E3779B9u + rseed);
             key = seed ^ (unsigned)((row + x0) >> 1) * 0x85ebca6bu;
         }
 #pragma unroll
-        for (int i = 0; i < 7; ++i)
-            S::store(LBM_CK(dst + i * P, reinterpret_cast<T*>(a.dst), 7 * P, V, 5u), o[i], key + 0x9E3779B9u * (unsigned)i);
+        for (int i = 0; i < NF; ++i)
+            S::store(LBM_CK(dst + i * P, reinterpret_cast<T*>(a.dst), NF * P, V, 5u), o[i], key + 0x9E3779B9u * (unsigned)i);
         if (CHECK) {
 #pragma unroll
             for (int v4 = 0; v4 < V / 4; ++v4)
@@ -630,7 +670,7 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
 // full x extent (each thread 4 consecutive nodes, nq = nx / 4 threads per
 // row) and marches through a chunk of planes.  Block row r = 0 .. FY + 1 is
 // grid row y0 - 1 + r: rows 1 .. FY are the tile, rows 0 and FY + 1 the halo
-// whose populations 3 and 4 the tile's second step pulls.  The last tile of a
+// whose th and m_y the tile's second step pulls (populations 3 and 4).  The last tile of a
 // cell whose ny is not a multiple of FY has fyb < FY rows; its halo is block
 // row fyb + 1 and the rows after it idle.  Threads past (FY + 2) nq idle too
 // (a batch launches every block with the same size).
@@ -641,7 +681,6 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
 // in flight while it runs.  Every node's arithmetic is the single step's
 // (collide_node), so two fused steps equal two single steps bit for bit.
 // Step n runs from frame rsrc to rdst, step n + 1 within rdst.
-constexpr int F2_PF = 1;                           // L2 prefetch distance in planes
 constexpr int F2_MAX_THREADS = 640;
 
 // Kernel variants: rows of 128 nodes (tuned: 8-row tiles, 320 threads, two
@@ -652,10 +691,10 @@ __host__ __device__ constexpr int f2_bound_threads(int nxc) { return nxc == 128 
 __host__ __device__ constexpr int f2_fixed_fy(int nxc) { return 8; }   // tile rows of the tuned variants
 __host__ __device__ constexpr int f2_bound_blocks(int nxc) { return nxc == 128 ? 2 : 1; }
 
-// A ring plane keeps, per population, only the rows the second step reads:
-// the FY tile rows for 0, 1, 2, 5, 6; block rows 0 .. FY for 3 and 1 .. FY + 1
-// for 4 (the halo row and, at an adiabatic face, the own row's bounce-back).
-__host__ __device__ constexpr int f2_slot_rows(int fy) { return 7 * fy + 2; }
+// A ring plane keeps, per field, only the rows the second step reads: th and
+// m_y for block rows 0 .. FY + 1 (the y-neighbours of the tile rows), m_x and
+// m_z for the FY tile rows.
+__host__ __device__ constexpr int f2_slot_rows(int fy) { return 4 * fy + 4; }
 __host__ __device__ constexpr size_t fused2_smem_bytes(int nx, int fy, int n_phases) {
     return sizeof(float) * 3 * (size_t)f2_slot_rows(fy) * nx + (sizeof(float4) + sizeof(float2)) * n_phases;
 }
@@ -665,26 +704,35 @@ __device__ __forceinline__ float f4get(const float4& v, int k) {
     return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
 }
 
-// Step at 4 nodes from pulled values: g1 = (l1, c1.x, c1.y, c1.z) and
-// g2 = (c2.y, c2.z, c2.w, r2) are assembled by the caller.
-struct Quad7 {
-    float4 o[7];
+// Step at 4 nodes of a row from the stored fields around them: th and m_x of
+// the row (cT, cX) with the nodes left (lT, lX) and right (rT, rX) of it, th
+// and m_y of the rows below (mT, mY) and above (pT, pY), th and m_z of the
+// planes below (dT, dZ) and above (uT, uZ), faces already applied.
+struct Quad4 {
+    float4 o[kFields];                             // th, m_x, m_y, m_z of the 4 nodes
 };
-__device__ __forceinline__ Quad7 collide_quad(const float4& g0, const float4& g1, const float4& g2,
-                                              const float4& g3, const float4& g4, const float4& g5,
-                                              const float4& g6, unsigned phw, const float4* s_sa,
-                                              const float2* s_sc, float kT, float kJ) {
-    Quad7 q;
+__device__ __forceinline__ Quad4 collide_quad(const float4& cT, const float4& cX, float lT, float lX, float rT,
+                                              float rX, const float4& mT, const float4& mY, const float4& pT,
+                                              const float4& pY, const float4& dT, const float4& dZ,
+                                              const float4& uT, const float4& uZ, unsigned phw,
+                                              const float4* s_sa, const float2* s_sc, float kT, float kJ) {
+    Quad4 q;
     float* o = reinterpret_cast<float*>(q.o);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int ph = (phw >> (8 * k)) & 255u;
         const float2 sc = s_sc[ph];
-        const Collided c = collide_node<true>(f4get(g0, k), f4get(g1, k), f4get(g2, k), f4get(g3, k),
-                                        f4get(g4, k), f4get(g5, k), f4get(g6, k), s_sa[ph],
-                                        make_float4(sc.x, sc.y, 0.f, 0.f), kT, kJ);
-#pragma unroll
-        for (int i = 0; i < 7; ++i) o[4 * i + k] = c.o[i];
+        const float g0 = 0.25f * f4get(cT, k);
+        const float g1 = k == 0 ? pull_p(lT, lX) : pull_p(f4get(cT, k - 1), f4get(cX, k - 1));
+        const float g2 = k == 3 ? pull_m(rT, rX) : pull_m(f4get(cT, k + 1), f4get(cX, k + 1));
+        const Collided c = collide_node<true>(g0, g1, g2, pull_p(f4get(mT, k), f4get(mY, k)),
+                                              pull_m(f4get(pT, k), f4get(pY, k)), pull_p(f4get(dT, k), f4get(dZ, k)),
+                                              pull_m(f4get(uT, k), f4get(uZ, k)), s_sa[ph],
+                                              make_float4(sc.x, sc.y, 0.f, 0.f), kT, kJ);
+        o[k] = c.th;
+        o[4 + k] = c.m[0];
+        o[8 + k] = c.m[1];
+        o[12 + k] = c.m[2];
     }
     return q;
 }
@@ -721,10 +769,10 @@ __device__ __forceinline__ void fused2_body(const StepArgs& a, float* fn, const 
     // warp whose row has no work skips the step (shuffles included)
     constexpr bool WR = NXC > 0 && NXC % 128 == 0;
     const int RS = f2_slot_rows(FY) * NXB;         // floats per ring plane
-    // population offsets within a ring plane, for block row r at row r - 1:
-    // population 3 keeps block rows 0 .. FY, population 4 rows 1 .. FY + 1
-    const int Q1 = FY * NXB, Q2 = 2 * FY * NXB, Q5 = 3 * FY * NXB, Q6 = 4 * FY * NXB;
-    const int Q3 = (5 * FY + 1) * NXB, Q4 = (6 * FY + 1) * NXB;
+    // field offsets within a ring plane, relative to own = (r - 1) NXB + x of
+    // block row r: th and m_y keep block rows 0 .. FY + 1, m_x and m_z rows
+    // 1 .. FY
+    const int QT = NXB, QY = (FY + 3) * NXB, QX = 2 * (FY + 2) * NXB, QZ = (3 * FY + 4) * NXB;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int r = tid / nq;                        // block row
@@ -749,12 +797,10 @@ __device__ __forceinline__ void fused2_body(const StepArgs& a, float* fn, const 
     const long long P = a.pstride;
     const long long PL = (long long)ny * pitch;
     const long long yrow = (long long)y * pitch;
-    // rows pulled for populations 3 and 4: the neighbour row, or the own
-    // node's opposite population at an adiabatic face (Eq. 24)
-    const long long o3 = PERIODIC ? 3 * P + (long long)(ylo ? ny - 1 : y - 1) * pitch
-                                  : (ylo ? 4 * P + yrow : 3 * P + yrow - pitch);
-    const long long o4 = PERIODIC ? 4 * P + (long long)(yhi ? 0 : y + 1) * pitch
-                                  : (yhi ? 3 * P + yrow : 4 * P + yrow + pitch);
+    // y-neighbour rows of the first step: the wrapped neighbour, or the own
+    // row at an adiabatic face (Eq. 24, m_y with the other sign)
+    const long long rym = ylo ? (PERIODIC ? yrow + (long long)(ny - 1) * pitch : yrow) : yrow - pitch;
+    const long long ryp = yhi ? (PERIODIC ? yrow - (long long)(ny - 1) * pitch : yrow) : yrow + pitch;
     const float* __restrict__ src = reinterpret_cast<const float*>(a.src);
     float* __restrict__ dst = reinterpret_cast<float*>(a.dst);
     const int z0 = bz * zchunk;
@@ -777,26 +823,32 @@ __device__ __forceinline__ void fused2_body(const StepArgs& a, float* fn, const 
     if (tid == 0) plane_pair(0, s_kc[0]);
     __syncthreads();                               // the B tables and s_kc[0] are ready
 
-    // L2 prefetch, F2_PF planes ahead: threads 0..7 of each row each fetch one
-    // population's row (what the first step at that plane pulls) or the
-    // phase bytes, by one bulk prefetch
-    const int q = x >> 2;
-    const int pf_k = q;                            // what this thread prefetches (< 8)
+    // L2 prefetch two planes ahead: lanes 0..4 of the block's last warp each
+    // fetch, by one bulk prefetch, one field's rows that the tile's first
+    // step reads there (th and m_y with the rows on either side, m_x and m_z
+    // the block rows, clamped to the cell) or the phase bytes.  Plane i + 2
+    // is read as the upper z-neighbour at the next iteration.  A bulk
+    // prefetch takes its operands from uniform registers, so lanes with
+    // different addresses are served one after another: one warp per block
+    // keeps that loop short.
+    const int pf_k = lane;                         // what this lane prefetches (< 5)
     const char* pf_base = nullptr;
     long long pf_plane = 4 * PL;                   // bytes per plane
-    unsigned pf_bytes = 4u * NXB;
+    unsigned pf_bytes = 0u;
     {
-        const long long off = pf_k == 0 ? yrow : pf_k == 1 ? P + yrow : pf_k == 2 ? 2 * P + yrow
-                            : pf_k == 3 ? o3 : pf_k == 4 ? o4 : pf_k == 5 ? 5 * P - PL + yrow
-                            : 6 * P + PL + yrow;
-        pf_base = reinterpret_cast<const char*>(src + off);
-        if (pf_k == 7) {
-            pf_base = reinterpret_cast<const char*>(a.phase + yrow);
+        const int wide = (pf_k == 0 || pf_k == 2) ? 1 : 0;
+        const int ya = max(y0 - 1 - wide, 0), yb = min(y0 + fyb + wide, ny - 1);
+        const long long off = pf_k == 0 ? 0 : pf_k == 1 ? P : pf_k == 2 ? 2 * P : 3 * P;
+        pf_base = reinterpret_cast<const char*>(src + off + (long long)ya * pitch);
+        pf_bytes = yb >= ya ? 4u * (unsigned)((yb - ya + 1) * pitch) : 0u;
+        if (pf_k == 4) {
+            pf_base = reinterpret_cast<const char*>(a.phase + (long long)ya * pitch);
             pf_plane = PL;
-            pf_bytes = NXB;
+            pf_bytes /= 4u;
         }
     }
-    const bool pf_lane = row_in && pf_k < 8 && (pf_k != 7 || (NXB & 15) == 0);
+    const bool pf_lane = (tid >> 5) == ((int)blockDim.x >> 5) - 1 && pf_k < 5 && pf_bytes > 0u &&
+                         (pf_k != 4 || (pitch & 15) == 0);
     unsigned phA = 0u, phB = 0u;                   // phase words of planes i - 2dz and i - dz
     // ring slot of plane p: p mod 3.  si tracks plane i; planes j, j - 1 and
     // j + 1 then sit in slots si + 1, si, si + 2 (up) or si + 2, si + 1, si
@@ -812,33 +864,34 @@ __device__ __forceinline__ void fused2_body(const StepArgs& a, float* fn, const 
         const PlaneK kn = s_kc[t & 1][0], kn1 = s_kc[t & 1][1];
         if (tid == 0) plane_pair(t + 1, s_kc[(t + 1) & 1]);   // read after this iteration's barrier
         {
-            const int ip = i + F2_PF * dz;
-            // the wall planes pull their own populations: nothing to prefetch there
-            if (pf_lane && ip >= z0 - 1 && ip <= z1 && ip >= 0 && ip < nz && (pf_k != 5 || ip > 0) &&
-                (pf_k != 6 || ip < nz - 1))
+            const int ip = i + 2 * dz;
+            if (pf_lane && ip >= max(z0 - 2, 0) && ip <= min(z1 + 1, nz - 1))
                 asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(pf_base + ip * pf_plane),
                              "r"(pf_bytes) : "memory");
         }
         // ---- loads of step n at plane i ----
         const bool first = i >= z0 - 1 && i <= z1 && i >= 0 && i < nz && row_in;
-        float4 q0, q1, q2, q3, q4, q5, q6;
+        float4 cT, cX, mT, mY, pT, pY, dT, dZ, uT, uZ;
         unsigned phC = 0u;
         if (first) {
             const float* s = src + (long long)i * PL;
-            q0 = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + yrow + x, src, 7 * P, 4, 11u)));
-            q1 = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + P + yrow + x, src, 7 * P, 4, 11u)));
-            q2 = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + 2 * P + yrow + x, src, 7 * P, 4, 11u)));
-            q3 = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + o3 + x, src, 7 * P, 4, 11u)));
-            q4 = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + o4 + x, src, 7 * P, 4, 11u)));
-            // the walls (Eq. 23) read the own node's opposite population
-            q5 = __ldg(reinterpret_cast<const float4*>(
-                LBM_CK(s + (i > 0 ? 5 * P - PL : 6 * P) + yrow + x, src, 7 * P, 4, 11u)));
-            q6 = __ldg(reinterpret_cast<const float4*>(
-                LBM_CK(s + (i < nz - 1 ? 6 * P + PL : 5 * P) + yrow + x, src, 7 * P, 4, 11u)));
+            const float* sd = s + (i > 0 ? -PL : 0);          // the walls (Eq. 23) use the own node
+            const float* su = s + (i < nz - 1 ? PL : 0);
+            const int NP = kFields;
+            cT = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + yrow + x, src, NP * P, 4, 11u)));
+            cX = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + P + yrow + x, src, NP * P, 4, 11u)));
+            mT = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + rym + x, src, NP * P, 4, 11u)));
+            mY = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + 2 * P + rym + x, src, NP * P, 4, 11u)));
+            pT = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + ryp + x, src, NP * P, 4, 11u)));
+            pY = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + 2 * P + ryp + x, src, NP * P, 4, 11u)));
+            dT = __ldg(reinterpret_cast<const float4*>(LBM_CK(sd + yrow + x, src, NP * P, 4, 11u)));
+            dZ = __ldg(reinterpret_cast<const float4*>(LBM_CK(sd + 3 * P + yrow + x, src, NP * P, 4, 11u)));
+            uT = __ldg(reinterpret_cast<const float4*>(LBM_CK(su + yrow + x, src, NP * P, 4, 11u)));
+            uZ = __ldg(reinterpret_cast<const float4*>(LBM_CK(su + 3 * P + yrow + x, src, NP * P, 4, 11u)));
             phC = __ldg(reinterpret_cast<const unsigned*>(
                 LBM_CK(a.phase + (long long)i * PL + yrow + x, a.phase, P, 4, 12u)));
         } else if (!WR) {
-            q0 = q1 = q2 = q3 = q4 = q5 = q6 = make_float4(0.f, 0.f, 0.f, 0.f);
+            cT = cX = mT = mY = pT = pY = dT = dZ = uT = uZ = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         // ---- step n + 1 at plane j, tile rows ----
         const int own = (r - 1) * NXB + x;          // this thread's nodes in a ring plane
@@ -847,68 +900,112 @@ __device__ __forceinline__ void fused2_body(const StepArgs& a, float* fn, const 
             const float* fs = fn + sj * RS + own;
             const float* fb = fn + sjm * RS + own;
             const float* fa = fn + sjp * RS + own;
-            float4 g0, c1, c2, g3, g4, g5, g6;
-            if (!WR && !second) g0 = c1 = c2 = g3 = g4 = g5 = g6 = make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 bT, bX, bmT, bmY, bpT, bpY, bdT, bdZ, buT, buZ;
+            if (!WR && !second)
+                bT = bX = bmT = bmY = bpT = bpY = bdT = bdZ = buT = buZ = make_float4(0.f, 0.f, 0.f, 0.f);
             if (WR || second) {
                 const float* rb = fn;
                 const int RN = 3 * RS;
-                g0 = *reinterpret_cast<const float4*>(LBM_CK(fs, rb, RN, 4, 15u));
-                c1 = *reinterpret_cast<const float4*>(LBM_CK(fs + Q1, rb, RN, 4, 15u));
-                c2 = *reinterpret_cast<const float4*>(LBM_CK(fs + Q2, rb, RN, 4, 15u));
-                g3 = (PERIODIC || !ylo) ? *reinterpret_cast<const float4*>(LBM_CK(fs + Q3 - NXB, rb, RN, 4, 15u))
-                                        : *reinterpret_cast<const float4*>(LBM_CK(fs + Q4, rb, RN, 4, 15u));
-                g4 = (PERIODIC || !yhi) ? *reinterpret_cast<const float4*>(LBM_CK(fs + Q4 + NXB, rb, RN, 4, 15u))
-                                        : *reinterpret_cast<const float4*>(LBM_CK(fs + Q3, rb, RN, 4, 15u));
-                g5 = j > 0 ? *reinterpret_cast<const float4*>(LBM_CK(fb + Q5, rb, RN, 4, 15u))
-                           : f4neg(*reinterpret_cast<const float4*>(LBM_CK(fs + Q6, rb, RN, 4, 15u)));
-                g6 = j < nz - 1 ? *reinterpret_cast<const float4*>(LBM_CK(fa + Q6, rb, RN, 4, 15u))
-                                : f4neg(*reinterpret_cast<const float4*>(LBM_CK(fs + Q5, rb, RN, 4, 15u)));
+                auto rd4 = [&](const float* q) { return *reinterpret_cast<const float4*>(LBM_CK(q, rb, RN, 4, 15u)); };
+                bT = rd4(fs + QT);
+                bX = rd4(fs + QX);
+                if (PERIODIC || !ylo) {
+                    bmT = rd4(fs + QT - NXB);
+                    bmY = rd4(fs + QY - NXB);
+                } else {
+                    bmT = bT;
+                    bmY = f4neg(rd4(fs + QY));
+                }
+                if (PERIODIC || !yhi) {
+                    bpT = rd4(fs + QT + NXB);
+                    bpY = rd4(fs + QY + NXB);
+                } else {
+                    bpT = bT;
+                    bpY = f4neg(rd4(fs + QY));
+                }
+                if (j > 0) {
+                    bdT = rd4(fb + QT);
+                    bdZ = rd4(fb + QZ);
+                } else {
+                    bdT = f4neg(bT);
+                    bdZ = rd4(fs + QZ);
+                }
+                if (j < nz - 1) {
+                    buT = rd4(fa + QT);
+                    buZ = rd4(fa + QZ);
+                } else {
+                    buT = f4neg(bT);
+                    buZ = rd4(fs + QZ);
+                }
             }
             // x-neighbours: from the next lane (every lane takes part), else
             // from the ring row
-            float l1 = __shfl_sync(kFull, c1.w, (lane + 31) & 31);
-            float r2 = __shfl_sync(kFull, c2.x, (lane + 1) & 31);
+            float lT = __shfl_sync(kFull, bT.w, (lane + 31) & 31);
+            float lX = __shfl_sync(kFull, bX.w, (lane + 31) & 31);
+            float rT = __shfl_sync(kFull, bT.x, (lane + 1) & 31);
+            float rX = __shfl_sync(kFull, bX.x, (lane + 1) & 31);
             if (WR || second) {
-                if (!own_left) l1 = *LBM_CK(fs + Q1 - x + xm, (const float*)fn, 3 * RS, 1, 15u);
-                if (!own_right) r2 = *LBM_CK(fs + Q2 - x + xp, (const float*)fn, 3 * RS, 1, 15u);
-                if (!PERIODIC && x == 0) l1 = c2.x;                 // Eq. 24 at x = 0
-                if (!PERIODIC && x + 4 == NXB) r2 = c1.w;           // and at x = nx - 1
-                const float4 g1 = make_float4(l1, c1.x, c1.y, c1.z);
-                const float4 g2 = make_float4(c2.y, c2.z, c2.w, r2);
-                const Quad7 o = collide_quad(g0, g1, g2, g3, g4, g5, g6, phA, s_sa, s_sc, kn1.kT, kn1.kJ);
+                if (!own_left) {
+                    lT = *LBM_CK(fs + QT - x + xm, (const float*)fn, 3 * RS, 1, 15u);
+                    lX = *LBM_CK(fs + QX - x + xm, (const float*)fn, 3 * RS, 1, 15u);
+                }
+                if (!own_right) {
+                    rT = *LBM_CK(fs + QT - x + xp, (const float*)fn, 3 * RS, 1, 15u);
+                    rX = *LBM_CK(fs + QX - x + xp, (const float*)fn, 3 * RS, 1, 15u);
+                }
+                if (!PERIODIC && x == 0) {                 // Eq. 24 at x = 0
+                    lT = bT.x;
+                    lX = -bX.x;
+                }
+                if (!PERIODIC && x + 4 == NXB) {           // and at x = nx - 1
+                    rT = bT.w;
+                    rX = -bX.w;
+                }
+                const Quad4 o = collide_quad(bT, bX, lT, lX, rT, rX, bmT, bmY, bpT, bpY, bdT, bdZ, buT, buZ, phA,
+                                             s_sa, s_sc, kn1.kT, kn1.kJ);
                 float* d = dst + (long long)j * PL + yrow + x;
 #pragma unroll
-                for (int p = 0; p < 7; ++p) *reinterpret_cast<float4*>(LBM_CK(d + p * P, dst, 7 * P, 4, 14u)) = o.o[p];
+                for (int f = 0; f < kFields; ++f)
+                    *reinterpret_cast<float4*>(LBM_CK(d + f * P, dst, kFields * P, 4, 14u)) = o.o[f];
             }
         }
         // ---- step n at plane i into the ring ----
         if (!WR || first) {
-            if (i == 0) q5 = f4neg(q5);
-            if (i == nz - 1) q6 = f4neg(q6);
-            float l1 = __shfl_sync(kFull, q1.w, (lane + 31) & 31);
-            float r2 = __shfl_sync(kFull, q2.x, (lane + 1) & 31);
+            if (i == 0) dT = f4neg(dT);
+            if (i == nz - 1) uT = f4neg(uT);
+            if (!PERIODIC && ylo) mY = f4neg(mY);
+            if (!PERIODIC && yhi) pY = f4neg(pY);
+            float lT = __shfl_sync(kFull, cT.w, (lane + 31) & 31);
+            float lX = __shfl_sync(kFull, cX.w, (lane + 31) & 31);
+            float rT = __shfl_sync(kFull, cT.x, (lane + 1) & 31);
+            float rX = __shfl_sync(kFull, cX.x, (lane + 1) & 31);
             if (WR || first) {
-                if (!own_left) l1 = __ldg(LBM_CK(src + (long long)i * PL + P + yrow + xm, src, 7 * P, 1, 13u));
-                if (!own_right) r2 = __ldg(LBM_CK(src + (long long)i * PL + 2 * P + yrow + xp, src, 7 * P, 1, 13u));
-                if (!PERIODIC && x == 0) l1 = q2.x;
-                if (!PERIODIC && x + 4 == NXB) r2 = q1.w;
-                const float4 g1 = make_float4(l1, q1.x, q1.y, q1.z);
-                const float4 g2 = make_float4(q2.y, q2.z, q2.w, r2);
-                const Quad7 o = collide_quad(q0, g1, g2, q3, q4, q5, q6, phC, s_sa, s_sc, kn.kT, kn.kJ);
-                float* w = fn + si * RS + own;       // block row 0 only writes population 3
+                const float* s = src + (long long)i * PL;
+                if (!own_left) {
+                    lT = __ldg(LBM_CK(s + yrow + xm, src, kFields * P, 1, 13u));
+                    lX = __ldg(LBM_CK(s + P + yrow + xm, src, kFields * P, 1, 13u));
+                }
+                if (!own_right) {
+                    rT = __ldg(LBM_CK(s + yrow + xp, src, kFields * P, 1, 13u));
+                    rX = __ldg(LBM_CK(s + P + yrow + xp, src, kFields * P, 1, 13u));
+                }
+                if (!PERIODIC && x == 0) {
+                    lT = cT.x;
+                    lX = -cX.x;
+                }
+                if (!PERIODIC && x + 4 == NXB) {
+                    rT = cT.w;
+                    rX = -cX.w;
+                }
+                const Quad4 o = collide_quad(cT, cX, lT, lX, rT, rX, mT, mY, pT, pY, dT, dZ, uT, uZ, phC, s_sa,
+                                             s_sc, kn.kT, kn.kJ);
+                float* w = fn + si * RS + own;       // halo rows keep th and m_y only
                 const int RN = 3 * RS;
+                *reinterpret_cast<float4*>(LBM_CK(w + QT, fn, RN, 4, 16u)) = o.o[0];
+                *reinterpret_cast<float4*>(LBM_CK(w + QY, fn, RN, 4, 16u)) = o.o[2];
                 if (tile_row) {
-                    *reinterpret_cast<float4*>(LBM_CK(w, fn, RN, 4, 16u)) = o.o[0];
-                    *reinterpret_cast<float4*>(LBM_CK(w + Q1, fn, RN, 4, 16u)) = o.o[1];
-                    *reinterpret_cast<float4*>(LBM_CK(w + Q2, fn, RN, 4, 16u)) = o.o[2];
-                    *reinterpret_cast<float4*>(LBM_CK(w + Q3, fn, RN, 4, 16u)) = o.o[3];
-                    *reinterpret_cast<float4*>(LBM_CK(w + Q4, fn, RN, 4, 16u)) = o.o[4];
-                    *reinterpret_cast<float4*>(LBM_CK(w + Q5, fn, RN, 4, 16u)) = o.o[5];
-                    *reinterpret_cast<float4*>(LBM_CK(w + Q6, fn, RN, 4, 16u)) = o.o[6];
-                } else if (r == 0) {
-                    *reinterpret_cast<float4*>(LBM_CK(w + Q3, fn, RN, 4, 16u)) = o.o[3];
-                } else {                                 // r == fyb + 1
-                    *reinterpret_cast<float4*>(LBM_CK(w + Q4, fn, RN, 4, 16u)) = o.o[4];
+                    *reinterpret_cast<float4*>(LBM_CK(w + QX, fn, RN, 4, 16u)) = o.o[1];
+                    *reinterpret_cast<float4*>(LBM_CK(w + QZ, fn, RN, 4, 16u)) = o.o[3];
                 }
             }
         }
@@ -1073,13 +1170,13 @@ __global__ void init_kernel(void* __restrict__ fv, float* __restrict__ tsnap, lo
             }
         }
         tsnap[i] = ts;
-        f[i] = to_store<FMT>(0.25f * th);
-        const T e = to_store<FMT>(0.125f * th);
-        for (int q = 1; q < 7; ++q) f[q * P + i] = e;
+        f[i] = to_store<FMT>(th);                  // equilibrium: jhat = 0
+        for (int q = 1; q < kFields; ++q) f[q * P + i] = to_store<FMT>(0.f);
     }
 }
 
-// T = sum_i f_i (Eq. 14) of the current state, written in the original order.
+// T = sum_i f_i (Eq. 14) of the current state, written in the original order:
+// the stored th plus the plane's reference.
 template <int FMT>
 __global__ void temperature_kernel(const void* __restrict__ fv, long long P, Layout L,
                                    const float* __restrict__ ref, float* __restrict__ T) {
@@ -1095,11 +1192,7 @@ __global__ void temperature_kernel(const void* __restrict__ fv, long long P, Lay
         c[2] = (int)(r / L.n[1]);
         const int zc = c[L.perm[2]];
         const long long k = ((long long)zc * L.NY + c[L.perm[1]]) * L.pitch + c[L.perm[0]];
-        const float th = ((S::scalar(f + k) + S::scalar(f + P + k)) +
-                          (S::scalar(f + 2 * P + k) + S::scalar(f + 3 * P + k))) +
-                         ((S::scalar(f + 4 * P + k) + S::scalar(f + 5 * P + k)) +
-                          S::scalar(f + 6 * P + k));
-        T[i] = th + ref[zc];
+        T[i] = S::scalar(f + k) + ref[zc];
     }
 }
 

@@ -69,17 +69,17 @@ def test_missing_library_fails_loudly(tmp_path):
 
 def test_workspace_bytes_cover_the_buffers(lib):
     """lbm_workspace_bytes is at least the context's raw buffer bytes (two
-    distribution buffers of 7 values, phase map and its canonical copy, the
+    distribution buffers of 4 stored fields per node, phase map and its canonical copy, the
     T staging and snapshot fields, the check history) and only alignment and
     per-plane scratch above that; 16-bit storage needs less; bad input gives 0."""
     nx, ny, nz = 128, 128, 256
     N = nx * ny * nz
-    raw = 2 * 7 * 4 * N + N + N + 4 * N + 4 * N + 8 * 4 * 65536
+    raw = 2 * 4 * 4 * N + N + N + 4 * N + 4 * N + 8 * 4 * 65536
     got = lbm.lbm_workspace_bytes(nx, ny, nz, lbm.LBM_STORE_F32)
     assert raw <= got <= raw + (1 << 20)
     assert lbm.lbm_workspace_bytes(nx, ny, nz, lbm.LBM_STORE_BF16) < got
     # padding: rows of 5 nodes are padded to 8 (4-node vectors) along any axis
-    assert lbm.lbm_workspace_bytes(5, 9, 7, lbm.LBM_STORE_F32) >= 2 * 7 * 4 * 8 * 9 * 7
+    assert lbm.lbm_workspace_bytes(5, 9, 7, lbm.LBM_STORE_F32) >= 2 * 4 * 4 * 8 * 9 * 7
     assert lbm.lbm_workspace_bytes(1, 8, 8, 0) == 0
     assert lbm.lbm_workspace_bytes(8, 8, 8, 9) == 0
     st, h = lbm.lbm_create_with_workspace(8, 8, 8, 0, 0, 1 << 20)
