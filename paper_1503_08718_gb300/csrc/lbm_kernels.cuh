@@ -674,11 +674,9 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
 // cell whose ny is not a multiple of FY has fyb < FY rows; its halo is block
 // row fyb + 1 and the rows after it idle.  Threads past (FY + 2) nq idle too
 // (a batch launches every block with the same size).
-// Iteration i computes step n at plane i for all rows (pulled from global
-// memory, written to a ring of three shared planes) and step n + 1 at plane
-// i - 2 for the tile rows (pulled from the ring, written to global memory).
-// The loads of plane i are issued before the second step's work, so they are
-// in flight while it runs.  Every node's arithmetic is the single step's
+// Iteration i computes step n + 1 at plane i - 2 for the tile rows (pulled
+// from a ring of three shared planes, written to global memory) and step n
+// at plane i for all rows (pulled from global memory, written to the ring).  Every node's arithmetic is the single step's
 // (collide_node), so two fused steps equal two single steps bit for bit.
 // Step n runs from frame rsrc to rdst, step n + 1 within rdst.
 constexpr int F2_MAX_THREADS = 640;
@@ -869,30 +867,6 @@ __device__ __forceinline__ void fused2_body(const StepArgs& a, float* fn, const 
                 asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(pf_base + ip * pf_plane),
                              "r"(pf_bytes) : "memory");
         }
-        // ---- loads of step n at plane i ----
-        const bool first = i >= z0 - 1 && i <= z1 && i >= 0 && i < nz && row_in;
-        float4 cT, cX, mT, mY, pT, pY, dT, dZ, uT, uZ;
-        unsigned phC = 0u;
-        if (first) {
-            const float* s = src + (long long)i * PL;
-            const float* sd = s + (i > 0 ? -PL : 0);          // the walls (Eq. 23) use the own node
-            const float* su = s + (i < nz - 1 ? PL : 0);
-            const int NP = kFields;
-            cT = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + yrow + x, src, NP * P, 4, 11u)));
-            cX = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + P + yrow + x, src, NP * P, 4, 11u)));
-            mT = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + rym + x, src, NP * P, 4, 11u)));
-            mY = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + 2 * P + rym + x, src, NP * P, 4, 11u)));
-            pT = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + ryp + x, src, NP * P, 4, 11u)));
-            pY = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + 2 * P + ryp + x, src, NP * P, 4, 11u)));
-            dT = __ldg(reinterpret_cast<const float4*>(LBM_CK(sd + yrow + x, src, NP * P, 4, 11u)));
-            dZ = __ldg(reinterpret_cast<const float4*>(LBM_CK(sd + 3 * P + yrow + x, src, NP * P, 4, 11u)));
-            uT = __ldg(reinterpret_cast<const float4*>(LBM_CK(su + yrow + x, src, NP * P, 4, 11u)));
-            uZ = __ldg(reinterpret_cast<const float4*>(LBM_CK(su + 3 * P + yrow + x, src, NP * P, 4, 11u)));
-            phC = __ldg(reinterpret_cast<const unsigned*>(
-                LBM_CK(a.phase + (long long)i * PL + yrow + x, a.phase, P, 4, 12u)));
-        } else if (!WR) {
-            cT = cX = mT = mY = pT = pY = dT = dZ = uT = uZ = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
         // ---- step n + 1 at plane j, tile rows ----
         const int own = (r - 1) * NXB + x;          // this thread's nodes in a ring plane
         const bool second = tile_row && j >= z0 && j < z1;
@@ -968,6 +942,33 @@ __device__ __forceinline__ void fused2_body(const StepArgs& a, float* fn, const 
                 for (int f = 0; f < kFields; ++f)
                     *reinterpret_cast<float4*>(LBM_CK(d + f * P, dst, kFields * P, 4, 14u)) = o.o[f];
             }
+        }
+        // ---- loads of step n at plane i ----
+        // issued after step n + 1: holding them in flight across that step
+        // would need its registers too (the two-step kernel then spills); the
+        // L2 prefetch of this plane two iterations ago keeps their latency short
+        const bool first = i >= z0 - 1 && i <= z1 && i >= 0 && i < nz && row_in;
+        float4 cT, cX, mT, mY, pT, pY, dT, dZ, uT, uZ;
+        unsigned phC = 0u;
+        if (first) {
+            const float* s = src + (long long)i * PL;
+            const float* sd = s + (i > 0 ? -PL : 0);          // the walls (Eq. 23) use the own node
+            const float* su = s + (i < nz - 1 ? PL : 0);
+            const int NP = kFields;
+            cT = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + yrow + x, src, NP * P, 4, 11u)));
+            cX = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + P + yrow + x, src, NP * P, 4, 11u)));
+            mT = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + rym + x, src, NP * P, 4, 11u)));
+            mY = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + 2 * P + rym + x, src, NP * P, 4, 11u)));
+            pT = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + ryp + x, src, NP * P, 4, 11u)));
+            pY = __ldg(reinterpret_cast<const float4*>(LBM_CK(s + 2 * P + ryp + x, src, NP * P, 4, 11u)));
+            dT = __ldg(reinterpret_cast<const float4*>(LBM_CK(sd + yrow + x, src, NP * P, 4, 11u)));
+            dZ = __ldg(reinterpret_cast<const float4*>(LBM_CK(sd + 3 * P + yrow + x, src, NP * P, 4, 11u)));
+            uT = __ldg(reinterpret_cast<const float4*>(LBM_CK(su + yrow + x, src, NP * P, 4, 11u)));
+            uZ = __ldg(reinterpret_cast<const float4*>(LBM_CK(su + 3 * P + yrow + x, src, NP * P, 4, 11u)));
+            phC = __ldg(reinterpret_cast<const unsigned*>(
+                LBM_CK(a.phase + (long long)i * PL + yrow + x, a.phase, P, 4, 12u)));
+        } else if (!WR) {
+            cT = cX = mT = mY = pT = pY = dT = dZ = uT = uZ = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         // ---- step n at plane i into the ring ----
         if (!WR || first) {
