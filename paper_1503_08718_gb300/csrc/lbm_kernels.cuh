@@ -821,11 +821,12 @@ __device__ __forceinline__ void fused2_body(const StepArgs& a, float* fn, const 
     if (tid == 0) plane_pair(0, s_kc[0]);
     __syncthreads();                               // the B tables and s_kc[0] are ready
 
-    // L2 prefetch two planes ahead: lanes 0..4 of the block's last warp each
+    // L2 prefetch one plane ahead: lanes 0..4 of the block's last warp each
     // fetch, by one bulk prefetch, one field's rows that the tile's first
     // step reads there (th and m_y with the rows on either side, m_x and m_z
-    // the block rows, clamped to the cell) or the phase bytes.  Plane i + 2
-    // is read as the upper z-neighbour at the next iteration.  A bulk
+    // the block rows, clamped to the cell) or the phase bytes.  Plane i + 1
+    // is read as the upper z-neighbour at the end of this iteration, after
+    // the second step has given the prefetch time to land.  A bulk
     // prefetch takes its operands from uniform registers, so lanes with
     // different addresses are served one after another: one warp per block
     // keeps that loop short.
@@ -862,7 +863,7 @@ __device__ __forceinline__ void fused2_body(const StepArgs& a, float* fn, const 
         const PlaneK kn = s_kc[t & 1][0], kn1 = s_kc[t & 1][1];
         if (tid == 0) plane_pair(t + 1, s_kc[(t + 1) & 1]);   // read after this iteration's barrier
         {
-            const int ip = i + 2 * dz;
+            const int ip = i + dz;
             if (pf_lane && ip >= max(z0 - 2, 0) && ip <= min(z1 + 1, nz - 1))
                 asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(pf_base + ip * pf_plane),
                              "r"(pf_bytes) : "memory");
