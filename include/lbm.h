@@ -360,12 +360,14 @@ lbm_status lbm_nn_conv3d(const void* x, int cin, const void* w, const float* bia
                          void* stream);
 
 /* The same 3x3x3 convolution (bias, leaky ReLU, BF16 or FP32 output) on the
- * fifth-generation tensor cores: tcgen05.mma with the accumulator in tensor
- * memory, one block per tile of 16 x 8 output voxels of a plane, the tile's
- * halo staged once in shared memory and read by every tap's MMA through its
- * own descriptor, the taps' weight slabs streamed by cp.async.bulk through
- * four shared-memory stages.  wk: the weight slabs lbm_nn_weights_kmajor
- * writes (27 * cin * cout BF16).
+ * fifth-generation tensor cores: tcgen05.mma with the accumulators in
+ * tensor memory, persistent blocks (one per SM) walking tiles of 16 x 8
+ * output voxels of one or more planes, each tile's halo staged once in
+ * shared memory and read by every tap's MMA through its own descriptor, the
+ * taps' weight slabs streamed by cp.async.bulk through a ring of
+ * shared-memory stages, the epilogue of one tile overlapping the MMAs of the
+ * next.  wk: the weight slabs lbm_nn_weights_kmajor writes
+ * (27 * cin * cout BF16).
  * Requires cin and cout multiples of 16, cout <= 256, h a multiple of 16 and
  * w a multiple of 8 (lbm_nn_conv3d_tc_supported); else LBM_ERR_INVALID_ARG.
  * Each block bounds its waits; a timeout is recorded for lbm_nn_tc_error. */
@@ -386,10 +388,12 @@ lbm_status lbm_nn_conv3d_wgrad_tc(const void* x, int cin, const void* g, int cou
 int lbm_nn_conv3d_wgrad_tc_supported(int cin, int cout, int n, int d, int h, int w);
 
 /* lbm_nn_conv3d_tc with an explicit launch configuration: tz output planes
- * per block (1, 2 or 4: the planes share every weight slab) and ns weight
- * stages (2 or 4); 0 lets the library choose, as lbm_nn_conv3d_tc does.
- * LBM_ERR_INVALID_ARG if the sizes or the configuration do not fit (d must
- * be a multiple of tz; tz accumulators must fit 256 tensor-memory columns). */
+ * per tile (1, 2 or 4: the planes share every weight slab) and ns weight
+ * stages in shared memory (>= 2); 0 lets the library choose, as
+ * lbm_nn_conv3d_tc does.  LBM_ERR_INVALID_ARG if the sizes or the
+ * configuration do not fit (d must be a multiple of tz; the two accumulator
+ * buffers of tz planes must fit 512 tensor-memory columns; the stages must
+ * fit shared memory). */
 lbm_status lbm_nn_conv3d_tc_cfg(const void* x, int cin, const void* wk, const float* bias, void* y, int cout,
                                 int n, int d, int h, int wdt, int relu, int out_f32, int tz, int ns, void* stream);
 

@@ -2,21 +2,21 @@
 // cores (tcgen05.mma, accumulator in tensor memory), sm_103a.
 //
 // Implicit GEMM: M = output voxels, N = output channels, K = 27 taps x input
-// channels.  A block computes one tile of 128 output voxels (16 rows of 8
-// voxels of one z plane of one cell) for all output channels.  Instead of
-// gathering an im2col matrix per tap, it stages the tile's halo once in
-// shared memory: 3 planes x 18 rows x 10 voxels of 16-byte channel chunks,
-// laid out so that every tap's A operand is the same canonical no-swizzle
-// K-major layout (8-row core matrices of 16-byte rows) at a different start
-// address: rows of 8 voxels are 16 bytes apart, the 16 rows of the tile 160
-// bytes apart (SBO) and consecutive 8-channel chunks 8640 bytes apart (LBO).
-// The 27 taps then cost 27 x K/16 MMA instructions and no extra copies.
-// The B operand (the tap's weights, K-major [cout][cin]) streams through two
-// shared-memory stages; tcgen05.commit on a per-stage mbarrier tells the
-// block when the MMAs that read a stage are done.  One thread issues the
-// MMAs; the accumulator (128 lanes x N FP32 columns) stays in tensor memory
-// until the epilogue reads it back with tcgen05.ld (warp w owns lanes
-// 32w .. 32w + 31), adds the bias, applies the leaky ReLU and stores.
+// channels.  A tile is 128 output voxels (16 rows of 8 voxels of one z plane
+// of one cell) for all output channels, times tz consecutive planes.  Instead
+// of gathering an im2col matrix per tap, the tile's halo is staged once in
+// shared memory: tz + 2 planes x 18 rows x 10 voxels of 16-byte channel
+// chunks, laid out so that every tap's A operand is the same canonical
+// no-swizzle K-major layout (8-row core matrices of 16-byte rows) at a
+// different start address: rows of 8 voxels are 16 bytes apart, the 16 rows
+// of the tile 160 bytes apart (SBO) and consecutive 8-channel chunks one halo
+// plane set apart (LBO).  The 27 taps then cost 27 x K/16 MMA instructions
+// and no extra copies.  The B operand (the tap's weights, K-major
+// [cout][cin]) streams through a ring of shared-memory stages; tcgen05.commit
+// on per-stage mbarriers frees each stage when the MMAs that read it are
+// done.  The forward kernel is persistent with warp roles (weight producer,
+// MMA issuer, halo loaders, epilogue) and two accumulator buffers in tensor
+// memory, so that loads, MMAs and the epilogue of consecutive tiles overlap.
 // Padding as the rest of the network: periodic in x and y, zero in z.
 //
 // Every wait on an mbarrier is bounded: on expiry the kernel records an
@@ -124,18 +124,37 @@ struct Vol {
     int n, d, h, w;
 };
 
-// Input channels per shared-memory halo (a channel group): at most 32, so
-// that the halo of two planes (46 KB) leaves room for four blocks per SM;
-// groups of 32 or 16.
+// Input channels per shared-memory halo (a channel group): 32 where they
+// divide the input channels, else 16.
 __host__ __device__ constexpr int cg_for(int cin) {
     return cin % 32 == 0 ? 32 : 16;
 }
 
-// Shared memory of the forward kernel for tz output planes per block and ns
-// weight stages: halo [cg/8][tz + 2][18][10] x 16 B, then the stages
-// [cg/8][N] x 16 B each, then the mbarriers and the TMEM address.
-__host__ __device__ constexpr size_t tc_smem_bytes(int cg, int n, int tz, int ns) {
-    return (size_t)(tz + 2) * HY * HX * cg * 2 + (size_t)ns * n * cg * 2 + 256;
+// Forward kernel: persistent blocks (one per SM) with warp roles, each block
+// walking the tiles blockIdx.x, blockIdx.x + gridDim.x, ...  A tile is TZ
+// consecutive z planes of the same 16 x 8 rows (TZ accumulators of N columns
+// that share every weight slab).
+//   warp 0 (one thread): streams the weight slabs, tile after tile, through
+//     a ring of WS stages (cp.async.bulk, completion on the stage's `w_full`
+//     mbarrier, the stage freed by the MMAs' commit to `w_empty`);
+//   warp 1 (one thread): issues the MMAs of each (tap, channel group) as its
+//     slab and halo are in, into one of two accumulator buffers (tile k uses
+//     buffer k & 1), and commits the halo stage to `h_empty` and the finished
+//     tile to `a_full`;
+//   warps 2-5: load each (tile, channel group) halo into a ring of HS stages
+//     (cp.async, zero fill outside the cell in z), then fence it for the
+//     tensor core and arrive on `h_full`;
+//   warps 6-9: the epilogue of tile k (tcgen05.ld of its buffer, bias, leaky
+//     ReLU, store) while the MMAs of tile k + 1 run in the other buffer; they
+//     free the buffer on `a_empty`.
+// The weights arrive pre-arranged (lbm_nn_weights_kmajor): slab (tap, group)
+// is [cg/8][N][8] BF16, exactly the stage's shared-memory image.
+constexpr int W_LOAD = 2, N_LOAD = 4, W_EPI = 6;   // first loader warp, loader warps, first epilogue warp
+constexpr int PT = 32 * (W_EPI + 4);               // threads of the forward kernel
+
+__host__ __device__ constexpr size_t tc_halo_bytes(int cg, int tz) { return (size_t)(tz + 2) * HY * HX * cg * 2; }
+__host__ __device__ constexpr size_t tc_smem_bytes(int cg, int n, int tz, int ws, int hs) {
+    return (size_t)hs * tc_halo_bytes(cg, tz) + (size_t)ws * n * cg * 2 + 8 * (2 * ws + 2 * hs + 5) + 16;
 }
 
 // Blocks an SM can hold are bounded by shared memory; make sure they never
@@ -147,56 +166,77 @@ size_t tmem_safe_smem(size_t smem, int cols) {
     return smem > floor ? smem : floor;
 }
 
-// Forward kernel, TZ tiles per block (TZ consecutive z planes of the same 16
-// x 8 rows: TZ accumulators of N columns that share every weight slab).
-// Roles: thread 0 streams the weight
-// slabs of the taps (one cp.async.bulk per slab into a free stage, completion
-// counted on the stage's `full` mbarrier); thread 32 issues each tap's MMAs
-// once its slab is in and commits them to the stage's `empty` mbarrier, which
-// frees the stage for the producer.  All threads load the halo of a channel
-// group (cp.async) and run the epilogue.  The weights arrive pre-arranged
-// (lbm_nn_weights_kmajor): slab (tap, group) is [cg/8][N][8] BF16, exactly
-// the stage's shared-memory image.
-template <bool RELU, bool OUT_F32, int TZ, int NS>
-__global__ void __launch_bounds__(THREADS) conv3_tc_kernel(const bf16* __restrict__ X, int Cin, int CG,
-                                                           const bf16* __restrict__ Wu,
-                                                           const float* __restrict__ bias,
-                                                           void* __restrict__ Yv, int N, int tmem_cols,
-                                                           Vol vol) {
+// waits of a whole warp that is not on the critical path: every lane polls
+// with a short sleep between polls (so that the spinning warps leave the
+// issue slots to the MMA thread); the outcome is the warp's
+__device__ __forceinline__ bool warp_wait(unsigned bar, unsigned parity) {
+    bool ok = false;
+    for (unsigned i = 0; i < kSpinLimit && !ok; ++i) {
+        unsigned r;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(r)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        ok = r != 0;
+        if (!ok) __nanosleep(64);
+    }
+    return __all_sync(0xffffffffu, ok);
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+template <bool RELU, bool OUT_F32, int TZ>
+__global__ void __launch_bounds__(PT, 1) conv3_tc_kernel(const bf16* __restrict__ X, int Cin, int CG,
+                                                         const bf16* __restrict__ Wu,
+                                                         const float* __restrict__ bias,
+                                                         void* __restrict__ Yv, int N, int tstride,
+                                                         int tmem_cols, Vol vol, int n_tiles, int WS, int HS) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int CG8 = CG >> 3;
-    unsigned char* halo = smem;
-    constexpr int NSTAGE = NS;
     constexpr int PZ = TZ + 2;                      // halo planes
     constexpr int PVOX = PZ * HY * HX;              // halo voxels
-    unsigned char* wst = smem + (size_t)PVOX * CG * 2;
-    const unsigned slab = (unsigned)N * CG * 2;          // bytes of one weight slab
-    unsigned long long* full = reinterpret_cast<unsigned long long*>(wst + NSTAGE * (size_t)slab);
-    unsigned long long* empty = full + NSTAGE;
-    unsigned* tmem_slot = reinterpret_cast<unsigned*>(empty + NSTAGE);
+    const unsigned hstage = (unsigned)PVOX * CG * 2;
+    const unsigned slab = (unsigned)N * CG * 2;     // bytes of one weight slab
+    unsigned char* halo = smem;
+    unsigned char* wst = smem + (size_t)HS * hstage;
+    unsigned long long* w_full = reinterpret_cast<unsigned long long*>(wst + (size_t)WS * slab);
+    unsigned long long* w_empty = w_full + WS;
+    unsigned long long* h_full = w_empty + WS;
+    unsigned long long* h_empty = h_full + HS;
+    unsigned long long* a_full = h_empty + HS;      // [2]
+    unsigned long long* a_empty = a_full + 2;       // [2]
+    unsigned long long* done = a_empty + 2;
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(done + 1);
     __shared__ volatile int s_fail;
-    __shared__ volatile int s_consumed;             // slabs the MMA thread has waited for
+    __shared__ long long s_issued, s_consumed;      // weight slabs issued / waited for
     const unsigned halo_s = smem_u32(halo), wst_s = smem_u32(wst);
-
-    const int tiles_x = vol.w / TILE_X, tiles_y = vol.h / TILE_Y;
-    int b = blockIdx.x;
-    const int tx = b % tiles_x; b /= tiles_x;
-    const int ty = b % tiles_y; b /= tiles_y;
-    const int zt = vol.d / TZ;                      // z tiles per cell
-    const int z0 = (b % zt) * TZ;
-    const int n0 = b / zt;
-    const int x0 = tx * TILE_X, y0 = ty * TILE_Y;
     const int ngroups = Cin / CG;
-    const int total = 27 * ngroups;                 // weight slabs / MMA batches, group-major
+    const int per_tile = 27 * ngroups;              // weight slabs per tile, group-major
+    const int tiles_x = vol.w / TILE_X, tiles_y = vol.h / TILE_Y, zt = vol.d / TZ;
+    const int my_tiles = (int)blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
     if (tid == 0) {
         s_fail = 0;
+        s_issued = 0;
         s_consumed = 0;
-        for (int s = 0; s < NSTAGE; ++s) {
-            mbar_init(smem_u32(&full[s]), 1);
-            mbar_init(smem_u32(&empty[s]), 1);
+        for (int s = 0; s < WS; ++s) {
+            mbar_init(smem_u32(&w_full[s]), 1);
+            mbar_init(smem_u32(&w_empty[s]), 1);
         }
+        for (int s = 0; s < HS; ++s) {
+            mbar_init(smem_u32(&h_full[s]), 32 * N_LOAD);
+            mbar_init(smem_u32(&h_empty[s]), 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(smem_u32(&a_full[s]), 1);
+            mbar_init(smem_u32(&a_empty[s]), 128);
+        }
+        mbar_init(smem_u32(done), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -209,135 +249,209 @@ __global__ void __launch_bounds__(THREADS) conv3_tc_kernel(const bf16* __restric
     __syncthreads();
     fence_after();
     const unsigned tmem = *tmem_slot;
-    const uint32_t idesc = instr_desc(N);
-    const unsigned lbo_a = PVOX * 16, sbo_a = HX * 16;
-    const unsigned lbo_b = (unsigned)N * 16, sbo_b = 128;
 
-    // producer: slab T into stage T % NSTAGE once the MMAs that last read it
-    // are done (batch T - NSTAGE committed to `empty`)
-    auto produce = [&](int T) {
-        const int s = T % NSTAGE;
-        if (T >= NSTAGE && !mbar_wait(smem_u32(&empty[s]), (unsigned)(((T / NSTAGE) - 1) & 1))) {
-            s_fail = 1;
-            return;
-        }
-        const unsigned fb = smem_u32(&full[s]);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(slab) : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                wst_s + (unsigned)s * slab),
-            "l"(Wu + (size_t)((T % 27) * ngroups + T / 27) * (slab / 2)), "r"(slab), "r"(fb)
-            : "memory");
+    // cell, first plane, first row and first voxel of this block's tile k
+    auto tile_at = [&](int k, int& n0, int& z0, int& y0, int& x0) {
+        int b = (int)blockIdx.x + k * (int)gridDim.x;
+        const int tx = b % tiles_x; b /= tiles_x;
+        const int ty = b % tiles_y; b /= tiles_y;
+        z0 = (b % zt) * TZ;
+        n0 = b / zt;
+        x0 = tx * TILE_X;
+        y0 = ty * TILE_Y;
     };
-    int next = 0;                                   // next slab the producer issues
-    for (int g = 0; g < ngroups; ++g) {
-        const int T0 = g * 27;
-        // the halo is rewritten: the previous group's MMAs must be done
-        if (g > 0 && tid == 32 && !s_fail &&
-            !mbar_wait(smem_u32(&empty[(T0 - 1) % NSTAGE]), (unsigned)(((T0 - 1) / NSTAGE) & 1)))
-            s_fail = 1;
-        __syncthreads();
-        if (s_fail) break;
-        // the first slabs of the group start while the halo loads
-        if (tid == 0)
-            for (; next < T0 + NSTAGE && next < total && !s_fail; ++next) produce(next);
-        for (int i = tid; i < PVOX * CG8; i += THREADS) {
-            const int hv = i / CG8, c8 = i - hv * CG8;
-            const int xh = hv % HX, yh = (hv / HX) % HY, zz = hv / (HX * HY);
-            const int z = z0 + zz - 1;
-            int y = y0 + yh - 1, x = x0 + xh - 1;
-            y = y < 0 ? y + vol.h : (y >= vol.h ? y - vol.h : y);
-            x = x < 0 ? x + vol.w : (x >= vol.w ? x - vol.w : x);
-            const bool in = z >= 0 && z < vol.d;
-            const long long v = (((long long)n0 * vol.d + (in ? z : 0)) * vol.h + y) * vol.w + x;
-            cp16(halo_s + (unsigned)((((c8 * PZ + zz) * HY + yh) * HX + xh) * 16),
-                 X + v * Cin + g * CG + c8 * 8, in ? 16u : 0u);
-        }
-        cp_commit();
-        cp_wait_all();
-        fence_proxy_async();
-        __syncthreads();
-        if (s_fail) break;
-        if (tid == 0) {
-            // the rest of the group's slabs, each as soon as its stage frees
-            for (; next < T0 + 27 && !s_fail; ++next) produce(next);
-        } else if (tid == 32) {
-            for (int t = 0; t < 27 && !s_fail; ++t) {
-                const int T = T0 + t, s = T % NSTAGE;
-                if (!mbar_wait(smem_u32(&full[s]), (unsigned)((T / NSTAGE) & 1))) {
+
+    if (warp == 0) {
+        if (lane == 0) {                            // weight producer
+            const long long total = (long long)my_tiles * per_tile;
+            long long T = 0;
+            int s = 0, g = 0, t = 0;                // stage, channel group, tap of slab T
+            unsigned round = 0;                     // fills of stage s so far
+            for (; T < total && !s_fail; ++T) {
+                if (round > 0 && !mbar_wait(smem_u32(&w_empty[s]), (round - 1) & 1u)) {
                     s_fail = 1;
                     break;
                 }
-                s_consumed = T + 1;
+                const unsigned fb = smem_u32(&w_full[s]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(slab)
+                             : "memory");
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        wst_s + (unsigned)s * slab),
+                    "l"(Wu + (size_t)(t * ngroups + g) * (slab / 2)), "r"(slab), "r"(fb)
+                    : "memory");
+                if (++s == WS) {
+                    s = 0;
+                    ++round;
+                }
+                if (++t == 27) {
+                    t = 0;
+                    if (++g == ngroups) g = 0;
+                }
+            }
+            s_issued = T;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {                            // MMA issuer
+            const uint32_t idesc = instr_desc(N);
+            const unsigned lbo_a = PVOX * 16, sbo_a = HX * 16;
+            const unsigned lbo_b = (unsigned)N * 16, sbo_b = 128;
+            // descriptors of halo stage 0 and weight stage 0; a start address
+            // is the descriptor's low field in 16-byte units, so an offset
+            // within shared memory is added to it directly
+            const uint64_t ad0 = smem_desc(halo_s, lbo_a, sbo_a);
+            const uint64_t bd0 = smem_desc(wst_s, lbo_b, sbo_b);
+            long long T = 0;
+            int ws = 0, hs = 0;                     // weight and halo stage
+            unsigned wround = 0, hround = 0;        // completed passes over each ring
+            for (int k = 0; k < my_tiles && !s_fail; ++k) {
+                const int ab = k & 1;
+                if (k >= 2 && !mbar_wait(smem_u32(&a_empty[ab]), (unsigned)(((k >> 1) - 1) & 1))) {
+                    s_fail = 1;
+                    break;
+                }
                 fence_after();
-                const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-                const unsigned b0 = wst_s + (unsigned)s * slab;
+                const unsigned dacc = tmem + (unsigned)(ab * TZ * tstride);
+                for (int g = 0; g < ngroups && !s_fail; ++g) {
+                    if (!mbar_wait(smem_u32(&h_full[hs]), hround & 1u)) {
+                        s_fail = 1;
+                        break;
+                    }
+                    const uint64_t adh = ad0 + (uint64_t)((hs * hstage) >> 4);
+                    for (int t = 0; t < 27; ++t, ++T) {
+                        if (!mbar_wait(smem_u32(&w_full[ws]), wround & 1u)) {
+                            s_fail = 1;
+                            break;
+                        }
+                        s_consumed = T + 1;
+                        fence_after();
+                        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+                        const uint64_t bdw = bd0 + (uint64_t)((ws * slab) >> 4);
+                        // consecutive MMAs go to different accumulators: MMAs into
+                        // one accumulator follow each other only after the
+                        // previous one is done
+                        for (int ks = 0; ks < CG / 16; ++ks)
 #pragma unroll
-                for (int tz = 0; tz < TZ; ++tz) {
-                    const unsigned a0 = halo_s + (unsigned)((((tz + dz) * HY + dy) * HX + dx) * 16);
-                    for (int ks = 0; ks < CG / 16; ++ks) {
-                        const uint64_t ad = smem_desc(a0 + 2u * ks * lbo_a, lbo_a, sbo_a);
-                        const uint64_t bd = smem_desc(b0 + 2u * ks * lbo_b, lbo_b, sbo_b);
-                        mma_bf16(tmem + (unsigned)(tz * N), ad, bd, idesc, (T > 0 || ks > 0) ? 1u : 0u);
+                            for (int tz = 0; tz < TZ; ++tz) {
+                                const uint64_t ad = adh + (uint64_t)((((tz + dz) * HY + dy) * HX + dx));
+                                mma_bf16(dacc + (unsigned)(tz * tstride), ad + (uint64_t)(ks * (2 * lbo_a >> 4)),
+                                         bdw + (uint64_t)(ks * (2 * lbo_b >> 4)), idesc,
+                                         (g > 0 || t > 0 || ks > 0) ? 1u : 0u);
+                            }
+                        mma_commit(smem_u32(&w_empty[ws]));
+                        if (++ws == WS) {
+                            ws = 0;
+                            ++wround;
+                        }
+                    }
+                    if (s_fail) break;
+                    mma_commit(smem_u32(&h_empty[hs]));
+                    if (++hs == HS) {
+                        hs = 0;
+                        ++hround;
                     }
                 }
-                mma_commit(smem_u32(&empty[s]));
+                if (s_fail) break;
+                mma_commit(smem_u32(&a_full[ab]));
+            }
+            // every MMA issued is done before the block frees its tensor memory
+            mma_commit(smem_u32(done));
+            if (!mbar_wait(smem_u32(done), 0u)) s_fail = 1;
+        }
+    } else if (warp < W_EPI) {                      // halo loaders
+        // thread lt owns cell j = lt % rc of every rc-cell halo row (a row:
+        // HX voxels x CG/8 chunks) and walks rows r0, r0 + rs, ...
+        const int lt = tid - 32 * W_LOAD;
+        const int rc = HX * CG8, rs = (32 * N_LOAD) / rc;
+        const int j = lt % rc, r0 = lt / rc;
+        const int xh = j / CG8, c8 = j - xh * CG8;
+        int hs = 0;                                 // halo stage
+        unsigned hround = 0;                        // completed passes over the ring
+        for (int k = 0; k < my_tiles && !s_fail; ++k) {
+            int n0, z0, y0, x0;
+            tile_at(k, n0, z0, y0, x0);
+            int x = x0 + xh - 1;
+            x = x < 0 ? x + vol.w : (x >= vol.w ? x - vol.w : x);
+            for (int g = 0; g < ngroups; ++g) {
+                if (hround > 0 && !warp_wait(smem_u32(&h_empty[hs]), (hround - 1) & 1u)) {
+                    s_fail = 1;
+                    break;
+                }
+                const unsigned hb = halo_s + (unsigned)hs * hstage + (unsigned)(((c8 * PZ) * HY * HX + xh) * 16);
+                const bf16* xs = X + (long long)x * Cin + g * CG + c8 * 8;
+                if (r0 < rs)
+                    for (int row = r0; row < PZ * HY; row += rs) {
+                        const int zz = row / HY, yh = row - zz * HY;
+                        const int z = z0 + zz - 1;
+                        int y = y0 + yh - 1;
+                        y = y < 0 ? y + vol.h : (y >= vol.h ? y - vol.h : y);
+                        const bool in = z >= 0 && z < vol.d;
+                        const long long rowv = (((long long)n0 * vol.d + (in ? z : 0)) * vol.h + y) * vol.w;
+                        cp16(hb + (unsigned)(row * HX * 16), xs + rowv * Cin, in ? 16u : 0u);
+                    }
+                cp_commit();
+                cp_wait_all();
+                fence_proxy_async();                // the tensor core reads it through the async proxy
+                mbar_arrive(smem_u32(&h_full[hs]));
+                if (++hs == HS) {
+                    hs = 0;
+                    ++hround;
+                }
             }
         }
-    }
-    // every MMA is done once the last batch's commit completes (a second
-    // bounded wait after a failure, before the tensor memory is freed)
-    if (tid == 32 && total > 0) {
-        const int T = total - 1;
-        if (!mbar_wait(smem_u32(&empty[T % NSTAGE]), (unsigned)((T / NSTAGE) & 1))) {
-            s_fail = 1;
-            mbar_wait(smem_u32(&empty[T % NSTAGE]), (unsigned)((T / NSTAGE) & 1));
+    } else {                                        // epilogue
+        const int q = warp & 3;                     // TMEM lanes 32q .. 32q + 31 (warps 6-9: 2, 3, 0, 1)
+        const int m = q * 32 + lane;                // output voxel m of the tile's planes
+        const int yy = m / TILE_X, xx = m % TILE_X;
+        for (int k = 0; k < my_tiles && !s_fail; ++k) {
+            const int ab = k & 1;
+            if (!warp_wait(smem_u32(&a_full[ab]), (unsigned)((k >> 1) & 1))) {
+                s_fail = 1;
+                break;
+            }
+            fence_after();
+            int n0, z0, y0, x0;
+            tile_at(k, n0, z0, y0, x0);
+            for (int tz = 0; tz < TZ; ++tz)
+                for (int c0 = 0; c0 < N; c0 += 16) {
+                    const long long v = (((long long)n0 * vol.d + z0 + tz) * vol.h + y0 + yy) * vol.w + x0 + xx;
+                    const unsigned trow = tmem + ((unsigned)(q * 32) << 16) + (unsigned)((ab * TZ + tz) * tstride);
+                    float acc[16];
+                    tmem_ld16(trow + (unsigned)c0, acc);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        float y = acc[i] + (bias ? bias[c0 + i] : 0.f);
+                        if (RELU) y = y > 0.f ? y : 0.01f * y;
+                        acc[i] = y;
+                    }
+                    if (OUT_F32) {
+                        float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(Yv) + v * N + c0);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            dst[u] = make_float4(acc[4 * u], acc[4 * u + 1], acc[4 * u + 2], acc[4 * u + 3]);
+                    } else {
+                        __align__(16) __nv_bfloat162 o[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) o[u] = __floats2bfloat162_rn(acc[2 * u], acc[2 * u + 1]);
+                        uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<bf16*>(Yv) + v * N + c0);
+                        dst[0] = *reinterpret_cast<const uint4*>(&o[0]);
+                        dst[1] = *reinterpret_cast<const uint4*>(&o[4]);
+                    }
+                }
+            fence_before();
+            mbar_arrive(smem_u32(&a_empty[ab]));
         }
     }
-    cp_wait_all();
     __syncthreads();
     // after a failure, the weight copies still in flight land before the
-    // block leaves (bounded)
+    // block leaves (bounded waits on the last phase of each stage)
     if (tid == 0 && s_fail)
-        for (int T = s_consumed; T < next; ++T) mbar_wait(smem_u32(&full[T % NSTAGE]), (unsigned)((T / NSTAGE) & 1));
-    __syncthreads();
-    fence_after();
-    const bool failed = s_fail != 0;
-    if (failed) {
-        if (tid == 0) atomicCAS(&g_tc_error, 0u, 1u);
-    } else {
-        // epilogue: lane m of accumulator tz is output voxel m of tile tz
-        const int m = warp * 32 + lane;
-        const int yy = m / TILE_X, xx = m % TILE_X;
-        for (int tz = 0; tz < TZ; ++tz)
-        for (int c0 = 0; c0 < N; c0 += 16) {
-            const long long v = (((long long)n0 * vol.d + z0 + tz) * vol.h + y0 + yy) * vol.w + x0 + xx;
-            const unsigned trow = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(tz * N);
-            float acc[16];
-            tmem_ld16(trow + (unsigned)c0, acc);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                float y = acc[i] + (bias ? bias[c0 + i] : 0.f);
-                if (RELU) y = y > 0.f ? y : 0.01f * y;
-                acc[i] = y;
-            }
-            if (OUT_F32) {
-                float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(Yv) + v * N + c0);
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    dst[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-            } else {
-                __align__(16) __nv_bfloat162 o[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) o[q] = __floats2bfloat162_rn(acc[2 * q], acc[2 * q + 1]);
-                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<bf16*>(Yv) + v * N + c0);
-                dst[0] = *reinterpret_cast<const uint4*>(&o[0]);
-                dst[1] = *reinterpret_cast<const uint4*>(&o[4]);
-            }
-        }
-    }
+        for (long long T = s_consumed; T < s_issued; ++T)
+            mbar_wait(smem_u32(&w_full[T % WS]), (unsigned)((T / WS) & 1));
+    if (tid == 0 && s_fail) atomicCAS(&g_tc_error, 0u, 1u);
     fence_before();
     __syncthreads();
+    fence_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols)
                      : "memory");
@@ -558,33 +672,45 @@ int tmem_cols_for(int n) {
     return c;
 }
 
-// Launch configuration of the forward kernel: z planes per block (tz) and
-// weight stages (ns).  Two planes share every weight slab (half the weight
-// traffic per output voxel, twice the MMA work per slab); more stages keep
-// more slabs in flight.  The first that fits two blocks per SM, else one.
+// Launch configuration of the forward kernel: z planes per tile (tz: the
+// planes share every weight slab and give the MMA thread tz independent
+// accumulators to interleave), weight stages (ws), halo stages (hs, two: one
+// loading while the MMAs read the other) and persistent blocks per SM
+// (per_sm: blocks on one SM interleave their MMA streams too).  The blocks
+// of an SM must fit its 512 tensor-memory columns with both accumulator
+// buffers each.  Default (measured on the network's layer shapes): two
+// blocks per SM where tensor and shared memory hold them with at least four
+// weight stages each, else one; within that the most planes per tile; as
+// many weight stages as fit, up to 16.
 struct TcCfg {
-    int tz, ns;
+    int tz, ws, hs, cols, per_sm;
     size_t smem;
 };
 
-TcCfg tc_cfg(int cin, int cout, int d, int tz_req, int ns_req) {
+constexpr size_t kTcSmemMax = (size_t)226 * 1024;
+
+TcCfg tc_cfg(int cin, int cout, int d, int tz_req, int ws_req) {
     const int cg = cg_for(cin);
-    const int cols_per_tile = tmem_cols_for(cout);
-    // measured on the network's layers: resident blocks hide the load
-    // latency better than deeper weight pipelines (two stages), and two
-    // planes sharing each weight slab pay while N <= 64 (four planes gain
-    // nothing more)
-    const int tz_pref = cols_per_tile <= 64 ? 2 : 1;
-    for (int tz : {4, 2, 1}) {
-        if (tz_req ? tz != tz_req : tz > tz_pref) continue;
-        if (d % tz || tz * cols_per_tile > 256) continue;
-        for (int ns : {2, 4}) {
-            if (ns_req ? ns != ns_req : ns != 2) continue;
-            const size_t sm = tc_smem_bytes(cg, cout, tz, ns);
-            if (sm <= (size_t)226 * 1024) return TcCfg{tz, ns, sm};
+    const int tcols = tmem_cols_for(cout);
+    const int hs = 2;
+    for (int per_sm = 2; per_sm >= 1; --per_sm) {
+        const size_t cap = kTcSmemMax / per_sm - (per_sm > 1 ? 1024 : 0);
+        for (int tz : {4, 2, 1}) {
+            if (tz_req && tz != tz_req) continue;
+            if (d % tz || 2 * tz * tcols > 512) continue;
+            const int cols = tmem_cols_for(2 * tz * tcols);
+            if (per_sm * cols > 512) continue;
+            int ws = 0;
+            if (ws_req) {
+                if (ws_req >= 2 && tc_smem_bytes(cg, cout, tz, ws_req, hs) <= cap) ws = ws_req;
+            } else {
+                for (int w = 16; w >= (per_sm > 1 ? 4 : 2) && !ws; --w)
+                    if (tc_smem_bytes(cg, cout, tz, w, hs) <= cap) ws = w;
+            }
+            if (ws) return TcCfg{tz, ws, hs, cols, per_sm, tc_smem_bytes(cg, cout, tz, ws, hs)};
         }
     }
-    return TcCfg{0, 0, 0};
+    return TcCfg{0, 0, 0, 0, 0, 0};
 }
 
 }  // namespace
@@ -604,11 +730,15 @@ lbm_status lbm_nn_conv3d_tc_cfg(const void* x, int cin, const void* wk, const fl
     const TcCfg cf = tc_cfg(cin, cout, d, tz, ns);
     if (!cf.tz) return LBM_ERR_INVALID_ARG;
     const int cg = cg_for(cin);
-    const int cols = tmem_cols_for(cf.tz * tmem_cols_for(cout));
-    const size_t smem = tmem_safe_smem(cf.smem, cols);
+    // at most per_sm blocks on an SM (their accumulators fill its tensor memory)
+    const size_t smem = std::max(cf.smem, (size_t)(227 * 1024) / (size_t)(cf.per_sm + 1) + 1);
     const Vol vol{n, d, h, wdt};
-    const long long blocks = (long long)(wdt / TILE_X) * (h / TILE_Y) * (d / cf.tz) * n;
-    if (blocks > 0x7fffffffLL) return LBM_ERR_INVALID_ARG;
+    const long long tiles = (long long)(wdt / TILE_X) * (h / TILE_Y) * (d / cf.tz) * n;
+    if (tiles > 0x7fffffffLL) return LBM_ERR_INVALID_ARG;
+    int dev = 0, n_sm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)n_sm * cf.per_sm);
     cudaStream_t st = (cudaStream_t)stream;
     const bf16* X = static_cast<const bf16*>(x);
     const bf16* W = static_cast<const bf16*>(wk);
@@ -616,31 +746,19 @@ lbm_status lbm_nn_conv3d_tc_cfg(const void* x, int cin, const void* wk, const fl
     cudaError_t e = cudaSuccess;
     auto go = [&](auto kern) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) kern<<<(unsigned)blocks, THREADS, smem, st>>>(X, cin, cg, W, bias, y, cout, cols, vol);
+        if (e == cudaSuccess)
+            kern<<<grid, PT, smem, st>>>(X, cin, cg, W, bias, y, cout, tstride, cf.cols, vol, (int)tiles, cf.ws, cf.hs);
     };
-    (void)tstride;
-    auto pick = [&](auto tzc, auto nsc) {
-        constexpr int TZ = decltype(tzc)::value, NS = decltype(nsc)::value;
-        if (relu && !out_f32) go(conv3_tc_kernel<true, false, TZ, NS>);
-        else if (!relu && !out_f32) go(conv3_tc_kernel<false, false, TZ, NS>);
-        else if (relu) go(conv3_tc_kernel<true, true, TZ, NS>);
-        else go(conv3_tc_kernel<false, true, TZ, NS>);
+    auto pick = [&](auto tzc) {
+        constexpr int TZ = decltype(tzc)::value;
+        if (relu && !out_f32) go(conv3_tc_kernel<true, false, TZ>);
+        else if (!relu && !out_f32) go(conv3_tc_kernel<false, false, TZ>);
+        else if (relu) go(conv3_tc_kernel<true, true, TZ>);
+        else go(conv3_tc_kernel<false, true, TZ>);
     };
-    using I1 = std::integral_constant<int, 1>;
-    using I2 = std::integral_constant<int, 2>;
-    using I4 = std::integral_constant<int, 4>;
-    using S2 = std::integral_constant<int, 2>;
-    using S4 = std::integral_constant<int, 4>;
-    if (cf.tz == 4) {
-        if (cf.ns == 4) pick(I4{}, S4{});
-        else pick(I4{}, S2{});
-    } else if (cf.tz == 2) {
-        if (cf.ns == 4) pick(I2{}, S4{});
-        else pick(I2{}, S2{});
-    } else {
-        if (cf.ns == 4) pick(I1{}, S4{});
-        else pick(I1{}, S2{});
-    }
+    if (cf.tz == 4) pick(std::integral_constant<int, 4>{});
+    else if (cf.tz == 2) pick(std::integral_constant<int, 2>{});
+    else pick(std::integral_constant<int, 1>{});
     if (e == cudaSuccess) e = cudaGetLastError();
     return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }

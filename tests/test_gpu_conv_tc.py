@@ -88,6 +88,48 @@ def test_tc_conv_forward_matches_reference_and_mma_sync(torch, cin, cout, vol):
     assert lbm.lbm_nn_tc_error(True) == 0
 
 
+@pytest.mark.parametrize("cin,cout,tz", [(64, 64, 2), (32, 128, 1), (64, 32, 4)])
+def test_tc_conv_persistent_blocks_walk_many_tiles(torch, cin, cout, tz):
+    """Cells with far more tiles than SMs: every persistent block walks many
+    tiles, both accumulator buffers and every ring stage wrap around several
+    times.  Against the mma.sync layer (same BF16 operands, FP32
+    accumulation: FP32 summation order apart) on every output, and against
+    the FP64 reference on sampled voxels."""
+    n, d, h, w = 2, 16, 64, 64
+    rng = np.random.default_rng(7 * cin + cout + tz)
+    x = _bf16_round(rng.standard_normal((n, d, h, w, cin)))
+    wt = _bf16_round(rng.standard_normal((cout, cin, 3, 3, 3)) / math.sqrt(cin * 27))
+    b = rng.standard_normal(cout)
+    xg, wg, bg = _dev(torch, x, wt, b)
+    V = n * d * h * w
+    wk = torch.empty((27, cout, cin), dtype=torch.bfloat16, device="cuda")
+    assert lbm.lbm_nn_weights_kmajor(wg.data_ptr(), wk.data_ptr(), cin, cout, 0, None) == lbm.LBM_OK
+    y = torch.empty((V, cout), dtype=torch.float32, device="cuda")
+    assert lbm.lbm_nn_conv3d_tc_cfg(xg.data_ptr(), cin, wk.data_ptr(), bg.data_ptr(), y.data_ptr(), cout,
+                                    n, d, h, w, 1, 1, tz, 0, None) == lbm.LBM_OK
+    y2 = torch.empty((V, cout), dtype=torch.float32, device="cuda")
+    assert lbm.lbm_nn_conv3d(xg.data_ptr(), cin, wg.data_ptr(), bg.data_ptr(), y2.data_ptr(), cout,
+                             n, d, h, w, 3, 1, 1, None) == lbm.LBM_OK
+    torch.cuda.synchronize()
+    assert lbm.lbm_nn_tc_error(True) == 0
+    got = y.cpu().numpy().reshape(n, d, h, w, cout)
+    other = y2.cpu().numpy().reshape(n, d, h, w, cout)
+    scale = np.max(np.abs(other))
+    assert np.max(np.abs(got - other)) <= 1e-5 * scale
+    # sampled voxels against the FP64 definition (periodic in x, y; zero in z)
+    for _ in range(64):
+        c, z, yy, xx = (int(rng.integers(0, s)) for s in (n, d, h, w))
+        acc = b.copy()
+        for dz in (-1, 0, 1):
+            if not 0 <= z + dz < d:
+                continue
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    acc += wt[:, :, dz + 1, dy + 1, dx + 1] @ x[c, z + dz, (yy + dy) % h, (xx + dx) % w]
+        leaky = np.where(acc > 0, acc, 0.01 * acc)
+        assert np.max(np.abs(got[c, z, yy, xx] - leaky)) <= 1e-3 * scale
+
+
 @pytest.mark.parametrize("tz,ns", [(1, 2), (1, 4), (2, 2), (2, 4), (4, 2), (4, 4)])
 @pytest.mark.parametrize("cin,cout", [(64, 64), (32, 128), (128, 64)])
 def test_tc_conv_every_launch_configuration(torch, cin, cout, tz, ns):
