@@ -925,7 +925,14 @@ def run_ours(args):
                          "kernel_source_sha16": kernel_source_sha16(),
                          "launch_us": launch_us,
                          "launches_timed": n_timed, "launch_timing": timing_mode,
-                         "frac_whole_step": achieved_step / peak},
+                         "frac_whole_step": achieved_step / peak,
+                         # the state is four fields per node; a state of seven
+                         # populations would move 57 B per update (FP32), 29 B
+                         # (16-bit): the same launch against that figure
+                         "seven_population_equivalent": {
+                             "bytes_per_lup": 57 if args.storage == "f32" else 29,
+                             "frac": (57 if args.storage == "f32" else 29) * n_vox * upd
+                             / (launch_us * 1e-6) / 1e9 / peak}},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_glups, "unit": "GLUPS",
                     "h2d_bytes_per_step": n_vox + lam.nbytes,
