@@ -31,13 +31,15 @@
  *     retrievable with lbm_last_error().  After LBM_ERR_CUDA the context is
  *     poisoned: only lbm_last_error() and lbm_destroy() remain valid.
  *   - One context per host thread; contexts are independent.
- *   - The collision is FP32.  Distributions are stored (FP32, or BF16 /
- *     FP16 with opts.storage) as deviations g_i = f_i - w_i R(z) from a
- *     per-plane reference temperature R(z) along the temperature-difference
- *     axis: the plane mean of T at the previous check, rounded to a
- *     power-of-two grid so that every change of frame is exact in FP32.
- *     The map is linear, so the frame changes no result in exact
- *     arithmetic; it keeps the stored values small.  Plane-flux and residual
+ *   - The collision is FP32.  The reduced collision leaves every node's
+ *     seven populations fixed by four numbers, so the state is stored (FP32,
+ *     or BF16 / FP16 with opts.storage) as four fields per node,
+ *     th = T - R(z) and jhat / 2; each step rebuilds the populations it
+ *     pulls exactly.  R(z) is a per-plane reference temperature along the
+ *     temperature-difference axis: the plane mean of T at the previous
+ *     check, rounded to a power-of-two grid so that every change of frame
+ *     is exact in FP32.  The map is linear, so the frame changes no result
+ *     in exact arithmetic; it keeps the stored values small.  Plane-flux and residual
  *     reductions are FP64.
  */
 #ifndef LBM_H
