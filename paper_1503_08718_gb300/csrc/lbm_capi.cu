@@ -28,6 +28,7 @@ struct lbm_ctx {
     int n[3] = {0, 0, 0};
     int device = 0;
     int n_sm = 152;                        // multiprocessors of the device
+    int l2_bytes = 0;                      // L2 cache of the device
     bool fuse_ok = false;                  // the two-step kernels got their shared memory
     int f2_smem_max = 0;                   // dynamic shared memory they may use (bytes)
     int pair_flip = 0;                     // chunk direction of the next lbm_advance pair
@@ -297,8 +298,16 @@ const void* f2_kernel(bool periodic, int nxc) {
     return periodic ? f2_kernel_ptr<true, 0>() : f2_kernel_ptr<false, 0>();
 }
 
+// Unless forced, the runtime-width variant is used only where the FP32 state
+// (both buffers) exceeds twice the L2: below that, single steps run from L2
+// at least as fast (measured on cubes of 64 to 176 nodes: single steps
+// 82-204 GLUPS against 56-193 for the runtime-width two-step kernel; the
+// tuned 128-node rows gain already at 128^3: 228 against 204).
 lbm::F2Plan f2_plan_for(const lbm_ctx* c, int nx, int ny, int nz, int n_phases, bool periodic, bool force) {
     if (!c->fuse_ok) return lbm::F2Plan{};
+    const bool tuned = nx == 128 || nx == 256;
+    const double state = 2.0 * lbm::kFields * sizeof(float) * (double)nx * ny * nz;
+    if (!force && !tuned && c->l2_bytes > 0 && state < 2.0 * c->l2_bytes) return lbm::F2Plan{};
     return lbm::f2_plan(nx, ny, nz, n_phases, c->n_sm, c->f2_smem_max, force,
                         [&](int nxc, int threads, size_t smem) {
                             int nb = 0;
@@ -608,7 +617,8 @@ lbm_status create_ctx(int nx, int ny, int nz, int cuda_device, char* ws, size_t 
               cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaMallocHost((void**)&c->h_ctl, sizeof(Ctl)) == cudaSuccess &&
               cudaEventCreate(&c->ev0) == cudaSuccess && cudaEventCreate(&c->ev1) == cudaSuccess &&
-              cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, cuda_device) == cudaSuccess;
+              cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, cuda_device) == cudaSuccess &&
+              cudaDeviceGetAttribute(&c->l2_bytes, cudaDevAttrL2CacheSize, cuda_device) == cudaSuccess;
     // the fused two-step kernels need more than the default 48 KB of shared
     // memory; without it every solve runs single steps
     if (ok) {

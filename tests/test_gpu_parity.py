@@ -420,3 +420,18 @@ def test_converged_braided_cell_matches_oracle(axis, lateral):
     assert np.max(np.abs(S.temperature() - ref.temperature())) <= T_TOL
     assert info.k_eff == pytest.approx(ref.k_eff()[0], rel=K_TOL)
     S.close()
+
+
+def test_default_plan_by_row_width_and_l2():
+    """Without fuse = 2 the runtime-width two-step kernel is planned only for
+    states beyond twice the L2 (below that single steps from L2 are at least
+    as fast); the tuned 128-node rows take it from 128^3 on."""
+    rng = np.random.default_rng(5)
+    lam = np.stack([I.random_spd(rng) for _ in range(2)])
+    for shape, spl in (((64, 64, 64), 1), ((96, 96, 96), 1), ((128, 128, 128), 2)):
+        S = lbm.Solver(*shape)
+        S.set_geometry(I.random_phase(rng, *shape, 2), 2)
+        S.set_tensors(lam)
+        S.solve(2, 0, S.opts(tol=0.0, max_iters=100))
+        assert S.launch_plan()["steps_per_launch"] == spl, (shape, S.launch_plan())
+        S.close()
