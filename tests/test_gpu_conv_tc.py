@@ -226,12 +226,15 @@ def test_network_on_tensor_cores_matches_mma_sync(torch):
 
 @pytest.mark.parametrize("cin,cout,vol", [(16, 32, (1, 3, 16, 8)), (32, 64, (2, 2, 16, 16)),
                                           (64, 64, (1, 4, 32, 8)), (96, 32, (1, 2, 16, 8)),
-                                          (128, 128, (1, 2, 16, 16)), (192, 64, (1, 2, 16, 8))])
+                                          (128, 128, (1, 2, 16, 16)), (192, 64, (1, 2, 16, 8)),
+                                          (32, 40, (1, 2, 16, 24)), (16, 8, (1, 3, 16, 8))])
 def test_tc_weight_gradient_matches_reference(torch, cin, cout, vol):
-    """dW of the tensor-core kernel (both operands MN-major, one accumulator
-    per tap in tensor memory) against reverse-mode differentiation of the
-    FP64 reference conv; FP32 accumulation, bound 1e-4 of the scale as for
-    the mma.sync weight gradient."""
+    """dW of the tensor-core kernel (both operands MN-major, accumulators in
+    tensor memory; with cout <= 64 the M = 128 rows hold two or three
+    x-shifted copies of the output gradient, so that one MMA gives two or
+    three taps) against reverse-mode differentiation of the FP64 reference
+    conv; FP32 accumulation, bound 1e-4 of the scale as for the mma.sync
+    weight gradient."""
     import torch as T
     n, d, h, w = vol
     assert lbm.lbm_nn_conv3d_wgrad_tc_supported(cin, cout, n, d, h, w) == 1
