@@ -519,7 +519,7 @@ lbm_status lbm_batch_solve(lbm_batch* b, lbm_lateral lateral, const lbm_solve_op
             S[5] = (tau[2] * tau[3] - tau[0] * tau[5]) / det;
             S[8] = (tau[0] * tau[4] - tau[1] * tau[3]) / det;
             // the device's per-phase table: B = (I - S_b) / 2 for FP32, S_b for 16 bits
-            lbm::phase_entry(S, op.storage == LBM_STORE_F32, &sb[2 * (size_t)q]);
+            lbm::phase_entry(S, &sb[2 * (size_t)q]);
         }
         BCUDA(b, cudaMemcpyAsync(base + p.off_sb, sb.data(), sizeof(float4) * sb.size(),
                                  cudaMemcpyHostToDevice, st));

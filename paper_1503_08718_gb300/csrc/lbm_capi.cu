@@ -808,7 +808,7 @@ lbm_status lbm_start(lbm_ctx* c, lbm_axis axis, lbm_lateral lateral, const lbm_s
         tau[8] += 0.5;
         inv3(tau, S);
         // the device's per-phase table: B = (I - S_b) / 2 for FP32, S_b for 16 bits
-        lbm::phase_entry(S, op.storage == LBM_STORE_F32, &sb[2 * (size_t)p]);
+        lbm::phase_entry(S, &sb[2 * (size_t)p]);
     }
 
     // buffers

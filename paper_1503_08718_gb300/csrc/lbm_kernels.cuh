@@ -30,11 +30,9 @@
 // S_b = tau^-1 (the 3x3 off-diagonal block of Eq. 12 inverted).  Because the
 // rows of M in Eq. 11 are orthogonal, M^-1 maps this back to
 //   fhat_0 = T / 4,   fhat_{2k-1,2k} = T / 8 +- jhat_k / 2,
-// which is M^-1 S M applied exactly (no 7x7 product on the device).  With
-// FP32 storage the device holds, per phase, the symmetric B = (I - S_b) / 2,
-// so jhat_k / 2 = (B j)_k: one 3x3 product and no further scaling per node.
-// The 16-bit-storage step (8 nodes per thread, tight on registers) holds S_b
-// and forms jhat = j - S_b j, which fits its register budget without spills.
+// which is M^-1 S M applied exactly (no 7x7 product on the device).  The
+// device holds, per phase, the symmetric B = (I - S_b) / 2, so jhat_k / 2 =
+// (B j)_k: one 3x3 product and no further scaling per node.
 // Interfaces need no code: each node uses its own phase's table entry and
 // streaming is plain (Eq. 21, the half-lattice division scheme of Section 2.3).
 //
@@ -287,7 +285,7 @@ __device__ void close_plane(const StepArgs& a, int z) {
 
 // The collision of one node (Eq. 5, 8-13 in the reduced form above) from its
 // seven pulled values relative to R_src, with the frame constants kT, kJ and
-// the phase's table entry (sa, sc) = B (BTAB) or S_b; returns the fields the
+// the phase's table entry (sa, sc) = B; returns the fields the
 // state stores, th = T - R_dst and m = jhat / 2, and q_z, the flux along z
 // (Eq. 16).  Every step kernel uses this one function.
 struct Collided {
@@ -296,19 +294,14 @@ struct Collided {
     float qz;
 };
 
-// host side of the table: the entry of one phase from S_b (FP64, 3x3 row-major)
-inline void phase_entry(const double* S, bool btab, float4* e) {
-    if (btab) {
-        e[0] = make_float4((float)(0.5 * (1.0 - S[0])), (float)(0.5 * (1.0 - S[4])),
-                           (float)(0.5 * (1.0 - S[8])), (float)(-0.5 * S[5]));
-        e[1] = make_float4((float)(-0.5 * S[2]), (float)(-0.5 * S[1]), 0.f, 0.f);
-    } else {
-        e[0] = make_float4((float)S[0], (float)S[4], (float)S[8], (float)S[5]);
-        e[1] = make_float4((float)S[2], (float)S[1], 0.f, 0.f);
-    }
+// host side of the table: the entry of one phase, B = (I - S_b) / 2 from S_b
+// (FP64, 3x3 row-major), rounded once to FP32
+inline void phase_entry(const double* S, float4* e) {
+    e[0] = make_float4((float)(0.5 * (1.0 - S[0])), (float)(0.5 * (1.0 - S[4])),
+                       (float)(0.5 * (1.0 - S[8])), (float)(-0.5 * S[5]));
+    e[1] = make_float4((float)(-0.5 * S[2]), (float)(-0.5 * S[1]), 0.f, 0.f);
 }
 
-template <bool BTAB>
 __device__ __forceinline__ Collided collide_node(float g0, float g1, float g2, float g3, float g4,
                                                  float g5, float g6, float4 sa, float4 sc, float kT,
                                                  float kJ) {
@@ -316,21 +309,11 @@ __device__ __forceinline__ Collided collide_node(float g0, float g1, float g2, f
     // T - R_dst(z) (Eq. 14) and the flux moment j, with the frame constants
     c.th = (((g0 + g1) + (g2 + g3)) + ((g4 + g5) + g6)) + kT;
     const float jx = g1 - g2, jy = g3 - g4, jz = (g5 - g6) + kJ;
-    // the symmetric table entry: (xx, yy, zz, yz) = sa, (xz, xy) = sc.xy
-    const float ax = fmaf(sa.x, jx, fmaf(sc.y, jy, sc.x * jz));
-    const float ay = fmaf(sc.y, jx, fmaf(sa.y, jy, sa.w * jz));
-    const float az = fmaf(sc.x, jx, fmaf(sa.w, jy, sa.z * jz));
-    if (BTAB) {                          // a = B j = jhat / 2
-        c.m[0] = ax;
-        c.m[1] = ay;
-        c.m[2] = az;
-        c.qz = fmaf(0.5f, jz, az);      // j_z / 2 + (B j)_z
-    } else {                             // a = S_b j, jhat = j - a
-        c.m[0] = 0.5f * (jx - ax);
-        c.m[1] = 0.5f * (jy - ay);
-        c.m[2] = 0.5f * (jz - az);
-        c.qz = fmaf(-0.5f, az, jz);     // (j_z + jhat_z) / 2
-    }
+    // a = B j = jhat / 2 with the symmetric B: (xx, yy, zz, yz) = sa, (xz, xy) = sc.xy
+    c.m[0] = fmaf(sa.x, jx, fmaf(sc.y, jy, sc.x * jz));
+    c.m[1] = fmaf(sc.y, jx, fmaf(sa.y, jy, sa.w * jz));
+    c.m[2] = fmaf(sc.x, jx, fmaf(sa.w, jy, sa.z * jz));
+    c.qz = fmaf(0.5f, jz, c.m[2]);      // j_z / 2 + (B j)_z
     return c;
 }
 
@@ -485,9 +468,11 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
     const long long rzm = zlo ? row : row - PL;
     const long long rzp = zhi ? row : row + PL;
 
-    Raw cT = S::zero(), cX = cT, mT = cT, mY = cT, pT = cT, pY = cT, dT = cT, dZ = cT, uT = cT, uZ = cT;
+    // a thread past the plane's last vector (active false) loads row 0 of
+    // the plane: in bounds, and nothing it computes is stored or summed
+    Raw cT, cX, mT, mY, pT, pY, dT, dZ, uT, uZ;
     uint2 ph = make_uint2(0u, 0u);
-    if (active) {
+    {
         cT = S::load(LBM_CK(src + row + x0, src, NF * P, V, 1u));
         cX = S::load(LBM_CK(src + P + row + x0, src, NF * P, V, 1u));
         mT = S::load(LBM_CK(src + rym + x0, src, NF * P, V, 1u));
@@ -578,7 +563,7 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const int bx, const
         const int p = (k < 4 ? (ph.x >> (8 * k)) : (ph.y >> (8 * (k - 4)))) & 0xff;
         const float4 sa = s_sb[2 * p];
         const float4 sc = s_sb[2 * p + 1];
-        const Collided cc = collide_node<FMT == 0>(g0, g1, g2, g3, g4, g5, g6, sa, sc, kT, kJ);
+        const Collided cc = collide_node(g0, g1, g2, g3, g4, g5, g6, sa, sc, kT, kJ);
         const float th = cc.th;
         const bool real = RAGGED ? k < n_real : active;   // n_real is 0 for inactive threads
         o[0][k] = th;
@@ -723,7 +708,7 @@ __device__ __forceinline__ Quad4 collide_quad(const float4& cT, const float4& cX
         const float g0 = 0.25f * f4get(cT, k);
         const float g1 = k == 0 ? pull_p(lT, lX) : pull_p(f4get(cT, k - 1), f4get(cX, k - 1));
         const float g2 = k == 3 ? pull_m(rT, rX) : pull_m(f4get(cT, k + 1), f4get(cX, k + 1));
-        const Collided c = collide_node<true>(g0, g1, g2, pull_p(f4get(mT, k), f4get(mY, k)),
+        const Collided c = collide_node(g0, g1, g2, pull_p(f4get(mT, k), f4get(mY, k)),
                                               pull_m(f4get(pT, k), f4get(pY, k)), pull_p(f4get(dT, k), f4get(dZ, k)),
                                               pull_m(f4get(uT, k), f4get(uZ, k)), s_sa[ph],
                                               make_float4(sc.x, sc.y, 0.f, 0.f), kT, kJ);
