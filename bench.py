@@ -459,8 +459,7 @@ def combined_form(lbm, I, stream, rel=1e-4, budget=40_000):
             iters.append(int(h[f, 0]))
     out["plain_f32_sequential"] = {"ms": tot, "iters_mean": float(np.mean(iters))}
     # network inference for all cells at once
-    net = W.WarmNet()
-    net.load(WARM_WEIGHTS)
+    net = W.WarmNet.from_file(WARM_WEIGHTS)
     phs = np.stack([c[0] for c in cells])
     x0, tl = net.make_input(phs, [c[1] for c in cells])
     vol = (len(cells), 64, 64, 64)
@@ -519,8 +518,7 @@ def warm_start_config5(lbm, I, stream, seeds=(5000, 5001, 5002, 5003), tol=1e-8)
 
     if not os.path.exists(WARM_WEIGHTS):
         return {"unavailable": "no trained warm-start weights"}
-    net = W.WarmNet()
-    net.load(WARM_WEIGHTS)
+    net = W.WarmNet.from_file(WARM_WEIGHTS)
     rows = []
     for s in seeds:
         g, phi = I.warm_cell_params(s)

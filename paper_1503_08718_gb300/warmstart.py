@@ -155,6 +155,17 @@ class WarmNet:
         arrs["hb"] = self.hb.cpu().numpy()
         np.savez(path, **arrs)
 
+    @classmethod
+    def from_file(cls, path: str, **kw):
+        """A network with the architecture (channels per level) the weights
+        file records, loaded from it."""
+        z = np.load(path)
+        if "chans" in z:
+            kw.setdefault("chans", tuple(int(c) for c in z["chans"]))
+        net = cls(**kw)
+        net.load(path)
+        return net
+
     def load(self, path: str):
         torch = self.torch
         z = np.load(path)
@@ -520,7 +531,7 @@ def main(argv=None):
     ap.add_argument("--train-cells", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--lr", type=float, default=5e-4)
-    ap.add_argument("--chans", default="32,64,128")
+    ap.add_argument("--chans", default="32,64,128,128")
     ap.add_argument("--eval-cells", type=int, default=10)
     ap.add_argument("--eval-shape", default="128,128,256")
     ap.add_argument("--weights", default=None, help="load instead of training")
@@ -528,11 +539,9 @@ def main(argv=None):
     ap.add_argument("--skip-eval", action="store_true")
     a = ap.parse_args(argv)
     chans = tuple(int(c) for c in a.chans.split(","))
-    net = WarmNet(seed=0, chans=chans)
-    summary = {"chans": chans}
-    if a.weights:
-        net.load(a.weights)
-    else:
+    net = WarmNet.from_file(a.weights) if a.weights else WarmNet(seed=0, chans=chans)
+    summary = {"chans": net.chans}
+    if not a.weights:
         t0 = time.time()
         ph, lams, temps, _ = generate_cells(range(a.train_cells), n=64)
         t1 = time.time()

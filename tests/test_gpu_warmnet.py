@@ -173,8 +173,7 @@ def test_warm_start_saves_iterations(torch):
     weights = os.path.join(root, "paper_1503_08718_gb300", "weights", "warmnet_braid64.npz")
     with open(os.path.join(root, "tests", "golden", "keff_reference.json")) as fh:
         refs = json.load(fh)["cells"]
-    net = WarmNet()
-    net.load(weights)
+    net = WarmNet.from_file(weights)
     saved, checked = [], 0
     for seed in (7000, 7001, 7002):
         ref = refs.get(f"warm64_{seed}")
