@@ -69,9 +69,9 @@ typedef enum {
 
 typedef enum { LBM_AXIS_X = 0, LBM_AXIS_Y = 1, LBM_AXIS_Z = 2 } lbm_axis;
 typedef enum { LBM_LATERAL_PERIODIC = 0, LBM_LATERAL_ADIABATIC = 1 } lbm_lateral;
-/* Storage of the distributions between steps; the collision is FP32 in every
- * mode.  BF16 and FP16 halve the memory traffic (29 instead of 57 bytes per
- * lattice update) and are rounded stochastically on store. */
+/* Storage of the state (four fields per node) between steps; the collision
+ * is FP32 in every mode.  BF16 and FP16 halve the memory traffic (17 instead
+ * of 33 bytes per lattice update) and are rounded stochastically on store. */
 typedef enum { LBM_STORE_F32 = 0, LBM_STORE_BF16 = 1, LBM_STORE_F16 = 2 } lbm_storage;
 
 typedef struct {
