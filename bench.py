@@ -508,7 +508,7 @@ def combined_form(lbm, I, stream, rel=1e-4, budget=40_000):
     return out
 
 
-def warm_start_config5(lbm, I, stream, seeds=(5000, 5001, 5002, 5003), tol=1e-8):
+def warm_start_config5(lbm, I, stream, seeds=tuple(range(5000, 5010)), tol=1e-8):
     """Learned warm start on 128x128x256 braided cells of the warm-start
     distribution (seeds 5000.., z axis, periodic laterals, FP32): iterations
     and device time to R_T <= tol from the linear profile and from the
